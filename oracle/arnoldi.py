@@ -1,0 +1,213 @@
+"""Gram-Schmidt Arnoldi-QR variants in plain FP64 numpy (test infrastructure only).
+
+Index convention (0-based): after ``k`` DCGS2 steps, columns q_0 .. q_{k-1} of Q are final,
+``w`` is the pending (projected once, unnormalised) vector, and Hessenberg columns
+0 .. k-2 are final.  H[i, j] is the coefficient of q_i in A q_j, so A Q_n = Q_{n+1} H.
+The paper's 1-based index j maps to k = j - 1.
+
+Pins (tests/test_oracle_arnoldi.py): Arnoldi relation and loss of orthogonality at O(eps),
+agreement of DCGS2, CGS2 and MGS Hessenbergs on well-conditioned problems, agreement with
+Householder QR (LAPACK) of the Krylov matrix, the k = 0 start, breakdown on A = I, the
+diagonal-matrix Lanczos case, and the Manteuffel spectrum through Krylov-Schur.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _matvec(A, x):
+    return A @ x
+
+
+class DCGS2Arnoldi:
+    """DCGS2-Arnoldi (Algorithm 4, Section 4) with one global reduction per step.
+
+    init(r0): w = r0 unnormalised (the factorised matrix is B = [r0, A Q], Section 1).
+    step():   one matvec on the pending w, one fused reduction, the delayed normalisation
+              (Pythagorean trick, Alg. 4 line 4), Stephen's trick for T_k (eq. 30), the
+              projection (Alg. 4 lines 7-9) and the lagged representation update
+              (Alg. 4 lines 10-12, with line 12 executed before line 11 since line 11 reads
+              H_{j-1,j-2}; eq. 52 shows the term belongs).
+    finish(): the last column by CGS2 with an explicit norm (end of Section 3: the n-th
+              iteration applies CGS2 with two additional reductions).
+    """
+
+    def __init__(self, A, r0, ncap: int):
+        self.A = A
+        m = r0.shape[0]
+        self.m = m
+        self.ncap = ncap
+        self.Q = np.zeros((m, ncap))
+        self.H = np.zeros((ncap, ncap - 1))
+        self.K = np.zeros((ncap, ncap - 1))   # K[:, j]: partial column j of H, completed one step late
+        self.w = np.array(r0, dtype=np.float64, copy=True)
+        self.k = 0
+        self.alphas = []
+        self.finished = False
+        self.breakdown = False
+
+    def step(self):
+        k = self.k
+        if k + 1 >= self.ncap:
+            raise ValueError("basis capacity exhausted")
+        Qk = self.Q[:, :k]
+        w = self.w
+        v = _matvec(self.A, w)                      # v = A w_{j-1} (Section 4, matvec on w)
+        # the single global reduction [Q_{1:j-2}, w_{j-1}]^T [w_{j-1}, A w_{j-1}] (Alg. 4 line 1)
+        C = Qk.T @ w                                # C_{1:j-2,j-1}
+        S = Qk.T @ v                                # S_{1:j-2,j}
+        beta = w @ w                                # beta_{j-1}
+        s = w @ v                                   # S_{j-1,j}
+        alpha2 = beta - C @ C                       # Alg. 4 line 4 (Pythagoras)
+        if not alpha2 > 0.0:
+            raise FloatingPointError("Pythagorean norm is not positive")
+        alpha = np.sqrt(alpha2)
+        if k >= 1:                                  # Alg. 4 lines 10 and 12: H column k-1
+            self.H[:k, k - 1] = self.K[:k, k - 1] + C
+            self.H[k, k - 1] = alpha
+            # happy breakdown: A q_{k-1} (nearly) lies in span(Q_k)
+            if alpha <= 1e-13 * np.linalg.norm(self.H[:k + 1, k - 1]):
+                self.breakdown = True
+        T = np.empty(k + 1)
+        T[:k] = S / alpha                           # Alg. 4 line 6
+        T[k] = (s - C @ S) / alpha ** 2             # Alg. 4 line 5 (Stephen's trick, eq. 30)
+        q = (w - Qk @ C) / alpha                    # Alg. 4 lines 7-8
+        self.Q[:, k] = q
+        self.w = v / alpha - Qk @ T[:k] - q * T[k]  # Alg. 4 line 9
+        # Alg. 4 line 11: K_{1:j-1,j-1} = T - (1/alpha) H_{1:j-1,1:j-2} C
+        self.K[:k + 1, k] = T - (self.H[:k + 1, :k] @ C) / alpha
+        self.alphas.append(alpha)
+        self.k = k + 1
+        return alpha
+
+    def finish(self):
+        """CGS2 on the pending w: finalises H column k-1 and q_k."""
+        k = self.k
+        Qk = self.Q[:, :k]
+        w = self.w
+        C1 = Qk.T @ w
+        u = w - Qk @ C1
+        C2 = Qk.T @ u
+        u = u - Qk @ C2
+        alpha = np.sqrt(u @ u)
+        self.H[:k, k - 1] = self.K[:k, k - 1] + C1 + C2
+        self.H[k, k - 1] = alpha
+        self.Q[:, k] = u / alpha
+        self.finished = True
+        return alpha
+
+    def result(self):
+        k = self.k
+        return self.Q[:, :k + 1].copy(), self.H[:k + 1, :k].copy()
+
+
+def dcgs2_arnoldi(A, r0, n: int):
+    """n DCGS2 steps plus the CGS2 finish: Q (m x (n+1)), H ((n+1) x n)."""
+    st = DCGS2Arnoldi(A, r0, n + 1)
+    for _ in range(n):
+        st.step()
+    st.finish()
+    return st.result()
+
+
+def cgs2_arnoldi(A, r0, n: int):
+    """CGS2-Arnoldi (Algorithm 3): two projections and a normalisation, 3 reductions/step.
+
+    q_0 = r0/||r0||; column j of H holds S + C above the diagonal and alpha below it
+    (H[i, j] = coefficient of q_i in A q_j, eq. "arnoldi").
+    """
+    m = r0.shape[0]
+    Q = np.zeros((m, n + 1))
+    H = np.zeros((n + 1, n))
+    Q[:, 0] = r0 / np.sqrt(r0 @ r0)
+    for j in range(n):
+        Qj = Q[:, :j + 1]
+        v = _matvec(A, Q[:, j])                     # generation of the next vector
+        S = Qj.T @ v                                # first projection
+        w = v - Qj @ S
+        C = Qj.T @ w                                # second projection
+        u = w - Qj @ C
+        alpha = np.sqrt(u @ u)                      # normalisation
+        Q[:, j + 1] = u / alpha
+        H[:j + 1, j] = S + C
+        H[j + 1, j] = alpha
+    return Q, H
+
+
+def mgs_arnoldi(A, r0, n: int):
+    """MGS-Arnoldi, level 1: sequential rank-1 projections, one reduction per inner product."""
+    m = r0.shape[0]
+    Q = np.zeros((m, n + 1))
+    H = np.zeros((n + 1, n))
+    Q[:, 0] = r0 / np.sqrt(r0 @ r0)
+    for j in range(n):
+        v = _matvec(A, Q[:, j])
+        for i in range(j + 1):
+            h = Q[:, i] @ v
+            v = v - h * Q[:, i]
+            H[i, j] = h
+        alpha = np.sqrt(v @ v)
+        H[j + 1, j] = alpha
+        Q[:, j + 1] = v / alpha
+    return Q, H
+
+
+def cgs2_qr(B):
+    """CGS2 QR of B (Algorithm 1): B = Q R, R upper triangular with R_jj = alpha_j."""
+    m, n = B.shape
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    for j in range(n):
+        a = B[:, j]
+        Qj = Q[:, :j]
+        S = Qj.T @ a
+        w = a - Qj @ S
+        C = Qj.T @ w
+        u = w - Qj @ C
+        alpha = np.sqrt(u @ u)
+        Q[:, j] = u / alpha
+        R[:j, j] = S + C
+        R[j, j] = alpha
+    return Q, R
+
+
+def dcgs2_qr(B):
+    """DCGS2 QR of B (Algorithm 2): one reduction per column, last column by CGS2.
+
+    At iteration j (0-based, j >= 1) the reduction [Q_{0:j-2}, w_{j-1}]^T [w_{j-1}, a_j]
+    gives C (delayed reorthogonalisation of w_{j-1}), beta, S_{0:j-2} and S_{j-1}; then
+    alpha_{j-1} by Pythagoras, q_{j-1}, Stephen's trick for S_{j-1,j}, the projection of
+    a_j, and column j-1 of R (S of the previous iteration plus C).
+    """
+    m, n = B.shape
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    w = B[:, 0].copy()                 # w_0 = a_0 (nothing to project against)
+    S_prev = np.zeros(0)               # S_{0:j-2, j-1} of the previous iteration
+    for j in range(1, n):
+        a = B[:, j]
+        Qp = Q[:, :j - 1]              # Q_{0:j-2}
+        C = Qp.T @ w
+        beta = w @ w
+        S = Qp.T @ a
+        s = w @ a
+        alpha = np.sqrt(beta - C @ C)
+        q = (w - Qp @ C) / alpha
+        Q[:, j - 1] = q
+        s_corr = (s - C @ S) / alpha   # Stephen's trick: q_{j-1}^T a_j
+        R[:j - 1, j - 1] = S_prev + C
+        R[j - 1, j - 1] = alpha
+        S_full = np.concatenate([S, [s_corr]])
+        w = a - Q[:, :j] @ S_full
+        S_prev = S_full
+    # last column: CGS2 with explicit norm
+    Qp = Q[:, :n - 1]
+    C1 = Qp.T @ w
+    u = w - Qp @ C1
+    C2 = Qp.T @ u
+    u = u - Qp @ C2
+    alpha = np.sqrt(u @ u)
+    Q[:, n - 1] = u / alpha
+    R[:n - 1, n - 1] = S_prev + C1 + C2
+    R[n - 1, n - 1] = alpha
+    return Q, R
