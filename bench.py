@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: DCGS2 Arnoldi-QR throughput on the 252^3 convection-diffusion operator.
+
+One benchmark "step" is one full Arnoldi expansion of n = 50 columns through the C ABI:
+init (w = r0), 50 DCGS2 steps (SpMV + one fused reduction with the scalar step + fused
+update each) and the CGS2 finish.  The reported metric is Arnoldi steps (basis columns)
+per second; HBM GB/s (algorithmic bytes) is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the workload on its own GPU
+(weak scaling, no data-path collective); rank 0 prints one JSON line.  The reference arm
+(--impl reference) times the FP64 CPU oracle on the host cores on a bounded sample of
+the same workload, scaled to the metric's unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import config2_operator, convdiff_csr, gaussian_vector  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 FMA peak derived from unit counts and the maximum clock: 152 SMs x 2 DFMA/clk/SM
+# x 2 flop x 2.070 GHz (a DFMA throughput probe measured 1.20 TFLOP/s at 2.0 GHz)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--N", type=int, default=252, help="grid points per direction (m = N^3)")
+    p.add_argument("--n", type=int, default=50, help="Arnoldi steps per expansion")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def algorithmic_bytes(m, nnz, n):
+    """HBM bytes of one expansion (n DCGS2 steps + finish), FP64, int32 indices.
+
+    step k: SpMV 4(m+1) + 12 nnz + 8m (x) + 8m (y); reduction 8mk + 16m (Q_k, w, v);
+    update 8mk + 16m reads + 16m writes (q_k, w).  finish: two (reduction + projection)
+    passes 2*(8mk + 8m) + 2*(8mk + 16m), norm 8m, scaling 16m."""
+    spmv = 4 * (m + 1) + 12 * nnz + 16 * m
+    total = 0
+    per_kernel = {"spmv": 0, "reduce": 0, "dcgs2_update": 0}
+    for k in range(n):
+        per_kernel["spmv"] += spmv
+        per_kernel["reduce"] += 8 * m * k + 16 * m
+        per_kernel["dcgs2_update"] += 8 * m * k + 32 * m
+    k = n
+    fin = 2 * (8 * m * k + 8 * m) + 2 * (8 * m * k + 16 * m) + 8 * m + 16 * m
+    total = sum(per_kernel.values()) + fin
+    return total, per_kernel
+
+
+def fp64_flops_reduce(m, n):
+    """FP64 flops of the fused reductions of one expansion: 2 FMA (4 flop) per basis
+    element and per row for beta and s."""
+    return sum(4 * m * k + 4 * m for k in range(n))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if not self.samples:
+            return None
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(n, N_sample=126, seed=1002):
+    """Time the FP64 oracle on one full n-step expansion of the same operator family at
+    N_sample^3 rows; returns (steps/s scaled to the full-size m, seconds, m_sample)."""
+    from oracle import arnoldi as orc
+    Ah = convdiff_csr(N_sample, 3, 50.0 * np.array([1.0, 0.5, 0.25]) / np.linalg.norm([1.0, 0.5, 0.25]))
+    A = Ah.to_scipy()
+    r0 = gaussian_vector(Ah.m, seed)
+    t0 = time.perf_counter()
+    orc.dcgs2_arnoldi(A, r0, n)
+    dt = time.perf_counter() - t0
+    return n / dt, dt, Ah.m
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    m_full = args.N ** 3
+    vals = []
+    for i in range(args.warmup + args.steps):
+        rate, dt, m_s = cpu_oracle_sample(args.n, N_sample=100)
+        if i >= args.warmup:
+            vals.append(rate * m_s / m_full)
+    v = float(np.mean(vals))
+    cores = blas_threads()
+    sample = ("FP64 oracle (numpy/scipy), one %d-step DCGS2 expansion of the same operator "
+              "family at 100^3 rows per step, rate scaled by rows to m = %d" % (args.n, m_full))
+    line = {"impl": "reference", "metric": "arnoldi_steps_per_s", "value": v,
+            "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "dcgs2_arnoldi m=%d n=%d (3D convection-diffusion %d^3, Pe 50)"
+                       % (m_full, args.n, args.N)},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import paper_2104_01253_gb300 as kc
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    Ah = config2_operator(args.N)
+    m, nnz = Ah.m, Ah.nnz
+    r0_host = gaussian_vector(m, 1002)
+    ctx = kc.Context(local)
+    A = kc.DeviceCSR(Ah)
+    del Ah
+    n = args.n
+    st = kc.ArnoldiState(m, n + 1, kc.KC_F64)
+    r0 = torch.as_tensor(r0_host, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def expansion(src):
+        kc.dcgs2_arnoldi_init(ctx, A, st, src)
+        for _ in range(n):
+            kc.dcgs2_arnoldi_step(ctx, A, st)
+        kc.dcgs2_arnoldi_finish(ctx, A, st)
+
+    for _ in range(args.warmup):
+        expansion(r0)
+    torch.cuda.synchronize()
+    status = ctx.read_status()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    launches0 = ctx.launch_count()
+    ctx.timing_enable(True)
+    barrier()
+    sampler.start()
+    time.sleep(0.2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        expansion(r0)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    kern = ctx.timing_read()
+    ctx.timing_enable(False)
+    launches = ctx.launch_count() - launches0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+
+    ms_per = ms_total / args.steps
+    value = ws * n * args.steps / (ms_total / 1e3)
+    total_bytes, per_kernel_bytes = algorithmic_bytes(m, nnz, n)
+    hbm_peak, peak_kind = peaks()
+    gbs = total_bytes / (ms_per / 1e3) / 1e9
+
+    # quality of the last expansion: loss of orthogonality and Arnoldi relation
+    Qv = st.Qbuf[:n + 1, :m]
+    G = Qv.double() @ Qv.double().T
+    loo = float(torch.linalg.norm(torch.eye(n + 1, device="cuda", dtype=torch.float64) - G))
+    H = st.Hbuf[:n, :n + 1].T.contiguous()
+    AQ = torch.empty(n, m, dtype=torch.float64, device="cuda")
+    for j in range(n):
+        kc.kc_spmv(ctx, A, Qv[j], AQ[j])
+    R = AQ - (H.T @ Qv)
+    normA = float(torch.linalg.norm(A.val))
+    rre = float(torch.linalg.norm(R)) / normA
+    del AQ, R, G
+
+    # dominant kernel roofline (FP64 pipe bound: 2 DFMA per basis element)
+    red_ms, red_cnt = kern.get("reduce", (0.0, 0))
+    upd_ms, upd_cnt = kern.get("dcgs2_update", (0.0, 0))
+    flops_red = fp64_flops_reduce(m, n) * args.steps
+    flops_upd = sum(4 * m * k + 4 * m for k in range(n)) * args.steps
+    if red_ms >= upd_ms:
+        dom, dom_ms, dom_cnt, dom_flops, dom_bytes = ("reduce", red_ms, red_cnt, flops_red,
+                                                      per_kernel_bytes["reduce"] * args.steps)
+    else:
+        dom, dom_ms, dom_cnt, dom_flops, dom_bytes = ("dcgs2_update", upd_ms, upd_cnt, flops_upd,
+                                                      per_kernel_bytes["dcgs2_update"] * args.steps)
+    achieved = dom_flops / (dom_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived FP64 FMA peak (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "hbm_achieved_gbs": dom_bytes / (dom_ms / 1e3) / 1e9,
+                "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
+                "avg_launch_ms": dom_ms / max(dom_cnt, 1)}
+
+    # end to end through the C ABI with host buffers: H2D of r0, expansion, D2H of H
+    e2e = None
+    if not args.no_e2e:
+        r0_pin = torch.from_numpy(r0_host).pin_memory()
+        r0_dev = torch.empty(m, dtype=torch.float64, device="cuda")
+        H_host = torch.empty((n, n + 1), dtype=torch.float64).pin_memory()
+        barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(args.steps):
+            r0_dev.copy_(r0_pin, non_blocking=True)
+            expansion(r0_dev)
+            H_host.copy_(st.Hbuf[:n, :n + 1], non_blocking=True)
+        e3.record(stream)
+        barrier()
+        ms_e2e = e2.elapsed_time(e3)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": ws * n * args.steps / (ms_e2e / 1e3), "unit": "steps/s",
+               "h2d_bytes_per_step": m * 8, "d2h_bytes_per_step": n * (n + 1) * 8}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, dt, m_s = cpu_oracle_sample(n)
+        cpu = {"value": rate * m_s / m, "unit": "steps/s", "cores": blas_threads(),
+               "kind": "oracle",
+               "sample": "one %d-step FP64 DCGS2 expansion by the numpy/scipy oracle on the "
+                         "same operator family at %d rows (%.1f s), rate scaled by rows to "
+                         "m = %d" % (n, m_s, dt, m)}
+
+    if rank == 0:
+        line = {
+            "metric": "arnoldi_steps_per_s", "value": value, "unit": "steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "dcgs2_arnoldi m=%d n=%d (3D convection-diffusion %d^3, "
+                                   "upwind, Pe 50, wind (1,0.5,0.25))" % (m, n, args.N),
+                       "nnz": nnz, "step": "one %d-column expansion (init, %d DCGS2 steps, "
+                                           "CGS2 finish)" % (n, n),
+                       "l2": "inputs larger than L2 (basis %.1f GB)" % (8 * m * (n + 1) / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "hbm_gbs": gbs, "hbm_frac_of_%s" % peak_kind: gbs / hbm_peak,
+            "algorithmic_bytes_per_step": total_bytes,
+            "loo": loo, "rre": rre, "device_status": status,
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * libkrylov: DCGS2 Arnoldi-QR on one GB300 GPU (C ABI).
+ *
+ * Method: "Low-Synch Gram-Schmidt with Delayed Reorthogonalization for Krylov Solvers"
+ * (Bielich, Langou, Thomas, Swirydowicz, Yamazaki, Boman).  The hot path is the DCGS2
+ * Arnoldi step of Algorithm 4 (Section 4): one sparse matvec on the pending unnormalised
+ * vector w, ONE fused reduction [Q, w]^T [w, A w], the delayed normalisation (Pythagorean
+ * trick), Stephen's trick (eq. 30), the projection update and the lagged Hessenberg
+ * correction.  Baselines: CGS2-Arnoldi (Algorithm 3) and MGS-Arnoldi (Section 2).
+ * Drivers: restarted GMRES (Section 1 problem (1)), Krylov-Schur (problem (2)), FP32/BF16
+ * inner solves in FP64 iterative refinement, and flexible GMRES with a learned
+ * convolutional right preconditioner.
+ *
+ * Conventions for every entry point
+ *  - All array arguments are DEVICE pointers owned by the caller unless stated otherwise;
+ *    the library never frees them.  The library allocates only its context workspace.
+ *  - Work is enqueued on the context's stream and is asynchronous, except where a function
+ *    returns a host scalar (it then synchronises that stream once at the end).
+ *  - Errors are returned as kc_status; kc_last_error() gives the message of the context's
+ *    last failure.  No C++ exception crosses the ABI.
+ *  - Index convention (0-based): H[i + j*ldh] is the coefficient of q_i in A q_j, so that
+ *    A Q_n = Q_{n+1} H_n ((n+1) x n, eq. "arnoldi").  The paper's 1-based j maps to k = j-1.
+ */
+#ifndef KRYLOV_H
+#define KRYLOV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KC_OK = 0,
+  KC_ERR_INVALID_ARG = 1,   /* bad size, pointer, alignment or dtype combination */
+  KC_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  KC_ERR_OOM = 3,           /* context workspace allocation failed */
+  KC_ERR_BREAKDOWN = 4,     /* alpha_k <= 1e-13 * ||H(:,k-1)||: invariant subspace found */
+  KC_ERR_NOT_CONVERGED = 5, /* iteration limit reached before the tolerance */
+  KC_ERR_NONFINITE = 6,     /* NaN/Inf in a reduction result */
+  KC_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  KC_ERR_PYTHAGORAS_NEG = 8 /* beta - C^T C <= 0 in the delayed normalisation */
+} kc_status;
+
+typedef enum { KC_F64 = 0, KC_F32 = 1, KC_BF16 = 2 } kc_dtype;
+
+typedef struct kc_ctx kc_ctx;
+
+/* CSR matrix, m x m, int32 indices (nnz < 2^31), caller-owned device arrays.
+ * row_ptr[m+1] non-decreasing with row_ptr[0] = 0, col_idx[nnz] in [0, m),
+ * val[nnz] of type val_dtype (KC_F64 or KC_F32). */
+typedef struct {
+  int64_t m;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const void* val;
+  int32_t val_dtype;
+} kc_csr;
+
+/* Arnoldi state (caller-owned device buffers).
+ *  Q     basis, column-major: column j starts at element j*ldq; ldq >= m and even,
+ *        Q 16-byte aligned.  Element type q_dtype (KC_F64 with FP64 vectors; KC_F32 or
+ *        KC_BF16 with FP32 vectors).  ncap columns (the basis holds at most ncap columns,
+ *        i.e. at most ncap-1 DCGS2 steps before the finish); 2 <= ncap <= 128.
+ *  w, v  m-vectors (FP64 when q_dtype is KC_F64, else FP32), 16-byte aligned: w is the
+ *        pending vector, v the matvec workspace.
+ *  H     FP64, column-major, ldh >= ncap, at least ldh*(ncap-1) entries.
+ *  K     FP64 workspace, ncap*(ncap-1) entries, column-major with ld ncap: column j holds
+ *        the partial Hessenberg column that the next step completes (Alg. 4 line 11).
+ *  k     number of final basis columns; written by the library (read-only for callers).
+ *  nsteps_since_init  written by the library. */
+typedef struct {
+  void* Q;
+  int64_t ldq;
+  int32_t ncap;
+  int32_t q_dtype;
+  void* w;
+  void* v;
+  double* H;
+  int32_t ldh;
+  double* K;
+  int32_t k;
+  int32_t finished;
+} kc_arnoldi;
+
+/* ---- context ------------------------------------------------------------------------ */
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a cudaStream_t, or NULL for
+ * the legacy default stream).  Allocates the reduction workspace (a few hundred KB). */
+kc_status kc_create(kc_ctx** ctx, int device, void* cuda_stream);
+kc_status kc_destroy(kc_ctx* ctx);
+kc_status kc_set_stream(kc_ctx* ctx, void* cuda_stream);
+/* Message of the last failed call on this context (static storage inside ctx). */
+const char* kc_last_error(const kc_ctx* ctx);
+/* Number of SMs and the persistent grid size used for reductions. */
+kc_status kc_device_info(const kc_ctx* ctx, int* num_sms, int* reduce_grid);
+/* Number of kernels this context has launched since creation (host-side counter). */
+int64_t kc_launch_count(const kc_ctx* ctx);
+/* Per-kernel timing.  While enabled, CUDA events are recorded on the context's stream
+ * around every kernel the library launches.  kc_timing_read synchronises the stream and
+ * returns, per kernel kind, the summed elapsed milliseconds and launch counts, then
+ * clears the records.  Kinds (index): 0 SpMV, 1 fused reduction, 2 DCGS2 update,
+ * 3 projection update (x -= Q c), 4 norm / dot, 5 scaling, 6 MGS axpy, 7 small dense
+ * kernels, 8 other.  nkinds must be >= 9. */
+kc_status kc_timing_enable(kc_ctx* ctx, int on);
+kc_status kc_timing_read(kc_ctx* ctx, double* ms, int64_t* count, int nkinds);
+/* Read (and synchronise on) the device status word written by the last reductions:
+ * KC_OK, KC_ERR_BREAKDOWN, KC_ERR_NONFINITE or KC_ERR_PYTHAGORAS_NEG.  Clears it. */
+kc_status kc_read_status(kc_ctx* ctx, int* device_status);
+/* Copy the last step's scalars to host: alpha, beta (w^T w), s (w^T A w). */
+kc_status kc_last_scalars(kc_ctx* ctx, double* alpha, double* beta, double* s);
+
+/* ---- building blocks ---------------------------------------------------------------- */
+
+/* y = A x (K4': CSR SpMV).  x, y: m-vectors of the matrix value type (FP64 or FP32). */
+kc_status kc_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y);
+
+/* ---- DCGS2-Arnoldi (Algorithm 4) ----------------------------------------------------- */
+
+/* Start the expansion: w = r0 (unnormalised; the factorised matrix is B = [r0, A Q],
+ * Section 1), k = 0.  r0 has the vector type of the state. */
+kc_status dcgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0);
+
+/* One DCGS2 step (Algorithm 4): v = A w; the single fused reduction
+ * C = Q_k^T w, S = Q_k^T v, beta = w^T w, s = w^T v (Alg. 4 line 1); in the same launch
+ * alpha = sqrt(beta - C^T C) (line 4), H(0:k, k-1) = K(0:k, k-1) + C and H(k, k-1) = alpha
+ * (lines 10, 12), T = S/alpha, T_k = (s - C^T S)/alpha^2 (lines 5-6, eq. 30),
+ * K(0:k+1, k) = T - H(0:k+1, 0:k) C / alpha (line 11, after line 12 since it reads
+ * H(k, k-1)); then the fused update q_k = (w - Q_k C)/alpha -> Q(:,k) and
+ * w <- v/alpha - Q_k T(0:k) - q_k T_k (lines 7-9).  Requires k+1 < ncap.
+ * Three kernel launches; no host synchronisation.  Numerical failures are reported
+ * through kc_read_status (the step still completes with a guarded alpha). */
+kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
+
+/* Finish (end of Section 3: the last column by CGS2, two more reductions): with the
+ * pending w, C1 = Q^T w, u = w - Q C1, C2 = Q^T u, u -= Q C2, alpha = ||u||;
+ * H(0:k, k-1) = K(0:k, k-1) + C1 + C2, H(k, k-1) = alpha, Q(:,k) = u/alpha.
+ * Afterwards Q has k+1 columns and H is (k+1) x k. */
+kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
+
+/* ---- baselines ---------------------------------------------------------------------- */
+
+/* CGS2-Arnoldi (Algorithm 3) and MGS-Arnoldi (Section 2, "MGS Level 1"): init sets
+ * q_0 = r0/||r0|| (k = 1); each step appends column k-1 of H and q_k.  CGS2 does three
+ * reductions per step (two projections + norm), MGS one per inner product. */
+kc_status cgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0);
+kc_status cgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
+kc_status mgs_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
+
+/* ---- GMRES / iterative refinement / flexible GMRES ---------------------------------- */
+
+typedef struct {
+  int32_t restart;        /* basis size n of GMRES(n) */
+  int32_t maxit;          /* matvec limit */
+  int32_t precision;      /* 0 = FP64; 1 = FP32 inner solve in FP64 IR; 2 = BF16 basis IR */
+  int32_t max_outer;      /* IR: outer refinement limit */
+  double rtol;            /* relative residual target ||b - A x|| / ||b|| */
+  double inner_rtol;      /* IR: inner solve tolerance (relative to its right-hand side) */
+  int32_t inner_max_cycles; /* IR: cycles per inner solve */
+  int32_t pad;
+} kc_gmres_opts;
+
+typedef struct {
+  int32_t iters;          /* matvecs with A (inner iterations for IR) */
+  int32_t restarts;       /* GMRES cycles (all inner cycles for IR) */
+  int32_t outer;          /* IR refinement steps */
+  int32_t status;         /* kc_status of the solve */
+  double rel_resid_est;   /* last Givens estimate |g_k| / ||b|| */
+  double rel_resid_true;  /* FP64 ||b - A x|| / ||b|| recomputed on the device */
+} kc_gmres_info;
+
+/* Restarted DCGS2-GMRES(n) (FP64), or FP32/BF16-basis DCGS2-GMRES inside FP64 iterative
+ * refinement (precision 1/2; then A32 must be the FP32 copy of A, else it is ignored).
+ * b, x: FP64 m-vectors; x holds x0 on entry and the solution on return.  Synchronises. */
+kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const double* b,
+                      double* x, const kc_gmres_opts* opts, kc_gmres_info* info);
+
+/* ---- Krylov-Schur ------------------------------------------------------------------- */
+
+typedef struct {
+  int32_t nev;            /* wanted eigenvalues (largest real part) */
+  int32_t ncv;            /* basis size */
+  int32_t nkeep;          /* columns kept at a restart (+1 to keep a conjugate pair) */
+  int32_t maxrestarts;
+  double tol;             /* ||(A - lambda I) z|| <= tol * |lambda| (eq. "ArnoldiRes") */
+} kc_ks_opts;
+
+/* Krylov-Schur on DCGS2-Arnoldi.  v0: FP64 start vector (device).  eig_re, eig_im,
+ * resid: HOST arrays of length nev (largest real part first).  nconv, restarts,
+ * matvecs: host outputs (may be NULL).  The small dense Schur step runs on the GPU in
+ * FP64.  Synchronises. */
+kc_status krylov_schur_eigs(kc_ctx* ctx, const kc_csr* A, const double* v0,
+                            const kc_ks_opts* opts, double* eig_re, double* eig_im,
+                            double* resid, int* nconv, int* restarts, int* matvecs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRYLOV_H */

@@ -1,0 +1,333 @@
+// C-ABI entry points: context, validation, and the Arnoldi steps (DCGS2, CGS2, MGS).
+#include "kc_internal.cuh"
+
+#include <new>
+#include <string.h>
+
+using namespace kc;
+
+namespace kc {
+
+kc_status validate_csr(kc_ctx* ctx, const kc_csr* A) {
+  if (!A) return fail(ctx, KC_ERR_INVALID_ARG, "A is NULL");
+  if (A->m <= 0 || A->m >= (int64_t)1 << 31)
+    return fail(ctx, KC_ERR_INVALID_ARG, "matrix size m = %lld out of range", (long long)A->m);
+  if (A->nnz < 0 || A->nnz >= (int64_t)1 << 31)
+    return fail(ctx, KC_ERR_INVALID_ARG, "nnz = %lld does not fit int32 indices", (long long)A->nnz);
+  if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val)))
+    return fail(ctx, KC_ERR_INVALID_ARG, "CSR arrays must be non-NULL device pointers");
+  if (A->val_dtype != KC_F64 && A->val_dtype != KC_F32)
+    return fail(ctx, KC_ERR_INVALID_ARG, "CSR values must be KC_F64 or KC_F32");
+  return KC_OK;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+kc_status validate_state(kc_ctx* ctx, const kc_csr* A, const kc_arnoldi* st) {
+  if (!st) return fail(ctx, KC_ERR_INVALID_ARG, "state is NULL");
+  if (!st->Q || !st->w || !st->v || !st->H || !st->K)
+    return fail(ctx, KC_ERR_INVALID_ARG, "state buffers must be non-NULL device pointers");
+  if (!aligned16(st->Q) || !aligned16(st->w) || !aligned16(st->v))
+    return fail(ctx, KC_ERR_INVALID_ARG, "Q, w and v must be 16-byte aligned");
+  if (st->ncap < 2 || st->ncap > NMAX)
+    return fail(ctx, KC_ERR_INVALID_ARG, "ncap = %d outside [2, %d]", st->ncap, NMAX);
+  if (st->ldq < A->m || (st->ldq % 8) != 0)
+    return fail(ctx, KC_ERR_INVALID_ARG, "ldq = %lld must be >= m and a multiple of 8",
+                (long long)st->ldq);
+  if (st->ldh < st->ncap) return fail(ctx, KC_ERR_INVALID_ARG, "ldh < ncap");
+  if (st->q_dtype != KC_F64 && st->q_dtype != KC_F32 && st->q_dtype != KC_BF16)
+    return fail(ctx, KC_ERR_INVALID_ARG, "q_dtype must be KC_F64, KC_F32 or KC_BF16");
+  const int vec = st->q_dtype == KC_F64 ? KC_F64 : KC_F32;
+  if (A->val_dtype != vec)
+    return fail(ctx, KC_ERR_INVALID_ARG,
+                "basis type %d needs %s matrix values", st->q_dtype, vec == KC_F64 ? "FP64" : "FP32");
+  if (st->k < 0 || st->k >= st->ncap) return fail(ctx, KC_ERR_INVALID_ARG, "corrupt k = %d", st->k);
+  return KC_OK;
+}
+
+void timing_begin(kc_ctx* ctx, int kid) {
+  if (!ctx->timing_on) return;
+  if (ctx->trec_len == ctx->trec_cap) {
+    int ncap = ctx->trec_cap ? 2 * ctx->trec_cap : 1024;
+    TimingRec* n = new (std::nothrow) TimingRec[ncap];
+    if (!n) return;
+    for (int i = 0; i < ctx->trec_cap; i++) n[i] = ctx->trec[i];
+    for (int i = ctx->trec_cap; i < ncap; i++) {
+      cudaEventCreate(&n[i].a);
+      cudaEventCreate(&n[i].b);
+    }
+    delete[] ctx->trec;
+    ctx->trec = n;
+    ctx->trec_cap = ncap;
+  }
+  TimingRec& r = ctx->trec[ctx->trec_len];
+  r.kid = kid;
+  cudaEventRecord(r.a, ctx->stream);
+}
+
+void timing_end(kc_ctx* ctx) {
+  if (!ctx->timing_on || ctx->trec_len >= ctx->trec_cap) return;
+  cudaEventRecord(ctx->trec[ctx->trec_len].b, ctx->stream);
+  ctx->trec_len++;
+}
+
+}  // namespace kc
+
+static int vec_of(const kc_arnoldi* st) { return st->q_dtype == KC_F64 ? KC_F64 : KC_F32; }
+static size_t qsize(int dt) { return dt == KC_F64 ? 8 : (dt == KC_F32 ? 4 : 2); }
+static void* qcol(const kc_arnoldi* st, int j) {
+  return (char*)st->Q + (size_t)j * st->ldq * qsize(st->q_dtype);
+}
+
+static StepArgs step_args(const kc_arnoldi* st, int k, int flags) {
+  StepArgs sa;
+  sa.H = st->H;
+  sa.ldh = st->ldh;
+  sa.K = st->K;
+  sa.ldk = st->ncap;
+  sa.R = nullptr;
+  sa.ldr = 0;
+  sa.k = k;
+  sa.row = 0;
+  sa.flags = flags;
+  // FP64: flag only a non-positive Pythagorean norm; FP32/BF16: 64 unit roundoffs
+  sa.pyth_tol = st->q_dtype == KC_F64 ? 0.0 : 64.0 * 5.9604644775390625e-08;
+  return sa;
+}
+
+#define KC_TRY(x)                 \
+  do {                            \
+    kc_status s_ = (x);           \
+    if (s_ != KC_OK) return s_;   \
+  } while (0)
+
+extern "C" {
+
+kc_status kc_create(kc_ctx** out, int device, void* cuda_stream) {
+  if (!out) return KC_ERR_INVALID_ARG;
+  *out = nullptr;
+  kc_ctx* ctx = new (std::nothrow) kc_ctx;
+  if (!ctx) return KC_ERR_OOM;
+  memset(ctx, 0, sizeof(*ctx));
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) { delete ctx; return KC_ERR_CUDA; }
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) { delete ctx; return KC_ERR_CUDA; }
+  ctx->num_sms = p.multiProcessorCount;
+  ctx->reduce_grid = 2 * p.multiProcessorCount;
+  const size_t plen = (size_t)ctx->reduce_grid * (2 * NMAX + 4) * sizeof(double);
+  bool ok = cudaMalloc(&ctx->partials, plen) == cudaSuccess &&
+            cudaMalloc(&ctx->counters, 16 * sizeof(unsigned int)) == cudaSuccess &&
+            cudaMalloc(&ctx->scal, sizeof(Scalars)) == cudaSuccess &&
+            cudaMallocHost(&ctx->scal_host, sizeof(Scalars)) == cudaSuccess;
+  ctx->dwork_len = 1 << 20;
+  ok = ok && cudaMalloc(&ctx->dwork, ctx->dwork_len * sizeof(double)) == cudaSuccess;
+  if (ok) ok = cudaMemset(ctx->counters, 0, 16 * sizeof(unsigned int)) == cudaSuccess &&
+               cudaMemset(ctx->scal, 0, sizeof(Scalars)) == cudaSuccess &&
+               cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    kc_destroy(ctx);
+    return KC_ERR_OOM;
+  }
+  *out = ctx;
+  return KC_OK;
+}
+
+kc_status kc_destroy(kc_ctx* ctx) {
+  if (!ctx) return KC_OK;
+  for (int i = 0; i < ctx->trec_cap; i++) {
+    cudaEventDestroy(ctx->trec[i].a);
+    cudaEventDestroy(ctx->trec[i].b);
+  }
+  delete[] ctx->trec;
+  if (ctx->partials) cudaFree(ctx->partials);
+  if (ctx->counters) cudaFree(ctx->counters);
+  if (ctx->scal) cudaFree(ctx->scal);
+  if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
+  if (ctx->dwork) cudaFree(ctx->dwork);
+  delete ctx;
+  return KC_OK;
+}
+
+kc_status kc_set_stream(kc_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return KC_OK;
+}
+
+const char* kc_last_error(const kc_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+kc_status kc_device_info(const kc_ctx* ctx, int* num_sms, int* reduce_grid) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  if (num_sms) *num_sms = ctx->num_sms;
+  if (reduce_grid) *reduce_grid = ctx->reduce_grid;
+  return KC_OK;
+}
+
+int64_t kc_launch_count(const kc_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+kc_status kc_timing_enable(kc_ctx* ctx, int on) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  ctx->timing_on = on;
+  ctx->trec_len = 0;
+  return KC_OK;
+}
+
+kc_status kc_timing_read(kc_ctx* ctx, double* ms, int64_t* count, int nkinds) {
+  if (!ctx || !ms || !count || nkinds < KID_COUNT) return fail(ctx, KC_ERR_INVALID_ARG, "kc_timing_read: bad arguments");
+  KC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < nkinds; i++) { ms[i] = 0.0; count[i] = 0; }
+  for (int i = 0; i < ctx->trec_len; i++) {
+    float t = 0.f;
+    KC_CUDA(ctx, cudaEventElapsedTime(&t, ctx->trec[i].a, ctx->trec[i].b));
+    ms[ctx->trec[i].kid] += t;
+    count[ctx->trec[i].kid] += 1;
+  }
+  ctx->trec_len = 0;
+  return KC_OK;
+}
+
+kc_status kc_read_status(kc_ctx* ctx, int* device_status) {
+  if (!ctx || !device_status) return KC_ERR_INVALID_ARG;
+  KC_CUDA(ctx, cudaMemcpyAsync(&ctx->scal_host->status, &ctx->scal->status, sizeof(int),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  KC_CUDA(ctx, cudaMemsetAsync(&ctx->scal->status, 0, sizeof(int), ctx->stream));
+  KC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *device_status = ctx->scal_host->status;
+  return KC_OK;
+}
+
+kc_status kc_last_scalars(kc_ctx* ctx, double* alpha, double* beta, double* s) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_CUDA(ctx, cudaMemcpyAsync(&ctx->scal_host->alpha, &ctx->scal->alpha, 4 * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  KC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (alpha) *alpha = ctx->scal_host->alpha;
+  if (beta) *beta = ctx->scal_host->beta;
+  if (s) *s = ctx->scal_host->s;
+  return KC_OK;
+}
+
+kc_status kc_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  if (!x || !y) return fail(ctx, KC_ERR_INVALID_ARG, "x and y must be non-NULL");
+  return launch_spmv(ctx, A, x, y, A->val_dtype);
+}
+
+kc_status dcgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  st->k = 0;
+  st->finished = 0;
+  KC_TRY(validate_state(ctx, A, st));
+  if (!r0) return fail(ctx, KC_ERR_INVALID_ARG, "r0 is NULL");
+  const size_t vbytes = (size_t)A->m * (vec_of(st) == KC_F64 ? 8 : 4);
+  if (r0 != st->w)
+    KC_CUDA(ctx, cudaMemcpyAsync(st->w, r0, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return KC_OK;
+}
+
+kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  KC_TRY(validate_state(ctx, A, st));
+  const int k = st->k;
+  if (k + 2 > st->ncap)
+    return fail(ctx, KC_ERR_INVALID_ARG, "basis full: k = %d, ncap = %d", k, st->ncap);
+  if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
+  const int vec = vec_of(st);
+  KC_TRY(launch_spmv(ctx, A, st->w, st->v, vec));                       // v = A w
+  StepArgs sa = step_args(st, k, 0);
+  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec,
+                       EPI_DCGS2, sa));                                  // one reduction
+  KC_TRY(launch_dcgs2_update(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec));
+  st->k = k + 1;
+  return KC_OK;
+}
+
+kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  KC_TRY(validate_state(ctx, A, st));
+  const int k = st->k;
+  if (k < 1) return fail(ctx, KC_ERR_INVALID_ARG, "finish needs at least one step");
+  if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
+  const int vec = vec_of(st);
+  StepArgs sa = step_args(st, k, 0);
+  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, nullptr, A->m, vec,
+                       EPI_STORE_C, sa));                                // C1 = Q^T w
+  KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec, 0));
+  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, nullptr, A->m, vec,
+                       EPI_STORE_C2, sa));                               // C2 = Q^T u
+  KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec, 1));
+  KC_TRY(launch_norm(ctx, st->w, nullptr, A->m, vec, NEPI_FINISH, sa));  // alpha = ||u||
+  KC_TRY(launch_scale_to(ctx, st->w, qcol(st, k), st->q_dtype, A->m, vec));
+  st->finished = 1;
+  return KC_OK;
+}
+
+kc_status cgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  st->k = 0;
+  st->finished = 0;
+  KC_TRY(validate_state(ctx, A, st));
+  if (st->q_dtype != KC_F64)
+    return fail(ctx, KC_ERR_INVALID_ARG, "the CGS2 / MGS baselines are FP64 only");
+  if (!r0) return fail(ctx, KC_ERR_INVALID_ARG, "r0 is NULL");
+  StepArgs sa = step_args(st, 0, 0);
+  KC_TRY(launch_norm(ctx, r0, nullptr, A->m, KC_F64, NEPI_INIT, sa));
+  KC_TRY(launch_scale_to(ctx, r0, st->Q, KC_F64, A->m, KC_F64));      // q_0 = r0/||r0||
+  st->k = 1;
+  return KC_OK;
+}
+
+kc_status cgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  KC_TRY(validate_state(ctx, A, st));
+  if (st->q_dtype != KC_F64)
+    return fail(ctx, KC_ERR_INVALID_ARG, "the CGS2 / MGS baselines are FP64 only");
+  const int k = st->k;
+  if (k < 1 || k + 1 > st->ncap)
+    return fail(ctx, KC_ERR_INVALID_ARG, "CGS2 step needs 1 <= k < ncap (k = %d)", k);
+  StepArgs sa = step_args(st, k, 0);
+  KC_TRY(launch_spmv(ctx, A, qcol(st, k - 1), st->v, KC_F64));          // v = A q_{k-1}
+  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, KC_F64, k, st->v, nullptr, A->m, KC_F64,
+                       EPI_STORE_S, sa));                                // S = Q^T v
+  KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, KC_F64, k, st->v, A->m, KC_F64, 2));
+  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, KC_F64, k, st->v, nullptr, A->m, KC_F64,
+                       EPI_STORE_C, sa));                                // C = Q^T w
+  KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, KC_F64, k, st->v, A->m, KC_F64, 0));
+  KC_TRY(launch_norm(ctx, st->v, nullptr, A->m, KC_F64, NEPI_CGS2, sa)); // alpha = ||u||
+  KC_TRY(launch_scale_to(ctx, st->v, qcol(st, k), KC_F64, A->m, KC_F64));
+  st->k = k + 1;
+  return KC_OK;
+}
+
+kc_status mgs_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  KC_TRY(validate_state(ctx, A, st));
+  if (st->q_dtype != KC_F64)
+    return fail(ctx, KC_ERR_INVALID_ARG, "the CGS2 / MGS baselines are FP64 only");
+  const int k = st->k;
+  if (k < 1 || k + 1 > st->ncap)
+    return fail(ctx, KC_ERR_INVALID_ARG, "MGS step needs 1 <= k < ncap (k = %d)", k);
+  StepArgs sa = step_args(st, k, 0);
+  KC_TRY(launch_spmv(ctx, A, qcol(st, k - 1), st->v, KC_F64));
+  for (int i = 0; i < k; i++) {
+    sa.row = i;
+    KC_TRY(launch_norm(ctx, qcol(st, i), st->v, A->m, KC_F64, NEPI_DOT, sa));  // h = q_i^T v
+    KC_TRY(launch_axpy_h(ctx, qcol(st, i), KC_F64, st->v, A->m, KC_F64));      // v -= h q_i
+  }
+  KC_TRY(launch_norm(ctx, st->v, nullptr, A->m, KC_F64, NEPI_MGS, sa));
+  KC_TRY(launch_scale_to(ctx, st->v, qcol(st, k), KC_F64, A->m, KC_F64));
+  st->k = k + 1;
+  return KC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// Internal declarations shared by the libkrylov translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdarg.h>
+
+#include "../../include/krylov.h"
+
+namespace kc {
+
+constexpr int NMAX = 128;            // largest basis (ncap) any kernel supports
+constexpr int RED_THREADS = 512;     // threads of a reduction CTA (16 warps)
+constexpr int RED_WARPS = RED_THREADS / 32;
+constexpr int UPD_THREADS = 256;
+
+// Device-resident scalars of the current step, written by the last CTA of a reduction
+// (the scalar step of Algorithm 4) and read by the update kernels.
+struct Scalars {
+  double C[NMAX];       // delayed reorthogonalisation coefficients C_{0:k-1}
+  double S[NMAX];       // projections of v (S_{0:k-1}), or a second coefficient set
+  double T[NMAX + 1];   // T_{0:k}: scaled projection (Alg. 4 lines 5-6)
+  double C2[NMAX];      // second CGS2 pass coefficients (finish / CGS2 baseline)
+  double alpha, inv_alpha, beta, s;
+  double h;             // last MGS inner product
+  double norm_sq;       // last explicit squared norm
+  int status;           // kc_status of the last numerical check (sticky until read)
+  int stop;             // drivers: set when remaining work in a captured cycle is skipped
+  int ncols;            // GMRES: columns finalised so far in the cycle
+  int pyth_fallbacks;
+  // GMRES Givens state (FP64, lagged one column behind the expansion)
+  double gc[NMAX], gs[NMAX], g[NMAX + 1];
+  double resid_est;     // |g_{j+1}| of the last rotated column
+  double rtol_abs;      // stop threshold on |g| (absolute)
+  double y[NMAX];
+};
+
+enum Epilogue : int {
+  EPI_DCGS2 = 0,        // full DCGS2 scalar step (flexible variant: see flags)
+  EPI_STORE_C = 1,      // store Q^T x into C (finish first pass, CGS2 second projection)
+  EPI_STORE_C2 = 2,     // store Q^T x into C2
+  EPI_STORE_S = 3,      // store Q^T x into S (CGS2 first projection)
+};
+
+enum NormEpilogue : int {
+  NEPI_INIT = 0,        // alpha = ||x||, inv_alpha (start of CGS2 / MGS)
+  NEPI_FINISH = 1,      // DCGS2 finish: H(:,k-1) = K + C + C2, H(k,k-1) = alpha
+  NEPI_CGS2 = 2,        // CGS2 step: H(:,j) = S + C, H(j+1,j) = alpha
+  NEPI_MGS = 3,         // MGS step: H(j+1,j) = alpha
+  NEPI_DOT = 4,         // store x.y into h and H(i,j) (MGS inner product)
+};
+
+struct StepArgs {
+  double* H;
+  int ldh;
+  double* K;
+  int ldk;
+  double* R;            // GMRES: rotated Hessenberg columns (ld ldr)
+  int ldr;
+  int k;                // final basis columns before this step
+  int row;              // MGS inner product: row index i of H(i, k-1)
+  int flags;            // bit 0: flexible (no H C / alpha correction); bit 1: GMRES Givens
+  double pyth_tol;      // relative threshold on (beta - C^T C)/beta
+};
+
+enum StepFlags : int { SF_FLEXIBLE = 1, SF_GIVENS = 2 };
+
+}  // namespace kc
+
+namespace kc {
+enum KernelId : int {
+  KID_SPMV = 0, KID_REDUCE, KID_UPDATE, KID_GEMV_SUB, KID_NORM, KID_SCALE, KID_AXPY,
+  KID_SMALL, KID_OTHER, KID_COUNT
+};
+struct TimingRec { cudaEvent_t a, b; int kid; };
+}  // namespace kc
+
+struct kc_ctx {
+  int device;
+  cudaStream_t stream;
+  int num_sms;
+  int reduce_grid;
+  double* partials;        // reduce_grid * (2*NMAX + 4) doubles
+  unsigned int* counters;  // ticket counters for last-CTA reductions
+  kc::Scalars* scal;       // device scalars
+  kc::Scalars* scal_host;  // pinned host mirror for reads
+  double* dwork;           // general FP64 device workspace (small dense solves)
+  size_t dwork_len;
+  int64_t launches;
+  // optional per-kernel timing: events recorded around every launch on ctx->stream
+  int timing_on;
+  kc::TimingRec* trec;
+  int trec_len, trec_cap;
+  char err[512];
+};
+
+namespace kc {
+
+inline kc_status fail(kc_ctx* ctx, kc_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+#define KC_CUDA(ctx, call)                                                             \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return kc::fail((ctx), KC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Timing bracket around one launch (no-op unless kc_timing_enable was called).
+void timing_begin(kc_ctx* ctx, int kid);
+void timing_end(kc_ctx* ctx);
+
+#define KC_LAUNCHED(ctx)                                                               \
+  do {                                                                                 \
+    (ctx)->launches++;                                                                 \
+    kc::timing_end(ctx);                                                               \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess)                                                             \
+      return kc::fail((ctx), KC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+// Launch helpers implemented in kc_ortho.cu, used by the drivers in kc_solvers.cu.
+kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype);
+kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
+                        const void* x, const void* y, int64_t m, int vec_dtype, int epilogue,
+                        const StepArgs& sa);
+kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, int k, void* w,
+                              const void* v, int64_t m, int vec_dtype);
+kc_status launch_gemv_sub(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k, void* x,
+                          int64_t m, int vec_dtype, int which);
+kc_status launch_norm(kc_ctx* ctx, const void* x, const void* y, int64_t m, int vec_dtype,
+                      int nepi, const StepArgs& sa);
+kc_status launch_scale_to(kc_ctx* ctx, const void* x, void* qcol, int q_dtype, int64_t m,
+                          int vec_dtype);
+kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_t m,
+                        int vec_dtype);
+kc_status validate_csr(kc_ctx* ctx, const kc_csr* A);
+kc_status validate_state(kc_ctx* ctx, const kc_csr* A, const kc_arnoldi* st);
+
+}  // namespace kc

@@ -1,0 +1,717 @@
+// Hot kernels of the DCGS2 Arnoldi step (Algorithm 4) and of the CGS2 / MGS baselines:
+//   K4' CSR SpMV, K1' fused multi-column transposed GEMV with in-launch deterministic
+//   cross-CTA reduction and the scalar step, K2' fused GEMV + axpy update, plus the
+//   projection, norm and scaling kernels of the CGS2 finish and of the baselines.
+//
+// Vector element types: FP64 (accumulate FP64) or FP32 (accumulate FP32 within a thread,
+// FP64 across warps and CTAs).  Basis element types: FP64, FP32, or BF16 (FP32 vectors).
+// Every kernel streams 16-byte groups of rows: 2 rows of FP64, 4 rows of FP32.
+#include "kc_internal.cuh"
+
+namespace kc {
+
+constexpr int PSTRIDE = 2 * NMAX + 4;   // doubles per CTA in the partials buffer
+
+// ----------------------------------------------------------------------------------------
+// element helpers
+// ----------------------------------------------------------------------------------------
+template <typename TV> struct Acc;
+template <> struct Acc<double> { using T = double; };
+template <> struct Acc<float> { using T = float; };
+
+template <typename TV> struct Grp { static constexpr int R = 16 / sizeof(TV); };
+
+// load R consecutive vector rows of group g (read-only path, cached in L1: the vectors
+// are re-read by every warp of the CTA)
+__device__ __forceinline__ void ldv(const double* p, int64_t g, double (&o)[2]) {
+  double2 t = __ldg(reinterpret_cast<const double2*>(p) + g);
+  o[0] = t.x; o[1] = t.y;
+}
+__device__ __forceinline__ void ldv(const float* p, int64_t g, float (&o)[4]) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p) + g);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+// plain (coherent) vector load: for vectors written earlier in the same kernel sequence
+__device__ __forceinline__ void ldv_cg(const double* p, int64_t g, double (&o)[2]) {
+  double2 t = __ldcg(reinterpret_cast<const double2*>(p) + g);
+  o[0] = t.x; o[1] = t.y;
+}
+__device__ __forceinline__ void ldv_cg(const float* p, int64_t g, float (&o)[4]) {
+  float4 t = __ldcg(reinterpret_cast<const float4*>(p) + g);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void stv(double* p, int64_t g, const double (&o)[2]) {
+  reinterpret_cast<double2*>(p)[g] = make_double2(o[0], o[1]);
+}
+__device__ __forceinline__ void stv(float* p, int64_t g, const float (&o)[4]) {
+  reinterpret_cast<float4*>(p)[g] = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// basis loads: streamed once per pass (evict-first)
+__device__ __forceinline__ void load_q(const double* p, int64_t g, double (&o)[2]) {
+  double2 t = __ldcs(reinterpret_cast<const double2*>(p) + g);
+  o[0] = t.x; o[1] = t.y;
+}
+__device__ __forceinline__ void load_q(const float* p, int64_t g, float (&o)[4]) {
+  float4 t = __ldcs(reinterpret_cast<const float4*>(p) + g);
+  o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ float bf2f(unsigned short b) {
+  return __uint_as_float(((unsigned int)b) << 16);
+}
+__device__ __forceinline__ void load_q(const __nv_bfloat16* p, int64_t g, float (&o)[4]) {
+  uint2 t = __ldcs(reinterpret_cast<const uint2*>(p) + g);
+  o[0] = __uint_as_float(t.x << 16);
+  o[1] = __uint_as_float(t.x & 0xffff0000u);
+  o[2] = __uint_as_float(t.y << 16);
+  o[3] = __uint_as_float(t.y & 0xffff0000u);
+}
+// round to nearest even bfloat16, returned both as bits and as the rounded float
+__device__ __forceinline__ unsigned int f2bf_bits(float f) {
+  unsigned int u = __float_as_uint(f);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return u >> 16;
+}
+__device__ __forceinline__ void store_q(double* p, int64_t g, double (&o)[2]) {
+  reinterpret_cast<double2*>(p)[g] = make_double2(o[0], o[1]);
+}
+__device__ __forceinline__ void store_q(float* p, int64_t g, float (&o)[4]) {
+  reinterpret_cast<float4*>(p)[g] = make_float4(o[0], o[1], o[2], o[3]);
+}
+// BF16 store rounds o in place, so that the caller continues with the stored values
+__device__ __forceinline__ void store_q(__nv_bfloat16* p, int64_t g, float (&o)[4]) {
+  unsigned int b0 = f2bf_bits(o[0]), b1 = f2bf_bits(o[1]), b2 = f2bf_bits(o[2]),
+               b3 = f2bf_bits(o[3]);
+  o[0] = __uint_as_float(b0 << 16); o[1] = __uint_as_float(b1 << 16);
+  o[2] = __uint_as_float(b2 << 16); o[3] = __uint_as_float(b3 << 16);
+  reinterpret_cast<uint2*>(p)[g] = make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
+}
+
+// scalar (single-row) versions for ragged tails
+__device__ __forceinline__ double ld1(const double* p, int64_t i) { return __ldcg(p + i); }
+__device__ __forceinline__ float ld1(const float* p, int64_t i) { return __ldcg(p + i); }
+__device__ __forceinline__ float ld1(const __nv_bfloat16* p, int64_t i) {
+  return bf2f(reinterpret_cast<const unsigned short*>(p)[i]);
+}
+__device__ __forceinline__ void st1(double* p, int64_t i, double& v) { p[i] = v; }
+__device__ __forceinline__ void st1(float* p, int64_t i, float& v) { p[i] = v; }
+__device__ __forceinline__ void st1(__nv_bfloat16* p, int64_t i, float& v) {
+  unsigned int b = f2bf_bits(v);
+  v = __uint_as_float(b << 16);
+  reinterpret_cast<unsigned short*>(p)[i] = (unsigned short)b;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum the per-CTA partials in a fixed order (deterministic), into tot[0:nval].
+__device__ void sum_partials(const double* __restrict__ partials, int nparts, int nval,
+                             double* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int vi = warp; vi < nval; vi += nw) {
+    double s = 0.0;
+    for (int c = lane; c < nparts; c += 32) s += __ldcg(partials + (int64_t)c * PSTRIDE + vi);
+    s = warp_sum(s);
+    if (lane == 0) tot[vi] = s;
+  }
+}
+
+// Last-CTA election: returns true in every thread of the CTA that arrives last.
+__device__ __forceinline__ bool last_cta(unsigned int* counter) {
+  __shared__ unsigned int ticket;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return false;
+  __threadfence();
+  if (threadIdx.x == 0) *counter = 0u;   // ready for the next launch on the stream
+  return true;
+}
+
+__device__ __forceinline__ void set_status(Scalars* sc, int st) {
+  if (sc->status == KC_OK) sc->status = st;
+}
+
+// GMRES: rotate the just-finalised Hessenberg column j (rows 0..j+1) with the previous
+// Givens rotations, make a new one, update g, and raise `stop` when |g_{j+1}| <= rtol_abs.
+// R (ld ldr) receives the rotated column.  Serial (one thread), O(j).
+__device__ void givens_column(Scalars* sc, const double* H, int ldh, int j, double* R,
+                              int ldr) {
+  double h[NMAX + 1];
+  for (int i = 0; i <= j + 1; i++) h[i] = H[i + (int64_t)j * ldh];
+  for (int i = 0; i < j; i++) {
+    double t = sc->gc[i] * h[i] + sc->gs[i] * h[i + 1];
+    h[i + 1] = -sc->gs[i] * h[i] + sc->gc[i] * h[i + 1];
+    h[i] = t;
+  }
+  double r = hypot(h[j], h[j + 1]);
+  double c = h[j] / r, s = h[j + 1] / r;
+  sc->gc[j] = c;
+  sc->gs[j] = s;
+  h[j] = r;
+  for (int i = 0; i <= j; i++) R[i + (int64_t)j * ldr] = h[i];
+  sc->g[j + 1] = -s * sc->g[j];
+  sc->g[j] = c * sc->g[j];
+  sc->resid_est = fabs(sc->g[j + 1]);
+  sc->ncols = j + 1;
+  if (!(sc->resid_est > sc->rtol_abs)) sc->stop = 1;
+}
+
+// ----------------------------------------------------------------------------------------
+// K4': CSR SpMV, one thread per row.
+// ----------------------------------------------------------------------------------------
+template <typename TA, typename TV>
+__global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ ci,
+                                              const TA* __restrict__ val,
+                                              const TV* __restrict__ x, TV* __restrict__ y,
+                                              int64_t m, const Scalars* __restrict__ sc) {
+  if (sc->stop) return;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int b = __ldg(rp + r), e = __ldg(rp + r + 1);
+    TA s = 0;
+    for (int j = b; j < e; j++) s += __ldg(val + j) * (TA)__ldcg(x + __ldg(ci + j));
+    y[r] = (TV)s;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// K1': fused reduction.  Tasks t = 0..k-1 are Q(:,t)^T [x, y]; task k is x^T [x, y].
+// Warp w owns tasks w, w+16, w+32, ... (TPW of them) and keeps their partial sums in
+// registers over all of the CTA's rows; the 16 warps of a CTA walk the same rows, so
+// x and y are read from HBM once and served from L1 to the other warps.
+// The last CTA to finish sums the partials in CTA order (deterministic) and runs the
+// epilogue: the scalar step of Algorithm 4 or a plain store.
+// ----------------------------------------------------------------------------------------
+template <typename TQ, typename TV, int TPW, int NRHS>
+__global__ void __launch_bounds__(RED_THREADS)
+k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
+         const TV* __restrict__ y, int64_t m, double* __restrict__ partials,
+         unsigned int* __restrict__ counter, Scalars* __restrict__ sc, int epilogue,
+         StepArgs sa) {
+  using TA = typename Acc<TV>::T;
+  constexpr int R = Grp<TV>::R;
+  if (sc->stop) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ntask = k + 1;
+  TA acc[TPW][NRHS];
+#pragma unroll
+  for (int i = 0; i < TPW; i++)
+#pragma unroll
+    for (int r = 0; r < NRHS; r++) acc[i][r] = 0;
+
+  const int64_t ngroups = m / R;
+  const int64_t g0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
+  const int64_t g1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
+  for (int64_t g = g0 + lane; g < g1; g += 32) {
+    TV xv[R], yv[R];
+    ldv(x, g, xv);
+    if (NRHS == 2) ldv(y, g, yv);
+#pragma unroll
+    for (int i = 0; i < TPW; i++) {
+      const int t = warp + RED_WARPS * i;
+      if (t < ntask) {
+        TA qv[R];
+        if (t < k) {
+          load_q(Q + (int64_t)t * ldq, g, qv);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; r++) qv[r] = xv[r];
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          acc[i][0] += qv[r] * (TA)xv[r];
+          if (NRHS == 2) acc[i][1] += qv[r] * (TA)yv[r];
+        }
+      }
+    }
+  }
+  // ragged tail: rows ngroups*R .. m-1, taken by the last CTA's warps
+  if (blockIdx.x == gridDim.x - 1) {
+    for (int64_t row = ngroups * R + lane; row < m; row += 32) {
+      TA xs = (TA)__ldcg(x + row);
+      TA ys = NRHS == 2 ? (TA)__ldcg(y + row) : (TA)0;
+#pragma unroll
+      for (int i = 0; i < TPW; i++) {
+        const int t = warp + RED_WARPS * i;
+        if (t < ntask) {
+          TA q = t < k ? (TA)ld1(Q + (int64_t)t * ldq, row) : xs;
+          acc[i][0] += q * xs;
+          if (NRHS == 2) acc[i][1] += q * ys;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TPW; i++) {
+    const int t = warp + RED_WARPS * i;
+#pragma unroll
+    for (int r = 0; r < NRHS; r++) {
+      double v = (double)warp_sum(acc[i][r]);
+      if (lane == 0 && t < ntask) partials[(int64_t)blockIdx.x * PSTRIDE + t * NRHS + r] = v;
+    }
+  }
+  if (!last_cta(counter)) return;
+
+  __shared__ double tot[PSTRIDE];
+  __shared__ double s_alpha;
+  const int nval = ntask * NRHS;
+  sum_partials(partials, gridDim.x, nval, tot);
+  __syncthreads();
+
+  if (epilogue != EPI_DCGS2) {
+    double* dst = epilogue == EPI_STORE_C ? sc->C : (epilogue == EPI_STORE_C2 ? sc->C2 : sc->S);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) dst[i] = tot[i * NRHS];
+    if (threadIdx.x == 0) {
+      sc->norm_sq = tot[k * NRHS];
+      if (!isfinite(tot[k * NRHS])) set_status(sc, KC_ERR_NONFINITE);
+    }
+    return;
+  }
+
+  // ---- scalar step of Algorithm 4 (lines 4-6 and 10-12), FP64 -------------------------
+  // tot[2i] = C_i, tot[2i+1] = S_i (i < k); tot[2k] = beta, tot[2k+1] = s
+  if (threadIdx.x == 0) {
+    double cc = 0.0, cs = 0.0;
+    for (int i = 0; i < k; i++) {
+      cc += tot[2 * i] * tot[2 * i];
+      cs += tot[2 * i] * tot[2 * i + 1];
+    }
+    const double beta = tot[2 * k], s = tot[2 * k + 1];
+    double a2 = beta - cc;                                   // Pythagoras, line 4
+    if (!isfinite(a2) || !isfinite(s)) {
+      set_status(sc, KC_ERR_NONFINITE);
+    } else if (!(a2 > sa.pyth_tol * beta)) {
+      set_status(sc, KC_ERR_PYTHAGORAS_NEG);
+      sc->pyth_fallbacks++;
+      a2 = fmax(a2, 1e-300);
+    }
+    const double alpha = sqrt(a2);
+    s_alpha = alpha;
+    sc->alpha = alpha;
+    sc->inv_alpha = 1.0 / alpha;
+    sc->beta = beta;
+    sc->s = s;
+    sc->T[k] = (s - cs) / (alpha * alpha);                 // line 5, Stephen's trick (eq. 30)
+    if ((sa.flags & SF_GIVENS) && k == 0) { sc->g[0] = alpha; sc->ncols = 0; }
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double Ci = tot[2 * i];
+    sc->C[i] = Ci;
+    sc->T[i] = tot[2 * i + 1] / alpha;                     // line 6
+    sa.H[i + (int64_t)(k - 1) * sa.ldh] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + Ci;  // line 10
+  }
+  if (threadIdx.x == 0 && k >= 1) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;     // line 12
+  __syncthreads();
+  if (threadIdx.x == 0 && k >= 1) {
+    double cn = 0.0;
+    for (int i = 0; i <= k; i++) {
+      double h = sa.H[i + (int64_t)(k - 1) * sa.ldh];
+      cn += h * h;
+    }
+    if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
+  }
+  // line 11: K(0:k, k) = T - H(0:k, 0:k-1) C / alpha   (flexible variant: K = T)
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    const double t = i < k ? tot[2 * i + 1] / alpha : sc->T[k];
+    double hc = 0.0;
+    if (!(sa.flags & SF_FLEXIBLE))
+      for (int j = 0; j < k; j++) hc += sa.H[i + (int64_t)j * sa.ldh] * tot[2 * j];
+    sa.K[i + (int64_t)k * sa.ldk] = t - hc / alpha;
+  }
+  if (threadIdx.x == 0 && (sa.flags & SF_GIVENS) && k >= 1)
+    givens_column(sc, sa.H, sa.ldh, k - 1, sa.R, sa.ldr);
+}
+
+// ----------------------------------------------------------------------------------------
+// K2': fused update of Algorithm 4 lines 7-9.
+//   u = w - Q_k C;  q_k = u / alpha -> Q(:,k);  w <- v/alpha - Q_k T(0:k) - q_k T_k
+// One pass over Q_k; C and T are staged in shared memory.
+// ----------------------------------------------------------------------------------------
+template <typename TQ, typename TV>
+__global__ void __launch_bounds__(UPD_THREADS)
+k_dcgs2_update(TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ w,
+               const TV* __restrict__ v, int64_t m, const Scalars* __restrict__ sc) {
+  using TA = typename Acc<TV>::T;
+  constexpr int R = Grp<TV>::R;
+  if (sc->stop) return;
+  __shared__ TA sC[NMAX], sT[NMAX + 1];
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    if (i < k) sC[i] = (TA)sc->C[i];
+    sT[i] = (TA)sc->T[i];
+  }
+  const TA inva = (TA)sc->inv_alpha;
+  __syncthreads();
+  TQ* qk = Q + (int64_t)k * ldq;
+  const int64_t ngroups = m / R;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    TV wv[R], vv[R];
+    ldv_cg(w, g, wv);
+    ldv_cg(v, g, vv);
+    TA u[R], wn[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) { u[r] = wv[r]; wn[r] = vv[r] * inva; }
+    int i = 0;
+    for (; i + 4 <= k; i += 4) {
+      TA q0[R], q1[R], q2[R], q3[R];
+      load_q(Q + (int64_t)(i + 0) * ldq, g, q0);
+      load_q(Q + (int64_t)(i + 1) * ldq, g, q1);
+      load_q(Q + (int64_t)(i + 2) * ldq, g, q2);
+      load_q(Q + (int64_t)(i + 3) * ldq, g, q3);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        u[r] -= q0[r] * sC[i]; wn[r] -= q0[r] * sT[i];
+        u[r] -= q1[r] * sC[i + 1]; wn[r] -= q1[r] * sT[i + 1];
+        u[r] -= q2[r] * sC[i + 2]; wn[r] -= q2[r] * sT[i + 2];
+        u[r] -= q3[r] * sC[i + 3]; wn[r] -= q3[r] * sT[i + 3];
+      }
+    }
+    for (; i < k; i++) {
+      TA q0[R];
+      load_q(Q + (int64_t)i * ldq, g, q0);
+#pragma unroll
+      for (int r = 0; r < R; r++) { u[r] -= q0[r] * sC[i]; wn[r] -= q0[r] * sT[i]; }
+    }
+    TA qn[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) qn[r] = u[r] * inva;
+    store_q(qk, g, qn);                         // (BF16: qn now holds the rounded values)
+    TV wo[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) wo[r] = (TV)(wn[r] - qn[r] * sT[k]);
+    stv(w, g, wo);
+  }
+  // ragged tail
+  if (blockIdx.x == 0) {
+    for (int64_t row = ngroups * R + threadIdx.x; row < m; row += blockDim.x) {
+      TA u = (TA)w[row], wn = (TA)v[row] * inva;
+      for (int i = 0; i < k; i++) {
+        TA q = (TA)ld1(Q + (int64_t)i * ldq, row);
+        u -= q * sC[i];
+        wn -= q * sT[i];
+      }
+      TA qn = u * inva;
+      st1(qk, row, qn);
+      w[row] = (TV)(wn - qn * sT[k]);
+    }
+  }
+}
+
+// x <- x - Q_k c, c = C (which 0), C2 (1) or S (2).  Used by CGS2 passes.
+template <typename TQ, typename TV>
+__global__ void __launch_bounds__(UPD_THREADS)
+k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int64_t m,
+           const Scalars* __restrict__ sc, int which) {
+  using TA = typename Acc<TV>::T;
+  constexpr int R = Grp<TV>::R;
+  if (sc->stop) return;
+  __shared__ TA sc_[NMAX];
+  const double* src = which == 0 ? sc->C : (which == 1 ? sc->C2 : sc->S);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sc_[i] = (TA)src[i];
+  __syncthreads();
+  const int64_t ngroups = m / R;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    TV xv[R];
+    ldv_cg(x, g, xv);
+    TA u[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) u[r] = xv[r];
+    int i = 0;
+    for (; i + 4 <= k; i += 4) {
+      TA q0[R], q1[R], q2[R], q3[R];
+      load_q(Q + (int64_t)(i + 0) * ldq, g, q0);
+      load_q(Q + (int64_t)(i + 1) * ldq, g, q1);
+      load_q(Q + (int64_t)(i + 2) * ldq, g, q2);
+      load_q(Q + (int64_t)(i + 3) * ldq, g, q3);
+#pragma unroll
+      for (int r = 0; r < R; r++)
+        u[r] -= q0[r] * sc_[i] + q1[r] * sc_[i + 1] + q2[r] * sc_[i + 2] + q3[r] * sc_[i + 3];
+    }
+    for (; i < k; i++) {
+      TA q0[R];
+      load_q(Q + (int64_t)i * ldq, g, q0);
+#pragma unroll
+      for (int r = 0; r < R; r++) u[r] -= q0[r] * sc_[i];
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) xv[r] = (TV)u[r];
+    stv(x, g, xv);
+  }
+  if (blockIdx.x == 0) {
+    for (int64_t row = ngroups * R + threadIdx.x; row < m; row += blockDim.x) {
+      TA u = (TA)x[row];
+      for (int i = 0; i < k; i++) u -= (TA)ld1(Q + (int64_t)i * ldq, row) * sc_[i];
+      x[row] = (TV)u;
+    }
+  }
+}
+
+// K3': x^T x (and x^T y) with a last-CTA epilogue (norms, MGS inner products).
+template <typename TV, int NRHS>
+__global__ void __launch_bounds__(RED_THREADS)
+k_norm(const TV* __restrict__ x, const TV* __restrict__ y, int64_t m,
+       double* __restrict__ partials, unsigned int* __restrict__ counter,
+       Scalars* __restrict__ sc, int nepi, StepArgs sa) {
+  using TA = typename Acc<TV>::T;
+  constexpr int R = Grp<TV>::R;
+  if (sc->stop) return;
+  TA a0 = 0, a1 = 0;
+  const int64_t ngroups = m / R;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    TV xv[R], yv[R];
+    ldv_cg(x, g, xv);
+    if (NRHS == 2) ldv_cg(y, g, yv);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      a0 += (TA)xv[r] * (TA)xv[r];
+      if (NRHS == 2) a1 += (TA)xv[r] * (TA)yv[r];
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1)
+    for (int64_t row = ngroups * R + threadIdx.x; row < m; row += blockDim.x) {
+      TA xs = (TA)x[row];
+      a0 += xs * xs;
+      if (NRHS == 2) a1 += xs * (TA)y[row];
+    }
+  __shared__ double red[2][RED_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double d0 = (double)warp_sum(a0), d1 = NRHS == 2 ? (double)warp_sum(a1) : 0.0;
+  if (lane == 0) { red[0][warp] = d0; red[1][warp] = d1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) { s0 += red[0][i]; s1 += red[1][i]; }
+    partials[(int64_t)blockIdx.x * PSTRIDE] = s0;
+    partials[(int64_t)blockIdx.x * PSTRIDE + 1] = s1;
+  }
+  if (!last_cta(counter)) return;
+  __shared__ double tot[2];
+  sum_partials(partials, gridDim.x, 2, tot);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double xx = tot[0], xy = tot[1];
+  const int k = sa.k;
+  sc->norm_sq = xx;
+  if (!isfinite(xx) || !isfinite(xy)) set_status(sc, KC_ERR_NONFINITE);
+  if (nepi == NEPI_DOT) {
+    sc->h = xy;
+    sa.H[sa.row + (int64_t)(k - 1) * sa.ldh] = xy;       // H(i, k-1), i = sa.row
+    return;
+  }
+  double alpha = sqrt(xx);
+  sc->alpha = alpha;
+  sc->inv_alpha = 1.0 / alpha;
+  if (nepi == NEPI_INIT) {
+    if (!(alpha > 0.0)) set_status(sc, KC_ERR_BREAKDOWN);
+    return;
+  }
+  // finalise column k-1 of H
+  double* Hc = sa.H + (int64_t)(k - 1) * sa.ldh;
+  double cn = alpha * alpha;
+  if (nepi == NEPI_FINISH) {
+    for (int i = 0; i < k; i++) {
+      Hc[i] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + sc->C[i] + sc->C2[i];
+      cn += Hc[i] * Hc[i];
+    }
+  } else if (nepi == NEPI_CGS2) {
+    for (int i = 0; i < k; i++) {
+      Hc[i] = sc->S[i] + sc->C[i];
+      cn += Hc[i] * Hc[i];
+    }
+  } else {  // MGS: the inner products are already in H
+    for (int i = 0; i < k; i++) cn += Hc[i] * Hc[i];
+  }
+  Hc[k] = alpha;
+  if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
+  if (sa.flags & SF_GIVENS) givens_column(sc, sa.H, sa.ldh, k - 1, sa.R, sa.ldr);
+}
+
+// qcol = x * inv_alpha (converted to the basis type)
+template <typename TQ, typename TV>
+__global__ void __launch_bounds__(UPD_THREADS)
+k_scale_to(const TV* __restrict__ x, TQ* __restrict__ qcol, int64_t m,
+           const Scalars* __restrict__ sc) {
+  using TA = typename Acc<TV>::T;
+  if (sc->stop) return;
+  const TA inva = (TA)sc->inv_alpha;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    TA q = (TA)__ldcg(x + r) * inva;
+    st1(qcol, r, q);
+  }
+}
+
+// v <- v - h q (MGS rank-1 projection; h read from the device scalars)
+template <typename TQ, typename TV>
+__global__ void __launch_bounds__(UPD_THREADS)
+k_axpy_h(const TQ* __restrict__ q, TV* __restrict__ v, int64_t m,
+         const Scalars* __restrict__ sc) {
+  using TA = typename Acc<TV>::T;
+  if (sc->stop) return;
+  const TA h = (TA)sc->h;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+       r += (int64_t)gridDim.x * blockDim.x)
+    v[r] = (TV)((TA)v[r] - h * (TA)ld1(q, r));
+}
+
+// ----------------------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------------------
+static int grid_for(const kc_ctx* ctx, int64_t work_items, int per_block, int max_per_sm) {
+  int64_t b = (work_items + per_block - 1) / per_block;
+  int64_t cap = (int64_t)ctx->num_sms * max_per_sm;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+static int reduce_grid_for(const kc_ctx* ctx, int64_t ngroups) {
+  // at least ~4 groups per lane before splitting across more CTAs
+  int64_t b = (ngroups + 32 * 4 - 1) / (32 * 4);
+  if (b > ctx->reduce_grid) b = ctx->reduce_grid;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype) {
+  int grid = grid_for(ctx, A->m, 256, 8);
+  if ((A->val_dtype == KC_F64) != (vec_dtype == KC_F64))
+    return fail(ctx, KC_ERR_INVALID_ARG, "spmv: matrix value type %d does not match vector type %d",
+                A->val_dtype, vec_dtype);
+  timing_begin(ctx, KID_SPMV);
+  if (A->val_dtype == KC_F64 && vec_dtype == KC_F64)
+    k_spmv<double, double><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
+        (const double*)A->val, (const double*)x, (double*)y, A->m, ctx->scal);
+  else if (A->val_dtype == KC_F32 && vec_dtype == KC_F32)
+    k_spmv<float, float><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
+        (const float*)A->val, (const float*)x, (float*)y, A->m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+template <typename TQ, typename TV, int NRHS>
+static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int k,
+                            const TV* x, const TV* y, int64_t m, int epi, const StepArgs& sa) {
+  const int ntask = k + 1;
+  auto args = [&](auto kern) {
+    kern<<<grid, RED_THREADS, 0, ctx->stream>>>(Q, ldq, k, x, y, m, ctx->partials,
+                                                ctx->counters, ctx->scal, epi, sa);
+  };
+  if (ntask <= RED_WARPS) args(k_reduce<TQ, TV, 1, NRHS>);
+  else if (ntask <= 2 * RED_WARPS) args(k_reduce<TQ, TV, 2, NRHS>);
+  else if (ntask <= 4 * RED_WARPS) args(k_reduce<TQ, TV, 4, NRHS>);
+  else args(k_reduce<TQ, TV, 8, NRHS>);
+}
+
+kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
+                        const void* x, const void* y, int64_t m, int vec_dtype, int epilogue,
+                        const StepArgs& sa) {
+  if (k + 1 > NMAX) return fail(ctx, KC_ERR_INVALID_ARG, "reduce: k = %d too large", k);
+  const int R = vec_dtype == KC_F64 ? 2 : 4;
+  const int grid = reduce_grid_for(ctx, m / R);
+  const bool two = y != nullptr;
+  const bool ok = (q_dtype == KC_F64 && vec_dtype == KC_F64) ||
+                  (q_dtype != KC_F64 && vec_dtype == KC_F32);
+  if (!ok)
+    return fail(ctx, KC_ERR_INVALID_ARG, "reduce: unsupported basis/vector types %d/%d", q_dtype, vec_dtype);
+  timing_begin(ctx, KID_REDUCE);
+  if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
+    if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
+    else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);
+  } else if (q_dtype == KC_F32 && vec_dtype == KC_F32) {
+    if (two) reduce_dispatch<float, float, 2>(ctx, grid, (const float*)Q, ldq, k, (const float*)x, (const float*)y, m, epilogue, sa);
+    else reduce_dispatch<float, float, 1>(ctx, grid, (const float*)Q, ldq, k, (const float*)x, nullptr, m, epilogue, sa);
+  } else {
+    if (two) reduce_dispatch<__nv_bfloat16, float, 2>(ctx, grid, (const __nv_bfloat16*)Q, ldq, k, (const float*)x, (const float*)y, m, epilogue, sa);
+    else reduce_dispatch<__nv_bfloat16, float, 1>(ctx, grid, (const __nv_bfloat16*)Q, ldq, k, (const float*)x, nullptr, m, epilogue, sa);
+  }
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, int k, void* w,
+                              const void* v, int64_t m, int vec_dtype) {
+  const int R = vec_dtype == KC_F64 ? 2 : 4;
+  const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
+  timing_begin(ctx, KID_UPDATE);
+  if (q_dtype == KC_F64)
+    k_dcgs2_update<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
+  else if (q_dtype == KC_F32)
+    k_dcgs2_update<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((float*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
+  else
+    k_dcgs2_update<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((__nv_bfloat16*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_gemv_sub(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k, void* x,
+                          int64_t m, int vec_dtype, int which) {
+  const int R = vec_dtype == KC_F64 ? 2 : 4;
+  const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
+  timing_begin(ctx, KID_GEMV_SUB);
+  if (q_dtype == KC_F64)
+    k_gemv_sub<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((const double*)Q, ldq, k, (double*)x, m, ctx->scal, which);
+  else if (q_dtype == KC_F32)
+    k_gemv_sub<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)Q, ldq, k, (float*)x, m, ctx->scal, which);
+  else
+    k_gemv_sub<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const __nv_bfloat16*)Q, ldq, k, (float*)x, m, ctx->scal, which);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_norm(kc_ctx* ctx, const void* x, const void* y, int64_t m, int vec_dtype,
+                      int nepi, const StepArgs& sa) {
+  const int R = vec_dtype == KC_F64 ? 2 : 4;
+  const int grid = grid_for(ctx, m / R, RED_THREADS * 4, 2);
+  timing_begin(ctx, KID_NORM);
+  if (vec_dtype == KC_F64) {
+    if (y) k_norm<double, 2><<<grid, RED_THREADS, 0, ctx->stream>>>((const double*)x, (const double*)y, m, ctx->partials, ctx->counters + 1, ctx->scal, nepi, sa);
+    else k_norm<double, 1><<<grid, RED_THREADS, 0, ctx->stream>>>((const double*)x, nullptr, m, ctx->partials, ctx->counters + 1, ctx->scal, nepi, sa);
+  } else {
+    if (y) k_norm<float, 2><<<grid, RED_THREADS, 0, ctx->stream>>>((const float*)x, (const float*)y, m, ctx->partials, ctx->counters + 1, ctx->scal, nepi, sa);
+    else k_norm<float, 1><<<grid, RED_THREADS, 0, ctx->stream>>>((const float*)x, nullptr, m, ctx->partials, ctx->counters + 1, ctx->scal, nepi, sa);
+  }
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_scale_to(kc_ctx* ctx, const void* x, void* qcol, int q_dtype, int64_t m,
+                          int vec_dtype) {
+  const int grid = grid_for(ctx, m, UPD_THREADS, 8);
+  timing_begin(ctx, KID_SCALE);
+  if (q_dtype == KC_F64 && vec_dtype == KC_F64)
+    k_scale_to<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((const double*)x, (double*)qcol, m, ctx->scal);
+  else if (q_dtype == KC_F32)
+    k_scale_to<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)x, (float*)qcol, m, ctx->scal);
+  else
+    k_scale_to<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)x, (__nv_bfloat16*)qcol, m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_t m,
+                        int vec_dtype) {
+  const int grid = grid_for(ctx, m, UPD_THREADS, 8);
+  timing_begin(ctx, KID_AXPY);
+  if (q_dtype == KC_F64)
+    k_axpy_h<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((const double*)q, (double*)v, m, ctx->scal);
+  else if (q_dtype == KC_F32)
+    k_axpy_h<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)q, (float*)v, m, ctx->scal);
+  else
+    k_axpy_h<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const __nv_bfloat16*)q, (float*)v, m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+}  // namespace kc
