@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--n", type=int, default=50, help="Arnoldi steps per expansion")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-check", action="store_true",
+                   help="skip the loss-of-orthogonality / Arnoldi-relation check")
     return p.parse_args()
 
 
@@ -154,6 +156,22 @@ def cpu_oracle_sample(n, N_sample=126, seed=1002):
     orc.dcgs2_arnoldi(A, r0, n)
     dt = time.perf_counter() - t0
     return n / dt, dt, Ah.m
+
+
+def quality(kc, ctx, A, st, m, n):
+    """||I - Q^T Q||_F and ||A Q_n - Q_{n+1} H||_F / ||A||_F of the last expansion
+    (check only; uses torch matmuls outside the timed region)."""
+    import torch
+    Qv = st.Qbuf[:n + 1, :m]
+    G = Qv @ Qv.T
+    loo = float(torch.linalg.norm(torch.eye(n + 1, device="cuda", dtype=torch.float64) - G))
+    H = st.Hbuf[:n, :n + 1].T.contiguous()
+    AQ = torch.empty(n, m, dtype=torch.float64, device="cuda")
+    for j in range(n):
+        kc.kc_spmv(ctx, A, Qv[j], AQ[j])
+    R = AQ - (H.T @ Qv)
+    rre = float(torch.linalg.norm(R)) / float(torch.linalg.norm(A.val))
+    return loo, rre
 
 
 def blas_threads():
@@ -265,18 +283,11 @@ def main():
     gbs = total_bytes / (ms_per / 1e3) / 1e9
 
     # quality of the last expansion: loss of orthogonality and Arnoldi relation
-    Qv = st.Qbuf[:n + 1, :m]
-    G = Qv.double() @ Qv.double().T
-    loo = float(torch.linalg.norm(torch.eye(n + 1, device="cuda", dtype=torch.float64) - G))
-    H = st.Hbuf[:n, :n + 1].T.contiguous()
-    AQ = torch.empty(n, m, dtype=torch.float64, device="cuda")
-    for j in range(n):
-        kc.kc_spmv(ctx, A, Qv[j], AQ[j])
-    R = AQ - (H.T @ Qv)
-    normA = float(torch.linalg.norm(A.val))
-    rre = float(torch.linalg.norm(R)) / normA
-    del AQ, R, G
+    loo = rre = None
+    if not args.no_check:
+        loo, rre = quality(kc, ctx, A, st, m, n)
 
+    # dominant kernel roofline (FP64 pipe bound: 2 DFMA per basis element)
     # dominant kernel roofline (FP64 pipe bound: 2 DFMA per basis element)
     red_ms, red_cnt = kern.get("reduce", (0.0, 0))
     upd_ms, upd_cnt = kern.get("dcgs2_update", (0.0, 0))

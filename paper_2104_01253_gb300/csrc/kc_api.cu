@@ -147,6 +147,7 @@ kc_status kc_destroy(kc_ctx* ctx) {
   if (ctx->scal) cudaFree(ctx->scal);
   if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
   if (ctx->dwork) cudaFree(ctx->dwork);
+  if (ctx->ws) cudaFree(ctx->ws);
   delete ctx;
   return KC_OK;
 }
@@ -240,9 +241,11 @@ kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
   if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
   const int vec = vec_of(st);
   KC_TRY(launch_spmv(ctx, A, st->w, st->v, vec));                       // v = A w
-  StepArgs sa = step_args(st, k, 0);
+  StepArgs sa = step_args(st, k, vec == KC_F32 ? SF_FALLBACK : 0);
   KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec,
                        EPI_DCGS2, sa));                                  // one reduction
+  if (vec == KC_F32)   // reduced precision: explicit norm when Pythagoras lost its digits
+    KC_TRY(launch_fallback_norm(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, sa));
   KC_TRY(launch_dcgs2_update(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec));
   st->k = k + 1;
   return KC_OK;

@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <stdio.h>
 #include <stdarg.h>
+#include <string.h>
+#include <math.h>
 
 #include "../../include/krylov.h"
 
@@ -24,12 +26,14 @@ struct Scalars {
   double T[NMAX + 1];   // T_{0:k}: scaled projection (Alg. 4 lines 5-6)
   double C2[NMAX];      // second CGS2 pass coefficients (finish / CGS2 baseline)
   double alpha, inv_alpha, beta, s;
+  double cs;            // C^T S (Stephen's trick)
   double h;             // last MGS inner product
   double norm_sq;       // last explicit squared norm
   int status;           // kc_status of the last numerical check (sticky until read)
   int stop;             // drivers: set when remaining work in a captured cycle is skipped
   int ncols;            // GMRES: columns finalised so far in the cycle
   int pyth_fallbacks;
+  int fallback;         // set when the explicit-norm pass must supply alpha
   // GMRES Givens state (FP64, lagged one column behind the expansion)
   double gc[NMAX], gs[NMAX], g[NMAX + 1];
   double resid_est;     // |g_{j+1}| of the last rotated column
@@ -65,7 +69,7 @@ struct StepArgs {
   double pyth_tol;      // relative threshold on (beta - C^T C)/beta
 };
 
-enum StepFlags : int { SF_FLEXIBLE = 1, SF_GIVENS = 2 };
+enum StepFlags : int { SF_FLEXIBLE = 1, SF_GIVENS = 2, SF_FALLBACK = 4 };
 
 }  // namespace kc
 
@@ -88,6 +92,8 @@ struct kc_ctx {
   kc::Scalars* scal_host;  // pinned host mirror for reads
   double* dwork;           // general FP64 device workspace (small dense solves)
   size_t dwork_len;
+  void* ws;                // solver workspace (basis, vectors), grown on demand
+  size_t ws_len;
   int64_t launches;
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
@@ -137,12 +143,15 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
                               const void* v, int64_t m, int vec_dtype);
 kc_status launch_gemv_sub(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k, void* x,
                           int64_t m, int vec_dtype, int which);
+kc_status launch_fallback_norm(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
+                               const void* w, int64_t m, const StepArgs& sa);
 kc_status launch_norm(kc_ctx* ctx, const void* x, const void* y, int64_t m, int vec_dtype,
                       int nepi, const StepArgs& sa);
 kc_status launch_scale_to(kc_ctx* ctx, const void* x, void* qcol, int q_dtype, int64_t m,
                           int vec_dtype);
 kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_t m,
                         int vec_dtype);
+kc_status ensure_workspace(kc_ctx* ctx, size_t bytes);
 kc_status validate_csr(kc_ctx* ctx, const kc_csr* A);
 kc_status validate_state(kc_ctx* ctx, const kc_csr* A, const kc_arnoldi* st);
 

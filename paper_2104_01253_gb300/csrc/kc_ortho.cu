@@ -162,6 +162,43 @@ __device__ void givens_column(Scalars* sc, const double* H, int ldh, int j, doub
   if (!(sc->resid_est > sc->rtol_abs)) sc->stop = 1;
 }
 
+// The scalar step of Algorithm 4 after alpha is known (all threads of one CTA).
+// Inputs in sc: C (C_{0:k-1}), S (raw S_{0:k-1} = Q_k^T v), s (= w^T v), cs (= C^T S).
+//   T_{0:k-1} = S/alpha (line 6), T_k = (s - C^T S)/alpha^2 (line 5, eq. 30);
+//   H(0:k, k-1) = K(0:k, k-1) + C (line 10), H(k, k-1) = alpha (line 12);
+//   K(0:k, k) = T - H(0:k, 0:k-1) C / alpha (line 11; the flexible variant keeps K = T);
+//   GMRES: Givens rotation of the finalised column k-1.
+__device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha) {
+  if (threadIdx.x == 0) {
+    sc->alpha = alpha;
+    sc->inv_alpha = 1.0 / alpha;
+    sc->T[k] = (sc->s - sc->cs) / (alpha * alpha);
+    if ((sa.flags & SF_GIVENS) && k == 0) { sc->g[0] = alpha; sc->ncols = 0; }
+    if (k >= 1) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    sc->T[i] = sc->S[i] / alpha;
+    sa.H[i + (int64_t)(k - 1) * sa.ldh] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + sc->C[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && k >= 1) {
+    double cn = 0.0;
+    for (int i = 0; i <= k; i++) {
+      double h = sa.H[i + (int64_t)(k - 1) * sa.ldh];
+      cn += h * h;
+    }
+    if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
+  }
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    double hc = 0.0;
+    if (!(sa.flags & SF_FLEXIBLE))
+      for (int j = 0; j < k; j++) hc += sa.H[i + (int64_t)j * sa.ldh] * sc->C[j];
+    sa.K[i + (int64_t)k * sa.ldk] = sc->T[i] - hc / alpha;
+  }
+  if (threadIdx.x == 0 && (sa.flags & SF_GIVENS) && k >= 1)
+    givens_column(sc, sa.H, sa.ldh, k - 1, sa.R, sa.ldr);
+}
+
 // ----------------------------------------------------------------------------------------
 // K4': CSR SpMV, one thread per row.
 // ----------------------------------------------------------------------------------------
@@ -277,6 +314,11 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
 
   // ---- scalar step of Algorithm 4 (lines 4-6 and 10-12), FP64 -------------------------
   // tot[2i] = C_i, tot[2i+1] = S_i (i < k); tot[2k] = beta, tot[2k+1] = s
+  __shared__ int s_ok;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    sc->C[i] = tot[2 * i];
+    sc->S[i] = tot[2 * i + 1];
+  }
   if (threadIdx.x == 0) {
     double cc = 0.0, cs = 0.0;
     for (int i = 0; i < k; i++) {
@@ -285,50 +327,25 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
     }
     const double beta = tot[2 * k], s = tot[2 * k + 1];
     double a2 = beta - cc;                                   // Pythagoras, line 4
+    sc->beta = beta;
+    sc->s = s;
+    sc->cs = cs;
+    s_ok = 1;
     if (!isfinite(a2) || !isfinite(s)) {
       set_status(sc, KC_ERR_NONFINITE);
     } else if (!(a2 > sa.pyth_tol * beta)) {
-      set_status(sc, KC_ERR_PYTHAGORAS_NEG);
-      sc->pyth_fallbacks++;
-      a2 = fmax(a2, 1e-300);
+      if (sa.flags & SF_FALLBACK) {
+        sc->fallback = 1;                                    // explicit norm pass follows
+        s_ok = 0;
+      } else {
+        set_status(sc, KC_ERR_PYTHAGORAS_NEG);
+        a2 = fmax(a2, 1e-300);
+      }
     }
-    const double alpha = sqrt(a2);
-    s_alpha = alpha;
-    sc->alpha = alpha;
-    sc->inv_alpha = 1.0 / alpha;
-    sc->beta = beta;
-    sc->s = s;
-    sc->T[k] = (s - cs) / (alpha * alpha);                 // line 5, Stephen's trick (eq. 30)
-    if ((sa.flags & SF_GIVENS) && k == 0) { sc->g[0] = alpha; sc->ncols = 0; }
+    s_alpha = sqrt(a2);
   }
   __syncthreads();
-  const double alpha = s_alpha;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double Ci = tot[2 * i];
-    sc->C[i] = Ci;
-    sc->T[i] = tot[2 * i + 1] / alpha;                     // line 6
-    sa.H[i + (int64_t)(k - 1) * sa.ldh] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + Ci;  // line 10
-  }
-  if (threadIdx.x == 0 && k >= 1) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;     // line 12
-  __syncthreads();
-  if (threadIdx.x == 0 && k >= 1) {
-    double cn = 0.0;
-    for (int i = 0; i <= k; i++) {
-      double h = sa.H[i + (int64_t)(k - 1) * sa.ldh];
-      cn += h * h;
-    }
-    if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
-  }
-  // line 11: K(0:k, k) = T - H(0:k, 0:k-1) C / alpha   (flexible variant: K = T)
-  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
-    const double t = i < k ? tot[2 * i + 1] / alpha : sc->T[k];
-    double hc = 0.0;
-    if (!(sa.flags & SF_FLEXIBLE))
-      for (int j = 0; j < k; j++) hc += sa.H[i + (int64_t)j * sa.ldh] * tot[2 * j];
-    sa.K[i + (int64_t)k * sa.ldk] = t - hc / alpha;
-  }
-  if (threadIdx.x == 0 && (sa.flags & SF_GIVENS) && k >= 1)
-    givens_column(sc, sa.H, sa.ldh, k - 1, sa.R, sa.ldr);
+  if (s_ok) scalar_step(sc, sa, k, s_alpha);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -454,6 +471,68 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
       x[row] = (TV)u;
     }
   }
+}
+
+// Explicit-norm fallback of the delayed normalisation: when the epilogue found
+// beta - C^T C too small to trust (reduced precision), alpha = ||w - Q_k C|| is computed
+// by one more pass and the scalar step runs here.  Returns at once otherwise.
+template <typename TQ, typename TV>
+__global__ void __launch_bounds__(UPD_THREADS)
+k_fallback_norm(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ w,
+                int64_t m, double* __restrict__ partials, unsigned int* __restrict__ counter,
+                Scalars* __restrict__ sc, StepArgs sa) {
+  using TA = typename Acc<TV>::T;
+  constexpr int R = Grp<TV>::R;
+  if (sc->stop || !sc->fallback) return;
+  __shared__ TA sc_[NMAX];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sc_[i] = (TA)sc->C[i];
+  __syncthreads();
+  double acc = 0.0;
+  const int64_t ngroups = m / R;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    TV xv[R];
+    ldv_cg(w, g, xv);
+    TA u[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) u[r] = xv[r];
+    for (int i = 0; i < k; i++) {
+      TA q0[R];
+      load_q(Q + (int64_t)i * ldq, g, q0);
+#pragma unroll
+      for (int r = 0; r < R; r++) u[r] -= q0[r] * sc_[i];
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) acc += (double)u[r] * (double)u[r];
+  }
+  if (blockIdx.x == 0)
+    for (int64_t row = ngroups * R + threadIdx.x; row < m; row += blockDim.x) {
+      TA u = (TA)w[row];
+      for (int i = 0; i < k; i++) u -= (TA)ld1(Q + (int64_t)i * ldq, row) * sc_[i];
+      acc += (double)u * (double)u;
+    }
+  __shared__ double red[UPD_THREADS / 32];
+  double v = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0;
+    for (int i = 0; i < UPD_THREADS / 32; i++) s0 += red[i];
+    partials[(int64_t)blockIdx.x * PSTRIDE] = s0;
+  }
+  if (!last_cta(counter)) return;
+  __shared__ double tot[1];
+  __shared__ double s_alpha;
+  sum_partials(partials, gridDim.x, 1, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_alpha = sqrt(tot[0]);
+    sc->fallback = 0;
+    sc->pyth_fallbacks++;
+    if (!(s_alpha > 0.0)) set_status(sc, KC_ERR_BREAKDOWN);
+  }
+  __syncthreads();
+  scalar_step(sc, sa, k, s_alpha);
 }
 
 // K3': x^T x (and x^T y) with a last-CTA epilogue (norms, MGS inner products).
@@ -666,6 +745,20 @@ kc_status launch_gemv_sub(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, 
     k_gemv_sub<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)Q, ldq, k, (float*)x, m, ctx->scal, which);
   else
     k_gemv_sub<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const __nv_bfloat16*)Q, ldq, k, (float*)x, m, ctx->scal, which);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_fallback_norm(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
+                               const void* w, int64_t m, const StepArgs& sa) {
+  const int grid = grid_for(ctx, m / 4, UPD_THREADS, 2);
+  timing_begin(ctx, KID_NORM);
+  if (q_dtype == KC_F32)
+    k_fallback_norm<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)Q, ldq, k, (const float*)w, m, ctx->partials, ctx->counters + 2, ctx->scal, sa);
+  else if (q_dtype == KC_BF16)
+    k_fallback_norm<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const __nv_bfloat16*)Q, ldq, k, (const float*)w, m, ctx->partials, ctx->counters + 2, ctx->scal, sa);
+  else
+    k_fallback_norm<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)w, m, ctx->partials, ctx->counters + 2, ctx->scal, sa);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }

@@ -161,6 +161,7 @@ def test_invalid_arguments_are_rejected(kc, ctx):
     st = kc.ArnoldiState(Ah.m, 3, kc.KC_F64)
     kc.dcgs2_arnoldi_init(ctx, A, st, torch.as_tensor(gaussian_vector(Ah.m, 1), device="cuda"))
     kc.dcgs2_arnoldi_step(ctx, A, st)
+    kc.dcgs2_arnoldi_step(ctx, A, st)              # k = 2: the finish still has column 2
     with pytest.raises(kc.KrylovError):            # basis full: k + 2 > ncap
         kc.dcgs2_arnoldi_step(ctx, A, st)
     bad = kc.ArnoldiState(Ah.m, 3, kc.KC_F64)

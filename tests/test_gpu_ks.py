@@ -1,0 +1,91 @@
+"""GPU parity of krylov_schur_eigs (DCGS2 expansion + FP64 dense Schur step on the GPU)
+against the oracle and against dense eigenvalues."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.krylov_schur import krylov_schur as orc_ks  # noqa: E402
+from synth import config3_operator, convdiff_csr, gaussian_vector, manteuffel_csr  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def kc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2104_01253_gb300 as kc
+    return kc
+
+
+@pytest.fixture(scope="module")
+def ctx(kc):
+    return kc.Context(0)
+
+
+def _match(a, b):
+    """Largest relative distance between two eigenvalue lists matched greedily."""
+    b = list(b)
+    worst = 0.0
+    for z in a:
+        j = int(np.argmin([abs(z - w) for w in b]))
+        worst = max(worst, abs(z - b[j]) / max(abs(b[j]), 1e-300))
+        b.pop(j)
+    return worst
+
+
+def test_ks_small_copy_matches_dense_and_oracle(kc, ctx):
+    """Config-3 family on a 40 x 40 grid: 10 largest-real-part eigenvalues."""
+    Ah = config3_operator(40)
+    v0 = gaussian_vector(Ah.m, 7)
+    A = kc.DeviceCSR(Ah)
+    res = kc.krylov_schur_eigs(ctx, A, torch.as_tensor(v0, device="cuda"), nev=10, ncv=40,
+                               nkeep=20, tol=1e-10)
+    assert res["status"] == 0 and res["nconv"] == 10
+    ev = np.linalg.eigvals(Ah.to_scipy().toarray())
+    ev = ev[np.argsort(-ev.real)][:10]
+    assert _match(res["eigs"], ev) < 1e-9
+    ro = orc_ks(Ah.to_scipy(), v0, nev=10, ncv=40, nkeep=20, tol=1e-10)
+    assert _match(res["eigs"], ro["eigs"]) < 1e-9
+    assert np.all(res["resid"] <= 1e-10 * np.abs(res["eigs"]))
+
+
+def test_ks_manteuffel_closed_form(kc, ctx):
+    """Distinct largest Manteuffel eigenvalues from the closed form (Section 5.1)."""
+    k, beta = 20, 0.5
+    Ah = manteuffel_csr(k, beta)
+    v0 = gaussian_vector(Ah.m, 8)
+    A = kc.DeviceCSR(Ah)
+    res = kc.krylov_schur_eigs(ctx, A, torch.as_tensor(v0, device="cuda"), nev=4, ncv=30,
+                               nkeep=15, tol=1e-10)
+    assert res["nconv"] == 4
+    L = k + 1
+    exact = sorted({round(2 * (2 - np.sqrt(1 - (beta / 2) ** 2) *
+                                (np.cos(l * np.pi / L) + np.cos(j * np.pi / L))), 12)
+                    for l in range(1, k + 1) for j in range(1, k + 1)}, reverse=True)[:4]
+    got = np.sort(res["eigs"].real)[::-1]
+    assert np.abs(got - np.array(exact)).max() < 1e-7
+
+
+def test_ks_complex_spectrum(kc, ctx):
+    """A strongly convective operator with complex Ritz values: conjugate pairs are kept
+    together at the truncation and the eigenvalues match dense LAPACK."""
+    Ah = convdiff_csr(30, 2, [300.0, -200.0])
+    A = Ah.to_scipy().toarray()
+    # make it non-normal with complex eigenvalues: add a rotation coupling
+    rng = np.random.default_rng(3)
+    import scipy.sparse as sp
+    from synth import CSR
+    M = sp.csr_matrix(A) + sp.random(900, 900, density=0.01, random_state=rng, format="csr") * 5.0
+    M = M.tocsr()
+    M.sort_indices()
+    Mh = CSR(900, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+    Md = kc.DeviceCSR(Mh)
+    v0 = gaussian_vector(900, 9)
+    res = kc.krylov_schur_eigs(ctx, Md, torch.as_tensor(v0, device="cuda"), nev=6, ncv=30,
+                               nkeep=14, tol=1e-10, maxrestarts=2000)
+    assert res["nconv"] == 6
+    ev = np.linalg.eigvals(M.toarray())
+    order = sorted(range(len(ev)), key=lambda i: (-ev[i].real, -ev[i].imag))
+    ev = ev[order][:6]
+    assert _match(res["eigs"], ev) < 1e-8
