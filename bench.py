@@ -288,7 +288,6 @@ def main():
         loo, rre = quality(kc, ctx, A, st, m, n)
 
     # dominant kernel roofline (FP64 pipe bound: 2 DFMA per basis element)
-    # dominant kernel roofline (FP64 pipe bound: 2 DFMA per basis element)
     red_ms, red_cnt = kern.get("reduce", (0.0, 0))
     upd_ms, upd_cnt = kern.get("dcgs2_update", (0.0, 0))
     flops_red = fp64_flops_reduce(m, n) * args.steps

@@ -93,6 +93,16 @@ kc_status kc_destroy(kc_ctx* ctx);
 kc_status kc_set_stream(kc_ctx* ctx, void* cuda_stream);
 /* Message of the last failed call on this context (static storage inside ctx). */
 const char* kc_last_error(const kc_ctx* ctx);
+/* FP64 arithmetic mode of the DCGS2 step (default 1).
+ *  0: every product of the two basis passes in FP64 FMAs.
+ *  1: FP64 with offload: C = Q^T w and the projection v/alpha - Q T stay in FP64; the
+ *     first-projection coefficients S = Q^T v and the product Q C use float-float
+ *     arithmetic (about 2^-44 relative) on the FP32/INT pipes.  An error d in S is
+ *     removed by the next step's delayed reorthogonalisation (it returns as -d/alpha in
+ *     the next C and cancels in H = K + C, Section 4), and Q C is scaled by the tiny C,
+ *     so Q and H keep FP64 accuracy while half of the FP64 FMAs leave the FP64 pipe. */
+kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode);
+int kc_get_fp64_mode(const kc_ctx* ctx);
 /* Number of SMs and the persistent grid size used for reductions. */
 kc_status kc_device_info(const kc_ctx* ctx, int* num_sms, int* reduce_grid);
 /* Number of kernels this context has launched since creation (host-side counter). */

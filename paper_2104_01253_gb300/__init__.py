@@ -48,6 +48,14 @@ class Context:
     def check(self, status):
         return _lib.check(self.handle, status)
 
+    def set_fp64_mode(self, mode: int):
+        """0: all FP64 products; 1: FP64 with float-float offload (default)."""
+        self.check(self.lib.kc_set_fp64_mode(self.handle, mode))
+
+    @property
+    def fp64_mode(self) -> int:
+        return int(self.lib.kc_get_fp64_mode(self.handle))
+
     def set_stream(self, stream):
         self.stream = stream
         self.check(self.lib.kc_set_stream(self.handle, C.c_void_p(stream.cuda_stream)))

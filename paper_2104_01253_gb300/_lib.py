@@ -54,6 +54,8 @@ _SIGS = {
     "kc_create": ([C.POINTER(C.c_void_p), C.c_int, _P], C.c_int),
     "kc_destroy": ([_P], C.c_int),
     "kc_set_stream": ([_P, _P], C.c_int),
+    "kc_set_fp64_mode": ([_P, C.c_int], C.c_int),
+    "kc_get_fp64_mode": ([_P], C.c_int),
     "kc_last_error": ([_P], C.c_char_p),
     "kc_device_info": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "kc_launch_count": ([_P], C.c_int64),

@@ -116,6 +116,7 @@ kc_status kc_create(kc_ctx** out, int device, void* cuda_stream) {
   cudaDeviceProp p;
   if (cudaGetDeviceProperties(&p, device) != cudaSuccess) { delete ctx; return KC_ERR_CUDA; }
   ctx->num_sms = p.multiProcessorCount;
+  ctx->fp64_mode = 1;
   ctx->reduce_grid = 2 * p.multiProcessorCount;
   const size_t plen = (size_t)ctx->reduce_grid * (2 * NMAX + 4) * sizeof(double);
   bool ok = cudaMalloc(&ctx->partials, plen) == cudaSuccess &&
@@ -151,6 +152,14 @@ kc_status kc_destroy(kc_ctx* ctx) {
   delete ctx;
   return KC_OK;
 }
+
+kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 1) return KC_ERR_INVALID_ARG;
+  ctx->fp64_mode = mode;
+  return KC_OK;
+}
+
+int kc_get_fp64_mode(const kc_ctx* ctx) { return ctx ? ctx->fp64_mode : -1; }
 
 kc_status kc_set_stream(kc_ctx* ctx, void* cuda_stream) {
   if (!ctx) return KC_ERR_INVALID_ARG;

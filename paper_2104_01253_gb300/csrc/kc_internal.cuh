@@ -95,6 +95,7 @@ struct kc_ctx {
   void* ws;                // solver workspace (basis, vectors), grown on demand
   size_t ws_len;
   int64_t launches;
+  int fp64_mode;           // 0: every product in FP64; 1: FP64 with float-float offload
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
   kc::TimingRec* trec;

@@ -218,6 +218,62 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rp,
   }
 }
 
+// Last CTA of a reduction: deterministic sum of the per-CTA partials, then either a plain
+// store of Q^T x or the scalar step of Algorithm 4 (lines 4-6, 10-12).
+__device__ void reduce_epilogue(const double* __restrict__ partials, int k, int NRHS,
+                                Scalars* __restrict__ sc, int epilogue, const StepArgs& sa) {
+  __shared__ double tot[PSTRIDE];
+  __shared__ double s_alpha;
+  const int nval = (k + 1) * NRHS;
+  sum_partials(partials, gridDim.x, nval, tot);
+  __syncthreads();
+
+  if (epilogue != EPI_DCGS2) {
+    double* dst = epilogue == EPI_STORE_C ? sc->C : (epilogue == EPI_STORE_C2 ? sc->C2 : sc->S);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) dst[i] = tot[i * NRHS];
+    if (threadIdx.x == 0) {
+      sc->norm_sq = tot[k * NRHS];
+      if (!isfinite(tot[k * NRHS])) set_status(sc, KC_ERR_NONFINITE);
+    }
+    return;
+  }
+
+  // ---- scalar step of Algorithm 4 (lines 4-6 and 10-12), FP64 -------------------------
+  // tot[2i] = C_i, tot[2i+1] = S_i (i < k); tot[2k] = beta, tot[2k+1] = s
+  __shared__ int s_ok;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    sc->C[i] = tot[2 * i];
+    sc->S[i] = tot[2 * i + 1];
+  }
+  if (threadIdx.x == 0) {
+    double cc = 0.0, cs = 0.0;
+    for (int i = 0; i < k; i++) {
+      cc += tot[2 * i] * tot[2 * i];
+      cs += tot[2 * i] * tot[2 * i + 1];
+    }
+    const double beta = tot[2 * k], s = tot[2 * k + 1];
+    double a2 = beta - cc;                                   // Pythagoras, line 4
+    sc->beta = beta;
+    sc->s = s;
+    sc->cs = cs;
+    s_ok = 1;
+    if (!isfinite(a2) || !isfinite(s)) {
+      set_status(sc, KC_ERR_NONFINITE);
+    } else if (!(a2 > sa.pyth_tol * beta)) {
+      if (sa.flags & SF_FALLBACK) {
+        sc->fallback = 1;                                    // explicit norm pass follows
+        s_ok = 0;
+      } else {
+        set_status(sc, KC_ERR_PYTHAGORAS_NEG);
+        a2 = fmax(a2, 1e-300);
+      }
+    }
+    s_alpha = sqrt(a2);
+  }
+  __syncthreads();
+  if (s_ok) scalar_step(sc, sa, k, s_alpha);
+}
+
 // ----------------------------------------------------------------------------------------
 // K1': fused reduction.  Tasks t = 0..k-1 are Q(:,t)^T [x, y]; task k is x^T [x, y].
 // Warp w owns tasks w, w+16, w+32, ... (TPW of them) and keeps their partial sums in
@@ -295,57 +351,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
     }
   }
   if (!last_cta(counter)) return;
-
-  __shared__ double tot[PSTRIDE];
-  __shared__ double s_alpha;
-  const int nval = ntask * NRHS;
-  sum_partials(partials, gridDim.x, nval, tot);
-  __syncthreads();
-
-  if (epilogue != EPI_DCGS2) {
-    double* dst = epilogue == EPI_STORE_C ? sc->C : (epilogue == EPI_STORE_C2 ? sc->C2 : sc->S);
-    for (int i = threadIdx.x; i < k; i += blockDim.x) dst[i] = tot[i * NRHS];
-    if (threadIdx.x == 0) {
-      sc->norm_sq = tot[k * NRHS];
-      if (!isfinite(tot[k * NRHS])) set_status(sc, KC_ERR_NONFINITE);
-    }
-    return;
-  }
-
-  // ---- scalar step of Algorithm 4 (lines 4-6 and 10-12), FP64 -------------------------
-  // tot[2i] = C_i, tot[2i+1] = S_i (i < k); tot[2k] = beta, tot[2k+1] = s
-  __shared__ int s_ok;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    sc->C[i] = tot[2 * i];
-    sc->S[i] = tot[2 * i + 1];
-  }
-  if (threadIdx.x == 0) {
-    double cc = 0.0, cs = 0.0;
-    for (int i = 0; i < k; i++) {
-      cc += tot[2 * i] * tot[2 * i];
-      cs += tot[2 * i] * tot[2 * i + 1];
-    }
-    const double beta = tot[2 * k], s = tot[2 * k + 1];
-    double a2 = beta - cc;                                   // Pythagoras, line 4
-    sc->beta = beta;
-    sc->s = s;
-    sc->cs = cs;
-    s_ok = 1;
-    if (!isfinite(a2) || !isfinite(s)) {
-      set_status(sc, KC_ERR_NONFINITE);
-    } else if (!(a2 > sa.pyth_tol * beta)) {
-      if (sa.flags & SF_FALLBACK) {
-        sc->fallback = 1;                                    // explicit norm pass follows
-        s_ok = 0;
-      } else {
-        set_status(sc, KC_ERR_PYTHAGORAS_NEG);
-        a2 = fmax(a2, 1e-300);
-      }
-    }
-    s_alpha = sqrt(a2);
-  }
-  __syncthreads();
-  if (s_ok) scalar_step(sc, sa, k, s_alpha);
+  reduce_epilogue(partials, k, NRHS, sc, epilogue, sa);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -469,6 +475,241 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
       TA u = (TA)x[row];
       for (int i = 0; i < k; i++) u -= (TA)ld1(Q + (int64_t)i * ldq, row) * sc_[i];
       x[row] = (TV)u;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// FP64 with offload.  This GPU executes about 2 FP64 FMAs per SM per clock against
+// ~128 FP32 operations, so the two FP64 passes of a DCGS2 step are FP64-pipe bound.
+// Only half of their products need FP64: the reorthogonalisation coefficients
+// C = Q^T w (Alg. 4 line 3: a tiny result of heavy cancellation that enters H and q
+// directly) and the projection w <- v/alpha - Q T (line 9: its rounding error is the
+// Arnoldi representation error).  The first-projection coefficients S = Q^T v (line 2)
+// only need to be accurate enough for the next step's delayed reorthogonalisation to
+// remove what they leave behind (any error d in S reappears as -d/alpha in the next C and
+// cancels in H = K + C), and the product Q C in q = (w - Q C)/alpha (line 7) is
+// multiplied by the tiny C.  Both are evaluated here in float-float arithmetic
+// (operands split into two floats by integer operations, exact TwoProd products,
+// TwoSum accumulation; about 2^-44 relative), on the FP32/INT pipes, concurrently with
+// the FP64 FMAs of C and Q T.  Elements whose magnitude is outside [2^-80, 2^97] take
+// the FP64 path.
+// ----------------------------------------------------------------------------------------
+
+// x ~ hi + lo (to 2^-46 relative) using integer operations only; returns false when x is
+// outside the range where the split is exact enough (then use FP64 for this element).
+__device__ __forceinline__ bool split_df(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int H = (unsigned int)(b >> 32), L = (unsigned int)b;
+  const unsigned int e = (H >> 20) & 0x7ffu;
+  const unsigned int sgn = H & 0x80000000u;
+  const unsigned int hb = sgn | ((e - 896u) << 23) | ((H & 0xfffffu) << 3) | (L >> 29);
+  const float rf = __uint_as_float(0x4b000000u | ((L >> 6) & 0x7fffffu)) - 8388608.0f;
+  const float sc = __uint_as_float((e - 942u) << 23);
+  const bool zero = e == 0u;
+  hi = zero ? 0.0f : __uint_as_float(hb);
+  lo = zero ? 0.0f : __uint_as_float(__float_as_uint(rf * sc) | sgn);
+  return zero || (e - 943u) <= (1120u - 943u);
+}
+
+// (sh, sl) += (ah + al)(bh + bl), float-float with an exact leading product
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
+                                       float bl) {
+  const float p = ah * bh;
+  const float pe = fmaf(ah, bh, -p);
+  const float c = fmaf(ah, bl, fmaf(al, bh, pe));
+  const float t = sh + p;
+  const float bp = t - sh;
+  const float err = (sh - (t - bp)) + (p - bp);
+  sh = t;
+  sl += err + c;
+}
+
+// double from a float, by integer operations (exact for normal floats and zero)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// Fused DCGS2 reduction, FP64 with offload (EPI_DCGS2 only: NRHS = 2)
+template <int TPW>
+__global__ void __launch_bounds__(RED_THREADS)
+k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
+              const double* __restrict__ y, int64_t m, double* __restrict__ partials,
+              unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa) {
+  if (sc->stop) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ntask = k + 1;
+  double ac[TPW], as64[TPW];
+  float sh[TPW], sl[TPW];
+#pragma unroll
+  for (int i = 0; i < TPW; i++) { ac[i] = 0.0; as64[i] = 0.0; sh[i] = 0.0f; sl[i] = 0.0f; }
+  const int64_t ngroups = m / 2;
+  const int64_t g0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
+  const int64_t g1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
+  for (int64_t g = g0 + lane; g < g1; g += 32) {
+    double xv[2], yv[2];
+    ldv(x, g, xv);
+    ldv(y, g, yv);
+    float yh[2], yl[2];
+    const bool ys = split_df(yv[0], yh[0], yl[0]) & split_df(yv[1], yh[1], yl[1]);
+#pragma unroll
+    for (int i = 0; i < TPW; i++) {
+      const int t = warp + RED_WARPS * i;
+      if (t < k) {
+        double qv[2];
+        load_q(Q + (int64_t)t * ldq, g, qv);
+        ac[i] = fma(qv[0], xv[0], ac[i]);
+        ac[i] = fma(qv[1], xv[1], ac[i]);
+        float qh[2], ql[2];
+        const bool qs = split_df(qv[0], qh[0], ql[0]) & split_df(qv[1], qh[1], ql[1]);
+        if (qs && ys) {
+          df_mac(sh[i], sl[i], qh[0], ql[0], yh[0], yl[0]);
+          df_mac(sh[i], sl[i], qh[1], ql[1], yh[1], yl[1]);
+        } else {
+          as64[i] = fma(qv[0], yv[0], as64[i]);
+          as64[i] = fma(qv[1], yv[1], as64[i]);
+        }
+      } else if (t == k) {     // beta = w^T w and s = w^T v in FP64
+        ac[i] = fma(xv[0], xv[0], ac[i]);
+        ac[i] = fma(xv[1], xv[1], ac[i]);
+        as64[i] = fma(xv[0], yv[0], as64[i]);
+        as64[i] = fma(xv[1], yv[1], as64[i]);
+      }
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1) {           // ragged tail (m odd): FP64
+    for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
+      const double xs = __ldcg(x + row), ys1 = __ldcg(y + row);
+#pragma unroll
+      for (int i = 0; i < TPW; i++) {
+        const int t = warp + RED_WARPS * i;
+        if (t < ntask) {
+          const double q = t < k ? __ldcg(Q + (int64_t)t * ldq + row) : xs;
+          ac[i] = fma(q, xs, ac[i]);
+          as64[i] = fma(q, ys1, as64[i]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TPW; i++) {
+    const int t = warp + RED_WARPS * i;
+    const double c = warp_sum(ac[i]);
+    const double sv = warp_sum(as64[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])));
+    if (lane == 0 && t < ntask) {
+      partials[(int64_t)blockIdx.x * PSTRIDE + 2 * t] = c;
+      partials[(int64_t)blockIdx.x * PSTRIDE + 2 * t + 1] = sv;
+    }
+  }
+  if (!last_cta(counter)) return;
+  reduce_epilogue(partials, k, 2, sc, EPI_DCGS2, sa);
+}
+
+// DCGS2 update, FP64 with offload: u = w - Q C in float-float (C scaled by a power of two
+// into float range), w <- v/alpha - Q T - q T_k in FP64.
+__global__ void __launch_bounds__(UPD_THREADS)
+k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__ w,
+                    const double* __restrict__ v, int64_t m, const Scalars* __restrict__ sc) {
+  if (sc->stop) return;
+  __shared__ double sC[NMAX], sT[NMAX + 1];
+  __shared__ float cH[NMAX], cL[NMAX];
+  __shared__ double s_scale;
+  __shared__ int s_cok;
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    if (i < k) sC[i] = sc->C[i];
+    sT[i] = sc->T[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double cmax = 0.0;
+    for (int i = 0; i < k; i++) cmax = fmax(cmax, fabs(sC[i]));
+    int ex = 0;
+    if (cmax > 0.0) frexp(cmax, &ex);
+    s_scale = ldexp(1.0, ex);                 // C / scale lies in (-1, 1)
+    s_cok = 1;
+  }
+  __syncthreads();
+  const double inv_scale = 1.0 / s_scale;     // exact: a power of two
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    float h, l;
+    if (!split_df(sC[i] * inv_scale, h, l)) { h = 0.0f; l = 0.0f; if (sC[i] != 0.0) s_cok = 0; }
+    cH[i] = h;
+    cL[i] = l;
+  }
+  __syncthreads();
+  const bool cok = s_cok;
+  const double inva = sc->inv_alpha, scale = s_scale;
+  double* qk = Q + (int64_t)k * ldq;
+  const int64_t ngroups = m / 2;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    double wv[2], vv[2];
+    ldv_cg(w, g, wv);
+    ldv_cg(v, g, vv);
+    double wn[2] = {vv[0] * inva, vv[1] * inva};
+    double u64[2] = {wv[0], wv[1]};
+    float zh[2] = {0.0f, 0.0f}, zl[2] = {0.0f, 0.0f};
+    int i = 0;
+    for (; i + 2 <= k; i += 2) {
+      double q0[2], q1[2];
+      load_q(Q + (int64_t)i * ldq, g, q0);
+      load_q(Q + (int64_t)(i + 1) * ldq, g, q1);
+      wn[0] = fma(-q0[0], sT[i], wn[0]);
+      wn[1] = fma(-q0[1], sT[i], wn[1]);
+      wn[0] = fma(-q1[0], sT[i + 1], wn[0]);
+      wn[1] = fma(-q1[1], sT[i + 1], wn[1]);
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        float h0, l0, h1, l1;
+        const bool ok = split_df(q0[r], h0, l0) & split_df(q1[r], h1, l1) & cok;
+        if (ok) {
+          df_mac(zh[r], zl[r], h0, l0, cH[i], cL[i]);
+          df_mac(zh[r], zl[r], h1, l1, cH[i + 1], cL[i + 1]);
+        } else {
+          u64[r] = fma(-q0[r], sC[i], u64[r]);
+          u64[r] = fma(-q1[r], sC[i + 1], u64[r]);
+        }
+      }
+    }
+    for (; i < k; i++) {
+      double q0[2];
+      load_q(Q + (int64_t)i * ldq, g, q0);
+      wn[0] = fma(-q0[0], sT[i], wn[0]);
+      wn[1] = fma(-q0[1], sT[i], wn[1]);
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        float h0, l0;
+        if (split_df(q0[r], h0, l0) && cok) df_mac(zh[r], zl[r], h0, l0, cH[i], cL[i]);
+        else u64[r] = fma(-q0[r], sC[i], u64[r]);
+      }
+    }
+    double qn[2], wo[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      const double u = fma(-f2d_bits(zh[r]), scale, fma(-f2d_bits(zl[r]), scale, u64[r]));
+      qn[r] = u * inva;
+      wo[r] = fma(-qn[r], sT[k], wn[r]);
+    }
+    store_q(qk, g, qn);
+    stv(w, g, wo);
+  }
+  if (blockIdx.x == 0) {        // ragged tail: FP64
+    for (int64_t row = ngroups * 2 + threadIdx.x; row < m; row += blockDim.x) {
+      double u = w[row], wn1 = v[row] * inva;
+      for (int i = 0; i < k; i++) {
+        const double q = __ldcg(Q + (int64_t)i * ldq + row);
+        u = fma(-q, sC[i], u);
+        wn1 = fma(-q, sT[i], wn1);
+      }
+      const double qn1 = u * inva;
+      qk[row] = qn1;
+      w[row] = fma(-qn1, sT[k], wn1);
     }
   }
 }
@@ -705,7 +946,19 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
   if (!ok)
     return fail(ctx, KC_ERR_INVALID_ARG, "reduce: unsupported basis/vector types %d/%d", q_dtype, vec_dtype);
   timing_begin(ctx, KID_REDUCE);
-  if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
+  if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
+      ctx->fp64_mode == 1) {
+    const int ntask = k + 1;
+    auto go = [&](auto kern) {
+      kern<<<grid, RED_THREADS, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
+                                                  (const double*)y, m, ctx->partials,
+                                                  ctx->counters, ctx->scal, sa);
+    };
+    if (ntask <= RED_WARPS) go(k_reduce_f64x<1>);
+    else if (ntask <= 2 * RED_WARPS) go(k_reduce_f64x<2>);
+    else if (ntask <= 4 * RED_WARPS) go(k_reduce_f64x<4>);
+    else go(k_reduce_f64x<8>);
+  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
     if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
     else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);
   } else if (q_dtype == KC_F32 && vec_dtype == KC_F32) {
@@ -724,7 +977,9 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
   const int R = vec_dtype == KC_F64 ? 2 : 4;
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_UPDATE);
-  if (q_dtype == KC_F64)
+  if (q_dtype == KC_F64 && ctx->fp64_mode == 1)
+    k_dcgs2_update_f64x<<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
+  else if (q_dtype == KC_F64)
     k_dcgs2_update<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
   else if (q_dtype == KC_F32)
     k_dcgs2_update<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((float*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);

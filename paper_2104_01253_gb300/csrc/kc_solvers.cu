@@ -183,6 +183,8 @@ static kc_status gmres_cycle(kc_ctx* ctx, const kc_csr* A, const Cycle& c, void*
   *matvecs += (h->stop && h->ncols < c.n) ? h->ncols + 1 : c.n;
   *status = h->status;
   KC_CUDA(ctx, cudaMemsetAsync(&ctx->scal->status, 0, sizeof(int), ctx->stream));
+  // the cycle is over: later kernels (the FP64 residual, the next cycle) must run
+  KC_CUDA(ctx, cudaMemsetAsync(&ctx->scal->stop, 0, sizeof(int), ctx->stream));
   return KC_OK;
 }
 
