@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--n", type=int, default=50, help="Arnoldi steps per expansion")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-baselines", action="store_true")
+    p.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1])
     p.add_argument("--no-check", action="store_true",
                    help="skip the loss-of-orthogonality / Arnoldi-relation check")
     return p.parse_args()
@@ -70,12 +72,6 @@ def algorithmic_bytes(m, nnz, n):
     fin = 2 * (8 * m * k + 8 * m) + 2 * (8 * m * k + 16 * m) + 8 * m + 16 * m
     total = sum(per_kernel.values()) + fin
     return total, per_kernel
-
-
-def fp64_flops_reduce(m, n):
-    """FP64 flops of the fused reductions of one expansion: 2 FMA (4 flop) per basis
-    element and per row for beta and s."""
-    return sum(4 * m * k + 4 * m for k in range(n))
 
 
 class ClockSampler:
@@ -228,6 +224,7 @@ def main():
     m, nnz = Ah.m, Ah.nnz
     r0_host = gaussian_vector(m, 1002)
     ctx = kc.Context(local)
+    ctx.set_fp64_mode(args.fp64_mode)
     A = kc.DeviceCSR(Ah)
     del Ah
     n = args.n
@@ -287,25 +284,64 @@ def main():
     if not args.no_check:
         loo, rre = quality(kc, ctx, A, st, m, n)
 
-    # dominant kernel roofline (FP64 pipe bound: 2 DFMA per basis element)
-    red_ms, red_cnt = kern.get("reduce", (0.0, 0))
-    upd_ms, upd_cnt = kern.get("dcgs2_update", (0.0, 0))
-    flops_red = fp64_flops_reduce(m, n) * args.steps
-    flops_upd = sum(4 * m * k + 4 * m for k in range(n)) * args.steps
-    if red_ms >= upd_ms:
-        dom, dom_ms, dom_cnt, dom_flops, dom_bytes = ("reduce", red_ms, red_cnt, flops_red,
-                                                      per_kernel_bytes["reduce"] * args.steps)
+    # dominant kernel roofline.  FP64 FMAs on the FP64 pipe per basis element: 2 in the
+    # all-FP64 mode, 1 with offload (S and Q C move to the FP32/INT pipes).  The bound is
+    # whichever of the FP64 pipe and HBM the kernel uses the larger fraction of.
+    fma_per_elem = 2 if ctx.fp64_mode == 0 else 1
+    per = {}
+    for name in ("reduce", "dcgs2_update"):
+        ms_k, cnt_k = kern.get(name, (0.0, 0))
+        if cnt_k == 0:
+            continue
+        flops = sum(2 * fma_per_elem * m * k + 4 * m for k in range(n)) * args.steps
+        byts = per_kernel_bytes[name] * args.steps
+        t = ms_k / 1e3
+        per[name] = {"ms": ms_k, "cnt": cnt_k, "tflops": flops / t / 1e12,
+                     "gbs": byts / t / 1e9}
+    dom = max(per, key=lambda k: per[k]["ms"])
+    d = per[dom]
+    f_alu = d["tflops"] / FP64_PEAK_TFLOPS
+    f_hbm = d["gbs"] / hbm_peak
+    if f_hbm >= f_alu:
+        roofline = {"bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": f_hbm, "peak_kind": peak_kind}
     else:
-        dom, dom_ms, dom_cnt, dom_flops, dom_bytes = ("dcgs2_update", upd_ms, upd_cnt, flops_upd,
-                                                      per_kernel_bytes["dcgs2_update"] * args.steps)
-    achieved = dom_flops / (dom_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_kind": "derived FP64 FMA peak (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "hbm_achieved_gbs": dom_bytes / (dom_ms / 1e3) / 1e9,
-                "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
-                "avg_launch_ms": dom_ms / max(dom_cnt, 1)}
+        roofline = {"bound": "alu", "achieved": d["tflops"], "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": f_alu,
+                    "peak_kind": "derived FP64 FMA peak (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
+    roofline.update({"kernel": dom, "traffic": None,
+                     "avg_launch_ms": d["ms"] / max(d["cnt"], 1),
+                     "fp64_tflops": d["tflops"], "fp64_frac": f_alu,
+                     "hbm_gbs": d["gbs"], "hbm_frac": f_hbm,
+                     "fp64_fma_per_basis_element": fma_per_elem})
+
+    # the same workload on the same GPU: DCGS2 with every product in FP64, CGS2, MGS
+    baselines = {}
+    if not args.no_baselines:
+        def timed(fn, reps=1):
+            fn()
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                fn()
+            t1.record(stream)
+            torch.cuda.synchronize()
+            return n * reps / (t0.elapsed_time(t1) / 1e3)
+        mode = ctx.fp64_mode
+        ctx.set_fp64_mode(0)
+        baselines["dcgs2_all_fp64_steps_per_s"] = timed(lambda: expansion(r0), 2)
+        ctx.set_fp64_mode(mode)
+
+        def classic(step):
+            kc.cgs2_arnoldi_init(ctx, A, st, r0)
+            for _ in range(n):
+                step(ctx, A, st)
+        baselines["cgs2_steps_per_s"] = timed(lambda: classic(kc.cgs2_arnoldi_step))
+        baselines["mgs_steps_per_s"] = timed(lambda: classic(kc.mgs_arnoldi_step))
+        baselines["note"] = ("same m, n and GPU; CGS2 = Algorithm 3 (3 reductions/step), "
+                             "MGS level 1 (one reduction per inner product)")
 
     # end to end through the C ABI with host buffers: H2D of r0, expansion, D2H of H
     e2e = None
@@ -357,7 +393,8 @@ def main():
             "algorithmic_bytes_per_step": total_bytes,
             "loo": loo, "rre": rre, "device_status": status,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64_mode": ["all-fp64", "fp64-with-float-float-offload"][ctx.fp64_mode],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "same_gpu_baselines": baselines,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
