@@ -149,6 +149,25 @@ kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
  * Afterwards Q has k+1 columns and H is (k+1) x k. */
 kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 
+/* One FP64 DCGS2 step, as dcgs2_arnoldi_step in its all-FP64 mode, that allocates
+ * nothing and needs no context.  (The paper has no counterpart: this is a deployment
+ * variant.)  It is meant for callers that cannot call cudaMalloc: code running inside
+ * a stream-ordered allocator or graph callback, plugins whose host application owns the
+ * device memory budget, or code that must not create a context.  The caller still passes
+ * the matrix and every state buffer (Q, w, v, H, K), exactly as for
+ * dcgs2_arnoldi_step; the reduction's scratch (per-CTA partial sums, the last-CTA ticket,
+ * the step scalars) lives in a file-scope device array of about 325 KB that every GPU
+ * loading the library keeps until the process exits.  Limits: FP64 basis and matrix
+ * only, ncap <= 128 (the same limit as the other entry points), at most 152 reduction
+ * CTAs; other sizes return KC_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents; the call clears what must start at zero (ticket, flags), and two
+ * calls that overlap on the GPU (different streams, concurrent graphs) race on it.
+ * Enqueued on `cuda_stream` (a cudaStream_t, NULL for the legacy stream); returns
+ * KC_ERR_CUDA if the set-up or a launch fails.  Numerical status is not reported. */
+kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st, void* cuda_stream);
+
 /* ---- baselines ---------------------------------------------------------------------- */
 
 /* CGS2-Arnoldi (Algorithm 3) and MGS-Arnoldi (Section 2, "MGS Level 1"): init sets

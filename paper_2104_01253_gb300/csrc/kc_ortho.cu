@@ -1063,3 +1063,100 @@ kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_
 }
 
 }  // namespace kc
+
+// ----------------------------------------------------------------------------------------
+// One DCGS2 step without any allocation, for callers that cannot call cudaMalloc: code
+// running inside a CUDA stream-ordered allocator callback, plugins whose host process owns
+// the device memory budget, and environments where a context (kc_create) is not
+// available.  The fused reduction's scratch (per-CTA partial sums, the last-CTA ticket
+// and the step scalars) lives in the file-scope array below instead of context workspace.
+// ----------------------------------------------------------------------------------------
+namespace kc {
+
+constexpr int NOALLOC_MAX_GRID = 152;   // reduction CTAs, and rows of partials below
+struct NoAllocScratch {
+  Scalars sc;
+  unsigned int counter[4];
+  double partials[NOALLOC_MAX_GRID * PSTRIDE];
+};
+
+// About 325 KB; every GPU that loads libkrylov holds it until the process exits.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// Device addresses of g_noalloc_scratch, looked up once per device (host code may not
+// use the symbol itself: on the host it only names a stand-in, not device memory).
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static NoAllocScratch* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+static kc_status noalloc_setup(NoAllocScratch** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+    return KC_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KC_ERR_CUDA;
+    g_noalloc_ptr[dev] = (NoAllocScratch*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KC_OK;
+}
+
+}  // namespace kc
+
+extern "C" kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st,
+                                                void* cuda_stream) {
+  using namespace kc;
+  if (validate_csr(nullptr, A) != KC_OK || validate_state(nullptr, A, st) != KC_OK)
+    return KC_ERR_INVALID_ARG;
+  if (st->q_dtype != KC_F64 || A->val_dtype != KC_F64) return KC_ERR_INVALID_ARG;
+  const int k = st->k;
+  if (k + 2 > st->ncap || st->finished) return KC_ERR_INVALID_ARG;
+  if (k + 1 > NMAX) return KC_ERR_INVALID_ARG;          // partials rows hold 2*NMAX+4 values
+  NoAllocScratch* scr = nullptr;
+  kc_status s = noalloc_setup(&scr);
+  if (s != KC_OK) return s;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const int64_t m = A->m;
+  // what must start at zero: the ticket counters, the stop flag and the status word
+  if (cudaMemsetAsync(scr->counter, 0, sizeof(scr->counter), stream) != cudaSuccess ||
+      cudaMemsetAsync(&scr->sc.stop, 0, sizeof(int), stream) != cudaSuccess ||
+      cudaMemsetAsync(&scr->sc.status, 0, sizeof(int), stream) != cudaSuccess)
+    return KC_ERR_CUDA;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return KC_ERR_CUDA;
+  int64_t gs = (m + 255) / 256;
+  const int gspmv = (int)(gs < 1 ? 1 : (gs > 8 * (int64_t)sms ? 8 * (int64_t)sms : gs));
+  k_spmv<double, double><<<gspmv, 256, 0, stream>>>(A->row_ptr, A->col_idx,
+      (const double*)A->val, (const double*)st->w, (double*)st->v, m, &scr->sc);
+  StepArgs sa = {};
+  sa.H = st->H;
+  sa.ldh = st->ldh;
+  sa.K = st->K;
+  sa.ldk = st->ncap;
+  sa.k = k;
+  sa.pyth_tol = 0.0;
+  int64_t gr = (m / 2 + 32 * 4 - 1) / (32 * 4);
+  const int maxg = sms < NOALLOC_MAX_GRID ? sms : NOALLOC_MAX_GRID;
+  const int grid = (int)(gr < 1 ? 1 : (gr > maxg ? maxg : gr));
+  const double* Q = (const double*)st->Q;
+  const double* w = (const double*)st->w;
+  const double* v = (const double*)st->v;
+  const int ntask = k + 1;
+  auto go = [&](auto kern) {
+    kern<<<grid, RED_THREADS, 0, stream>>>(Q, st->ldq, k, w, v, m, scr->partials, scr->counter,
+                                           &scr->sc, (int)EPI_DCGS2, sa);
+  };
+  if (ntask <= RED_WARPS) go(k_reduce<double, double, 1, 2>);
+  else if (ntask <= 2 * RED_WARPS) go(k_reduce<double, double, 2, 2>);
+  else if (ntask <= 4 * RED_WARPS) go(k_reduce<double, double, 4, 2>);
+  else go(k_reduce<double, double, 8, 2>);
+  int64_t gu = (m / 2 + UPD_THREADS - 1) / UPD_THREADS;
+  const int gupd = (int)(gu < 1 ? 1 : (gu > 8 * (int64_t)sms ? 8 * (int64_t)sms : gu));
+  k_dcgs2_update<double, double><<<gupd, UPD_THREADS, 0, stream>>>(
+      (double*)st->Q, st->ldq, k, (double*)st->w, (const double*)st->v, m, &scr->sc);
+  if (cudaGetLastError() != cudaSuccess) return KC_ERR_CUDA;
+  st->k = k + 1;
+  return KC_OK;
+}
