@@ -536,6 +536,37 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)d);
 }
 
+// One group of two rows of the offloaded reduction: C in FP64, S in float-float.
+template <int TPW>
+__device__ __forceinline__ void f64x_group(int warp, int k, const double (&xv)[2],
+                                           const double (&yv)[2], const double (&qv)[TPW][2],
+                                           double* ac, double* as64, float* sh, float* sl) {
+  float yh[2], yl[2];
+  const bool ys = split_df(yv[0], yh[0], yl[0]) & split_df(yv[1], yh[1], yl[1]);
+#pragma unroll
+  for (int i = 0; i < TPW; i++) {
+    const int t = warp + RED_WARPS * i;
+    if (t < k) {
+      ac[i] = fma(qv[i][0], xv[0], ac[i]);
+      ac[i] = fma(qv[i][1], xv[1], ac[i]);
+      float qh[2], ql[2];
+      const bool qs = split_df(qv[i][0], qh[0], ql[0]) & split_df(qv[i][1], qh[1], ql[1]);
+      if (qs && ys) {
+        df_mac(sh[i], sl[i], qh[0], ql[0], yh[0], yl[0]);
+        df_mac(sh[i], sl[i], qh[1], ql[1], yh[1], yl[1]);
+      } else {
+        as64[i] = fma(qv[i][0], yv[0], as64[i]);
+        as64[i] = fma(qv[i][1], yv[1], as64[i]);
+      }
+    } else if (t == k) {     // beta = w^T w and s = w^T v in FP64
+      ac[i] = fma(xv[0], xv[0], ac[i]);
+      ac[i] = fma(xv[1], xv[1], ac[i]);
+      as64[i] = fma(xv[0], yv[0], as64[i]);
+      as64[i] = fma(xv[1], yv[1], as64[i]);
+    }
+  }
+}
+
 // Fused DCGS2 reduction, FP64 with offload (EPI_DCGS2 only: NRHS = 2)
 template <int TPW>
 __global__ void __launch_bounds__(RED_THREADS)
@@ -552,36 +583,36 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
   const int64_t ngroups = m / 2;
   const int64_t g0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
   const int64_t g1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
-  for (int64_t g = g0 + lane; g < g1; g += 32) {
-    double xv[2], yv[2];
-    ldv(x, g, xv);
-    ldv(y, g, yv);
-    float yh[2], yl[2];
-    const bool ys = split_df(yv[0], yh[0], yl[0]) & split_df(yv[1], yh[1], yl[1]);
+  // two row groups per iteration, every load issued before any arithmetic
+  int64_t g = g0 + lane;
+  for (; g + 32 < g1; g += 64) {
+    double xa[2], ya[2], xb[2], yb[2];
+    ldv(x, g, xa);
+    ldv(y, g, ya);
+    ldv(x, g + 32, xb);
+    ldv(y, g + 32, yb);
+    double qa[TPW][2], qb[TPW][2];
 #pragma unroll
     for (int i = 0; i < TPW; i++) {
       const int t = warp + RED_WARPS * i;
       if (t < k) {
-        double qv[2];
-        load_q(Q + (int64_t)t * ldq, g, qv);
-        ac[i] = fma(qv[0], xv[0], ac[i]);
-        ac[i] = fma(qv[1], xv[1], ac[i]);
-        float qh[2], ql[2];
-        const bool qs = split_df(qv[0], qh[0], ql[0]) & split_df(qv[1], qh[1], ql[1]);
-        if (qs && ys) {
-          df_mac(sh[i], sl[i], qh[0], ql[0], yh[0], yl[0]);
-          df_mac(sh[i], sl[i], qh[1], ql[1], yh[1], yl[1]);
-        } else {
-          as64[i] = fma(qv[0], yv[0], as64[i]);
-          as64[i] = fma(qv[1], yv[1], as64[i]);
-        }
-      } else if (t == k) {     // beta = w^T w and s = w^T v in FP64
-        ac[i] = fma(xv[0], xv[0], ac[i]);
-        ac[i] = fma(xv[1], xv[1], ac[i]);
-        as64[i] = fma(xv[0], yv[0], as64[i]);
-        as64[i] = fma(xv[1], yv[1], as64[i]);
+        load_q(Q + (int64_t)t * ldq, g, qa[i]);
+        load_q(Q + (int64_t)t * ldq, g + 32, qb[i]);
       }
     }
+    f64x_group<TPW>(warp, k, xa, ya, qa, ac, as64, sh, sl);
+    f64x_group<TPW>(warp, k, xb, yb, qb, ac, as64, sh, sl);
+  }
+  if (g < g1) {
+    double xa[2], ya[2], qa[TPW][2];
+    ldv(x, g, xa);
+    ldv(y, g, ya);
+#pragma unroll
+    for (int i = 0; i < TPW; i++) {
+      const int t = warp + RED_WARPS * i;
+      if (t < k) load_q(Q + (int64_t)t * ldq, g, qa[i]);
+    }
+    f64x_group<TPW>(warp, k, xa, ya, qa, ac, as64, sh, sl);
   }
   if (blockIdx.x == gridDim.x - 1) {           // ragged tail (m odd): FP64
     for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
@@ -656,24 +687,19 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
     double u64[2] = {wv[0], wv[1]};
     float zh[2] = {0.0f, 0.0f}, zl[2] = {0.0f, 0.0f};
     int i = 0;
-    for (; i + 2 <= k; i += 2) {
-      double q0[2], q1[2];
-      load_q(Q + (int64_t)i * ldq, g, q0);
-      load_q(Q + (int64_t)(i + 1) * ldq, g, q1);
-      wn[0] = fma(-q0[0], sT[i], wn[0]);
-      wn[1] = fma(-q0[1], sT[i], wn[1]);
-      wn[0] = fma(-q1[0], sT[i + 1], wn[0]);
-      wn[1] = fma(-q1[1], sT[i + 1], wn[1]);
+    for (; i + 2 <= k; i += 2) {        // two columns' loads in flight before arithmetic
+      double q[2][2];
 #pragma unroll
-      for (int r = 0; r < 2; r++) {
-        float h0, l0, h1, l1;
-        const bool ok = split_df(q0[r], h0, l0) & split_df(q1[r], h1, l1) & cok;
-        if (ok) {
-          df_mac(zh[r], zl[r], h0, l0, cH[i], cL[i]);
-          df_mac(zh[r], zl[r], h1, l1, cH[i + 1], cL[i + 1]);
-        } else {
-          u64[r] = fma(-q0[r], sC[i], u64[r]);
-          u64[r] = fma(-q1[r], sC[i + 1], u64[r]);
+      for (int j = 0; j < 2; j++) load_q(Q + (int64_t)(i + j) * ldq, g, q[j]);
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        wn[0] = fma(-q[j][0], sT[i + j], wn[0]);
+        wn[1] = fma(-q[j][1], sT[i + j], wn[1]);
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+          float h0, l0;
+          if (split_df(q[j][r], h0, l0) && cok) df_mac(zh[r], zl[r], h0, l0, cH[i + j], cL[i + j]);
+          else u64[r] = fma(-q[j][r], sC[i + j], u64[r]);
         }
       }
     }
