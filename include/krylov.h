@@ -219,6 +219,40 @@ typedef struct {
  * resid: HOST arrays of length nev (largest real part first).  nconv, restarts,
  * matvecs: host outputs (may be NULL).  The small dense Schur step runs on the GPU in
  * FP64.  Synchronises. */
+/* ---- learned preconditioner and flexible GMRES (additions; not in the paper) ----------- */
+
+/* The network: 6 layers of 3x3 convolutions, channels 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1,
+ * zero padding, no bias, ReLU after layers 0..4; BF16 weights and activations, FP32
+ * accumulation (tensor cores for the 32 -> 32 layers).  w32: FP32 master weights, layer by
+ * layer, each [Cout][3][3][Cin]; kc_cnn_param_count() values (37,440). */
+int64_t kc_cnn_param_count(void);
+
+/* y = net(x) for B single-channel H x W images (FP32, row-major, device).  Uses context
+ * workspace (grown on demand). */
+kc_status kc_cnn_forward(kc_ctx* ctx, const float* w32, const float* x, float* y, int B,
+                         int H, int W);
+
+/* One training step on a batch: forward (y = net(x), written to y), loss
+ * L = (1/B) sum_b ||y_b - e_b||^2 / ||e_b||^2 (host *loss, may be NULL; reading it
+ * synchronises), backward (dL/dw into grad if non-NULL, FP32), and, when t > 0, the Adam
+ * update of w32 with step number t, learning rate lr, beta1 0.9, beta2 0.999, eps 1e-8
+ * (adam_m, adam_v: FP32 moment buffers, kc_cnn_param_count() each, zero-initialised by
+ * the caller). */
+kc_status kc_cnn_train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_v, int64_t t,
+                            float lr, const float* x, const float* e, int B, int H, int W,
+                            float* y, float* grad, double* loss);
+
+/* Restarted flexible GMRES(opts->restart) with flexible DCGS2 and the network as right
+ * preconditioner: M(w) = rms(w) net(w / rms(w)) on the H x W grid (m = H W, row-major).
+ * With w32 == NULL the preconditioner is the identity (the flexible machinery alone).
+ * The flexible step stores zhat_k = M(w_k), applies A to it, keeps the single reduction of
+ * Algorithm 4, and finalises H(:, k) = T + C_{k+1} (no H C / alpha correction); the update
+ * is x += sum_k zhat_k y_k / alpha_k.  FP64 vectors; b, x device, x = x0 on entry.
+ * opts->precision must be 0.  Synchronises once per cycle. */
+kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, int W,
+                       const double* b, double* x, const kc_gmres_opts* opts,
+                       kc_gmres_info* info);
+
 kc_status krylov_schur_eigs(kc_ctx* ctx, const kc_csr* A, const double* v0,
                             const kc_ks_opts* opts, double* eig_re, double* eig_im,
                             double* resid, int* nconv, int* restarts, int* matvecs);

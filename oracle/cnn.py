@@ -90,3 +90,45 @@ def apply_preconditioner(ws, r_vec, H, W):
         return np.zeros(H * W)
     y, _ = forward(ws, x / s)
     return (y * s).reshape(H * W)
+
+
+def _round_bf16(x):
+    """Round float64 values to the nearest bfloat16 (ties to even), as float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16_storage(ws, x):
+    """The network with BF16 weights and BF16-stored hidden activations (what the GPU
+    kernels keep in memory): weights rounded to bfloat16, each hidden layer's ReLU output
+    rounded to bfloat16, sums in FP64; input and output stay unrounded."""
+    wb = [_round_bf16(W) for W in ws]
+    h = x
+    acts = [x]
+    for li, W in enumerate(wb):
+        h = conv3x3(h, W)
+        if li < len(wb) - 1:
+            h = _round_bf16(np.maximum(h, 0.0))
+        acts.append(h)
+    return h, acts
+
+
+def loss_and_grads_bf16_storage(ws, r, e):
+    """loss_and_grads with the GPU's storage rounding: BF16 weights, BF16 hidden
+    activations and BF16 hidden-layer gradients dL/dz (the output gradient stays FP64)."""
+    B = r.shape[0]
+    wb = [_round_bf16(W) for W in ws]
+    y, acts = forward_bf16_storage(ws, r)
+    diff = y - e
+    en = np.sum(e * e, axis=(1, 2, 3))
+    L = float(np.mean(np.sum(diff * diff, axis=(1, 2, 3)) / en))
+    g = (2.0 / B) * diff / en[:, None, None, None]
+    grads = [None] * len(ws)
+    for li in range(len(ws) - 1, -1, -1):
+        if li < len(ws) - 1:
+            g = _round_bf16(g * (acts[li + 1] > 0.0))
+        gW, g = conv3x3_backward(acts[li], wb[li], g)
+        grads[li] = gW
+    return L, grads, y

@@ -223,3 +223,36 @@ def krylov_schur_eigs(ctx: Context, A: DeviceCSR, v0, nev=10, ncv=40, nkeep=20, 
     eigs = np.array(er[:]) + 1j * np.array(ei[:])
     return dict(eigs=eigs, resid=np.array(rs[:]), nconv=nconv.value, restarts=restarts.value,
                 matvecs=matvecs.value, status=st)
+
+
+# ---- learned preconditioner -----------------------------------------------------------------
+
+def kc_cnn_param_count() -> int:
+    return int(_lib.load().kc_cnn_param_count())
+
+
+def kc_cnn_forward(ctx: Context, w32, x, y, B: int, H: int, W: int):
+    ctx.check(ctx.lib.kc_cnn_forward(ctx.handle, _ptr(w32), _ptr(x), _ptr(y), B, H, W))
+
+
+def kc_cnn_train_step(ctx: Context, w32, adam_m, adam_v, t: int, lr: float, x, e, B: int,
+                      H: int, W: int, y, grad=None):
+    """One forward/backward/Adam step on the GPU; returns the batch loss."""
+    loss = C.c_double()
+    ctx.check(ctx.lib.kc_cnn_train_step(ctx.handle, _ptr(w32), _ptr(adam_m), _ptr(adam_v), t,
+                                        lr, _ptr(x), _ptr(e), B, H, W, _ptr(y), _ptr(grad),
+                                        C.byref(loss)))
+    return loss.value
+
+
+def fgmres_solve(ctx: Context, A: DeviceCSR, w32, H: int, W: int, b, x, restart=40,
+                 rtol=1e-10, maxit=100000):
+    """Flexible GMRES with the network (w32; None = identity) as right preconditioner."""
+    opts = kc_gmres_opts(restart, maxit, 0, 0, rtol, 0.0, 0, 0)
+    info = kc_gmres_info()
+    st = ctx.lib.fgmres_solve(ctx.handle, C.byref(A.c), _ptr(w32), H, W, _ptr(b), _ptr(x),
+                              C.byref(opts), C.byref(info))
+    if st not in (0, _lib.KC_ERR_NOT_CONVERGED):
+        ctx.check(st)
+    return dict(iters=info.iters, restarts=info.restarts, status=st,
+                rel_resid_est=info.rel_resid_est, rel_resid_true=info.rel_resid_true)

@@ -149,6 +149,7 @@ kc_status kc_destroy(kc_ctx* ctx) {
   if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
   if (ctx->dwork) cudaFree(ctx->dwork);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->cnn_ws) cudaFree(ctx->cnn_ws);
   delete ctx;
   return KC_OK;
 }

@@ -39,6 +39,7 @@ struct Scalars {
   double resid_est;     // |g_{j+1}| of the last rotated column
   double rtol_abs;      // stop threshold on |g| (absolute)
   double y[NMAX];
+  double zscale[NMAX];  // flexible GMRES: 1/alpha_k, the scale of the stored M(w_k)
 };
 
 enum Epilogue : int {
@@ -94,6 +95,8 @@ struct kc_ctx {
   size_t dwork_len;
   void* ws;                // solver workspace (basis, vectors), grown on demand
   size_t ws_len;
+  void* cnn_ws;            // convolutional preconditioner workspace, grown on demand
+  size_t cnn_ws_len;
   int64_t launches;
   int fp64_mode;           // 0: every product in FP64; 1: FP64 with float-float offload
   // optional per-kernel timing: events recorded around every launch on ctx->stream
@@ -153,6 +156,18 @@ kc_status launch_scale_to(kc_ctx* ctx, const void* x, void* qcol, int q_dtype, i
 kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_t m,
                         int vec_dtype);
 kc_status ensure_workspace(kc_ctx* ctx, size_t bytes);
+// convolutional preconditioner (kc_cnn.cu)
+kc_status cnn_prep(kc_ctx* ctx, const float* w32, __nv_bfloat16* wf, __nv_bfloat16* wt);
+kc_status cnn_forward(kc_ctx* ctx, const __nv_bfloat16* wf, const float* x, float* y,
+                      __nv_bfloat16* const* acts, bool keep, int B, int H, int W);
+kc_status cnn_backward(kc_ctx* ctx, const __nv_bfloat16* wf, const __nv_bfloat16* wt,
+                       const float* x, const float* g, __nv_bfloat16* const* acts,
+                       __nv_bfloat16* const* dz, float* dw, int B, int H, int W);
+kc_status cnn_loss_grad(kc_ctx* ctx, const float* y, const float* e, double* sums, float* g,
+                        int B, int64_t npix);
+kc_status cnn_adam(kc_ctx* ctx, float* w, const float* g, float* m, float* v, int64_t t,
+                   float lr, float b1, float b2, float eps);
+int64_t cnn_nparam();
 kc_status validate_csr(kc_ctx* ctx, const kc_csr* A);
 kc_status validate_state(kc_ctx* ctx, const kc_csr* A, const kc_arnoldi* st);
 

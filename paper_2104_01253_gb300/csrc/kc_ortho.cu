@@ -174,6 +174,7 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
     sc->inv_alpha = 1.0 / alpha;
     sc->T[k] = (sc->s - sc->cs) / (alpha * alpha);
     if ((sa.flags & SF_GIVENS) && k == 0) { sc->g[0] = alpha; sc->ncols = 0; }
+    if (sa.flags & SF_FLEXIBLE) sc->zscale[k] = 1.0 / alpha;
     if (k >= 1) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;
   }
   for (int i = threadIdx.x; i < k; i += blockDim.x) {

@@ -1,0 +1,164 @@
+"""GPU parity of the convolutional preconditioner and of flexible GMRES.
+
+The network stores BF16 weights, activations and hidden gradients and accumulates in
+FP32; the oracle counterpart applies the same BF16 rounding points in FP64
+(oracle.cnn.forward_bf16_storage / loss_and_grads_bf16_storage).  Remaining differences
+come from FP32 accumulation order, which can flip the rounding of a few BF16 values:
+tolerance 5e-3 relative (L2) for outputs and 2e-2 for weight gradients.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import cnn  # noqa: E402
+from oracle.gmres import gmres as orc_gmres  # noqa: E402
+from synth import convdiff_csr, gaussian_vector, varcoef_fields_2d  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def kc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2104_01253_gb300 as kc
+    return kc
+
+
+@pytest.fixture(scope="module")
+def ctx(kc):
+    return kc.Context(0)
+
+
+def pack(ws):
+    return np.concatenate([w.transpose(0, 2, 3, 1).reshape(-1) for w in ws]).astype(np.float32)
+
+
+def unpack(flat, template):
+    out, off = [], 0
+    for w in template:
+        co, ci = w.shape[0], w.shape[1]
+        n = co * 9 * ci
+        out.append(flat[off:off + n].reshape(co, 3, 3, ci).transpose(0, 3, 1, 2).astype(np.float64))
+        off += n
+    return out
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 40, 40), (1, 37, 50), (3, 8, 33)])
+def test_forward_matches_oracle(kc, ctx, B, H, W):
+    ws = cnn.init_weights(3)
+    w32 = pack(ws)
+    assert w32.size == kc.kc_cnn_param_count()
+    x = np.random.default_rng(4).standard_normal((B, 1, H, W)).astype(np.float32)
+    wd = torch.as_tensor(w32, device="cuda")
+    xd = torch.as_tensor(x, device="cuda")
+    yd = torch.zeros_like(xd)
+    kc.kc_cnn_forward(ctx, wd, xd, yd, B, H, W)
+    y = yd.cpu().numpy().astype(np.float64)
+    yo, _ = cnn.forward_bf16_storage(unpack(w32, ws), x.astype(np.float64))
+    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 5e-3
+
+
+def test_gradients_match_oracle(kc, ctx):
+    B, H, W = 2, 24, 40
+    ws = cnn.init_weights(5)
+    w32 = pack(ws)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((B, 1, H, W)).astype(np.float32)
+    e = rng.standard_normal((B, 1, H, W)).astype(np.float32)
+    wd = torch.as_tensor(w32, device="cuda")
+    grad = torch.zeros_like(wd)
+    yd = torch.zeros((B, 1, H, W), dtype=torch.float32, device="cuda")
+    loss = kc.kc_cnn_train_step(ctx, wd, None, None, 0, 0.0, torch.as_tensor(x, device="cuda"),
+                                torch.as_tensor(e, device="cuda"), B, H, W, yd, grad)
+    Lo, go, _ = cnn.loss_and_grads_bf16_storage(unpack(w32, ws), x.astype(np.float64),
+                                                e.astype(np.float64))
+    assert abs(loss - Lo) <= 1e-3 * Lo
+    g = unpack(grad.cpu().numpy(), ws)
+    for li in range(6):
+        rel = np.linalg.norm(g[li] - go[li]) / np.linalg.norm(go[li])
+        assert rel <= 2e-2, (li, rel)
+    # and the BF16-storage gradients are close to the exact FP64 gradients
+    _, gx, _ = cnn.loss_and_grads(unpack(w32, ws), x.astype(np.float64), e.astype(np.float64))
+    for li in range(6):
+        assert np.linalg.norm(g[li] - gx[li]) / np.linalg.norm(gx[li]) <= 0.25
+
+
+def test_adam_steps_reduce_the_loss(kc, ctx):
+    B, H, W = 4, 32, 32
+    ws = cnn.init_weights(7)
+    wd = torch.as_tensor(pack(ws), device="cuda")
+    m = torch.zeros_like(wd)
+    v = torch.zeros_like(wd)
+    rng = np.random.default_rng(8)
+    x = torch.as_tensor(rng.standard_normal((B, 1, H, W)).astype(np.float32), device="cuda")
+    e = x.clone() * 0.5                       # learnable target: a scaled identity
+    yd = torch.zeros_like(x)
+    first = kc.kc_cnn_train_step(ctx, wd, m, v, 1, 1e-3, x, e, B, H, W, yd)
+    for t in range(2, 200):
+        last = kc.kc_cnn_train_step(ctx, wd, m, v, t, 1e-3, x, e, B, H, W, yd)
+    assert last < 0.3 * first
+
+
+def _varcoef(N, seed):
+    kappa, wind = varcoef_fields_2d(N, seed)
+    return convdiff_csr(N, 2, wind, kappa=kappa)
+
+
+def test_fgmres_identity_equals_gmres(kc, ctx):
+    Ah = _varcoef(32, 64)
+    b = gaussian_vector(Ah.m, 71)
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(b, device="cuda")
+    x1 = torch.zeros_like(bd)
+    x2 = torch.zeros_like(bd)
+    i1 = kc.gmres_solve(ctx, A, bd, x1, restart=40, rtol=1e-10)
+    i2 = kc.fgmres_solve(ctx, A, None, 32, 32, bd, x2, restart=40, rtol=1e-10)
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert abs(i1["iters"] - i2["iters"]) <= 1
+    assert i2["rel_resid_true"] <= 1e-10
+    xo, io = orc_gmres(Ah.to_scipy(), b, restart=40, rtol=1e-10, precond=lambda w: w.copy())
+    assert abs(io["iters"] - i2["iters"]) <= 1
+    assert np.linalg.norm(x2.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
+
+
+def near_identity_weights(seed, eps=0.02):
+    """net(x) = relu(x) - relu(-x) = x through channels 0 and 1, plus small random weights
+    everywhere: a nonlinear preconditioner close to the identity."""
+    rng = np.random.default_rng(seed)
+    ws = [eps * rng.standard_normal(w.shape) / 3.0 for w in cnn.init_weights(0)]
+    ws[0][0, 0, 1, 1] += 1.0
+    ws[0][1, 0, 1, 1] -= 1.0
+    for l in range(1, 5):
+        ws[l][0, 0, 1, 1] += 1.0
+        ws[l][1, 1, 1, 1] += 1.0
+    ws[5][0, 0, 1, 1] += 1.0
+    ws[5][0, 1, 1, 1] -= 1.0
+    return ws
+
+
+def test_fgmres_with_network_converges(kc, ctx):
+    """A perturbed identity network is a nonlinear preconditioner: flexible GMRES must
+    reach 1e-10 with an iteration count close to the oracle's FGMRES on the same
+    BF16-storage network (a random untrained network makes both stagnate)."""
+    N = 32
+    Ah = _varcoef(N, 65)
+    b = gaussian_vector(Ah.m, 72)
+    ws = near_identity_weights(9)
+    w32 = pack(ws)
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(b, device="cuda")
+    x = torch.zeros_like(bd)
+    info = kc.fgmres_solve(ctx, A, torch.as_tensor(w32, device="cuda"), N, N, bd, x,
+                           restart=40, rtol=1e-10)
+    assert info["status"] == 0 and info["rel_resid_true"] <= 1e-10
+    wo = unpack(w32, ws)
+
+    def M(w):
+        s = np.sqrt(np.mean(w * w))
+        y, _ = cnn.forward_bf16_storage(wo, (w / s).reshape(1, 1, N, N))
+        return y.reshape(-1) * s
+
+    _, io = orc_gmres(Ah.to_scipy(), b, restart=40, rtol=1e-10, precond=M)
+    assert io["rel_resid_true"] <= 1e-10
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.1 * io["iters"])
