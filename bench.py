@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-baselines", action="store_true")
+    p.add_argument("--no-solvers", action="store_true",
+                   help="skip the GMRES time-to-1e-10 runs (plain FP64 vs FP32/BF16 IR)")
     p.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1])
     p.add_argument("--no-check", action="store_true",
                    help="skip the loss-of-orthogonality / Arnoldi-relation check")
@@ -168,6 +170,52 @@ def quality(kc, ctx, A, st, m, n):
     R = AQ - (H.T @ Qv)
     rre = float(torch.linalg.norm(R)) / float(torch.linalg.norm(A.val))
     return loo, rre
+
+
+def solver_suite(kc, ctx, A, m, stream):
+    """GMRES time to a 1e-10 relative residual, measured with CUDA events around the
+    C-ABI call (device-resident b and x): config 1 (2D, 100^2, GMRES(30)) and, on the
+    config-2 matrix, plain FP64 DCGS2-GMRES(50) against FP32- and BF16-basis GMRES(50)
+    inner solves in FP64 iterative refinement (b ~ N(0,1), seed 1004)."""
+    import torch
+    from synth import config1_operator
+    from synth import config2_operator  # noqa: F401  (same operator as A)
+
+    def timed_solve(fn):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        info = fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        info["seconds"] = t0.elapsed_time(t1) / 1e3
+        return info
+
+    out = {}
+    A1h = config1_operator()
+    A1 = kc.DeviceCSR(A1h)
+    b1 = torch.as_tensor(gaussian_vector(A1h.m, 1001), device="cuda")
+    x1 = torch.zeros_like(b1)
+    kc.gmres_solve(ctx, A1, b1, x1, restart=30, rtol=1e-10)          # warm-up
+    x1.zero_()
+    out["config1_fp64_gmres30"] = timed_solve(
+        lambda: kc.gmres_solve(ctx, A1, b1, x1, restart=30, rtol=1e-10))
+    A32 = kc.DeviceCSR.__new__(kc.DeviceCSR)
+    A32.m, A32.nnz = A.m, A.nnz
+    A32.row_ptr, A32.col_idx = A.row_ptr, A.col_idx
+    A32.val = A.val.float()
+    A32.val_dtype = kc.KC_F32
+    A32.c = kc.kc_csr(A32.m, A32.nnz, A32.row_ptr.data_ptr(), A32.col_idx.data_ptr(),
+                      A32.val.data_ptr(), kc.KC_F32)
+    b = torch.as_tensor(gaussian_vector(m, 1004), device="cuda")
+    for name, prec in (("config4_fp64_gmres50", 0), ("config4_ir_fp32_gmres50", 1),
+                       ("config4_ir_bf16basis_gmres50", 2)):
+        x = torch.zeros_like(b)
+        out[name] = timed_solve(lambda: kc.gmres_solve(
+            ctx, A, b, x, restart=50, rtol=1e-10, precision=prec, A32=A32, inner_rtol=1e-4,
+            inner_max_cycles=3))
+    del A32
+    return out
 
 
 def blas_threads():
@@ -368,6 +416,10 @@ def main():
         e2e = {"value": ws * n * args.steps / (ms_e2e / 1e3), "unit": "steps/s",
                "h2d_bytes_per_step": m * 8, "d2h_bytes_per_step": n * (n + 1) * 8}
 
+    solvers = None
+    if not args.no_solvers:
+        solvers = solver_suite(kc, ctx, A, m, stream)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, dt, m_s = cpu_oracle_sample(n)
@@ -396,6 +448,7 @@ def main():
             "fp64_mode": ["all-fp64", "fp64-with-float-float-offload"][ctx.fp64_mode],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "same_gpu_baselines": baselines,
             "gpu_launches": launches, "clocks": clocks,
+            "gmres_time_to_1e-10": solvers,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -243,7 +243,9 @@ kc_status kc_cnn_train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_
                             float* y, float* grad, double* loss);
 
 /* Restarted flexible GMRES(opts->restart) with flexible DCGS2 and the network as right
- * preconditioner: M(w) = rms(w) net(w / rms(w)) on the H x W grid (m = H W, row-major).
+ * preconditioner M(w) = w + rms(w) net(w / rms(w)) on the H x W grid (m = H W,
+ * row-major): the identity plus the learned correction, so that directions the network
+ * maps to (nearly) zero are not lost to the flexible basis.
  * With w32 == NULL the preconditioner is the identity (the flexible machinery alone).
  * The flexible step stores zhat_k = M(w_k), applies A to it, keeps the single reduction of
  * Algorithm 4, and finalises H(:, k) = T + C_{k+1} (no H C / alpha correction); the update

@@ -85,13 +85,13 @@ __global__ void k_fgm_prep(const double* __restrict__ w, float* __restrict__ x, 
     x[i] = (float)(w[i] * inv);
 }
 
-// zhat = rms(w) * net(w / rms(w))
-__global__ void k_fgm_post(const float* __restrict__ y, double* __restrict__ z, int64_t m,
-                           const Scalars* __restrict__ sc) {
+// zhat = w + rms(w) * net(w / rms(w)): the identity plus the learned correction
+__global__ void k_fgm_post(const float* __restrict__ y, const double* __restrict__ w,
+                           double* __restrict__ z, int64_t m, const Scalars* __restrict__ sc) {
   const double rms = sqrt(sc->norm_sq / (double)m);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
-    z[i] = (double)y[i] * rms;
+    z[i] = w[i] + (double)y[i] * rms;
 }
 
 // y <- R^{-1} g, then y_j <- y_j / alpha_j (so that x += Zhat y)
@@ -288,7 +288,7 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
     for (int k = 0; k < n; k++) {
       double* zk = Z + (size_t)k * ld;
       sa.k = k;
-      if (w32) {       // zhat = rms(w) net(w / rms(w))
+      if (w32) {       // zhat = w + rms(w) net(w / rms(w))
         StepArgs sn = {};
         if ((s = launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_INIT, sn)) != KC_OK) return s;
         timing_begin(ctx, KID_OTHER);
@@ -296,7 +296,7 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
         KC_LAUNCHED(ctx);
         if ((s = cnn_forward(ctx, cb.wf, xin, yout, cb.acts, false, 1, H, W)) != KC_OK) return s;
         timing_begin(ctx, KID_OTHER);
-        k_fgm_post<<<g, 256, 0, ctx->stream>>>(yout, zk, m, ctx->scal);
+        k_fgm_post<<<g, 256, 0, ctx->stream>>>(yout, w, zk, m, ctx->scal);
         KC_LAUNCHED(ctx);
       } else {         // identity: zhat = w
         KC_CUDA(ctx, cudaMemcpyAsync(zk, w, m * 8, cudaMemcpyDeviceToDevice, ctx->stream));

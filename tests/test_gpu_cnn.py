@@ -154,11 +154,38 @@ def test_fgmres_with_network_converges(kc, ctx):
     assert info["status"] == 0 and info["rel_resid_true"] <= 1e-10
     wo = unpack(w32, ws)
 
-    def M(w):
+    def M(w):                       # the identity plus the network's correction
         s = np.sqrt(np.mean(w * w))
         y, _ = cnn.forward_bf16_storage(wo, (w / s).reshape(1, 1, N, N))
-        return y.reshape(-1) * s
+        return w + y.reshape(-1) * s
 
     _, io = orc_gmres(Ah.to_scipy(), b, restart=40, rtol=1e-10, precond=M)
     assert io["rel_resid_true"] <= 1e-10
     assert abs(info["iters"] - io["iters"]) <= max(3, 0.1 * io["iters"])
+
+
+def test_trained_network_reduces_fgmres_iterations(kc, ctx):
+    """Train on (residual, correction) pairs from plain GMRES solves on seeded operators
+    0..11 (32 x 32 grids), then solve held-out operators 64..66: the learned
+    preconditioner must cut the matvec count of plain GMRES(40).  (The size of the gain is
+    an empirical result with no closed form.)"""
+    from paper_2104_01253_gb300 import train as tr
+    N = 32
+    r, e = tr.generate_pairs(ctx, N, range(12), restart=40, max_cycles=30)
+    assert r.shape[0] >= 100
+    w, hist = tr.train(ctx, r, e, steps=600, batch=16, lr=2e-3, seed=0)
+    assert np.mean(hist[-50:]) < 0.8 * np.mean(hist[:20])
+    gains = []
+    for seed in (64, 65, 66):
+        Ah = tr.varcoef_operator(N, seed)
+        A = kc.DeviceCSR(Ah)
+        b = torch.as_tensor(gaussian_vector(Ah.m, 2000 + seed), device="cuda")
+        x1 = torch.zeros_like(b)
+        x2 = torch.zeros_like(b)
+        plain = kc.gmres_solve(ctx, A, b, x1, restart=40, rtol=1e-10)
+        flex = kc.fgmres_solve(ctx, A, w, N, N, b, x2, restart=40, rtol=1e-10)
+        assert plain["status"] == 0 and flex["status"] == 0
+        assert flex["rel_resid_true"] <= 1e-10
+        gains.append(plain["iters"] / flex["iters"])
+    print("held-out iteration ratios plain/learned:", gains)
+    assert min(gains) > 1.0
