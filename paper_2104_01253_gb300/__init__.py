@@ -52,6 +52,10 @@ class Context:
         """0: all FP64 products; 1: FP64 with float-float offload (default)."""
         self.check(self.lib.kc_set_fp64_mode(self.handle, mode))
 
+    def set_staged(self, on: bool):
+        """Stage the FP64 basis passes through shared memory with bulk copies."""
+        self.check(self.lib.kc_set_staged(self.handle, 1 if on else 0))
+
     @property
     def fp64_mode(self) -> int:
         return int(self.lib.kc_get_fp64_mode(self.handle))

@@ -56,6 +56,7 @@ _SIGS = {
     "kc_set_stream": ([_P, _P], C.c_int),
     "kc_set_fp64_mode": ([_P, C.c_int], C.c_int),
     "kc_get_fp64_mode": ([_P], C.c_int),
+    "kc_set_staged": ([_P, C.c_int], C.c_int),
     "kc_last_error": ([_P], C.c_char_p),
     "kc_device_info": ([_P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "kc_launch_count": ([_P], C.c_int64),

@@ -162,6 +162,12 @@ kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode) {
 
 int kc_get_fp64_mode(const kc_ctx* ctx) { return ctx ? ctx->fp64_mode : -1; }
 
+kc_status kc_set_staged(kc_ctx* ctx, int on) {
+  if (!ctx || on < 0 || on > 1) return KC_ERR_INVALID_ARG;
+  ctx->staged = on;
+  return KC_OK;
+}
+
 kc_status kc_set_stream(kc_ctx* ctx, void* cuda_stream) {
   if (!ctx) return KC_ERR_INVALID_ARG;
   ctx->stream = (cudaStream_t)cuda_stream;

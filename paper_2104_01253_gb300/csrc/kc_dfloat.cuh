@@ -1,0 +1,50 @@
+// Float-float helpers for the FP64 offload mode: splitting a double into two floats with
+// integer operations (no FP64 instruction), an exact-product multiply-accumulate, and the
+// exact float -> double widening, also by integer operations.
+#pragma once
+
+#include "kc_internal.cuh"
+
+namespace kc {
+
+// x ~ hi + lo (to 2^-46 relative) using integer operations only; returns false when x is
+// outside the range where the split is exact enough (then use FP64 for this element).
+__device__ __forceinline__ bool split_df(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int H = (unsigned int)(b >> 32), L = (unsigned int)b;
+  const unsigned int e = (H >> 20) & 0x7ffu;
+  const unsigned int sgn = H & 0x80000000u;
+  const unsigned int hb = sgn | ((e - 896u) << 23) | ((H & 0xfffffu) << 3) | (L >> 29);
+  const float rf = __uint_as_float(0x4b000000u | ((L >> 6) & 0x7fffffu)) - 8388608.0f;
+  const float sc = __uint_as_float((e - 942u) << 23);
+  const bool zero = e == 0u;
+  hi = zero ? 0.0f : __uint_as_float(hb);
+  lo = zero ? 0.0f : __uint_as_float(__float_as_uint(rf * sc) | sgn);
+  return zero || (e - 943u) <= (1120u - 943u);
+}
+
+// (sh, sl) += (ah + al)(bh + bl), float-float with an exact leading product
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
+                                       float bl) {
+  const float p = ah * bh;
+  const float pe = fmaf(ah, bh, -p);
+  const float c = fmaf(ah, bl, fmaf(al, bh, pe));
+  const float t = sh + p;
+  const float bp = t - sh;
+  const float err = (sh - (t - bp)) + (p - bp);
+  sh = t;
+  sl += err + c;
+}
+
+// double from a float, by integer operations (exact for normal floats and zero)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+}  // namespace kc

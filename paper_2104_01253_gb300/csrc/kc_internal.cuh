@@ -99,6 +99,7 @@ struct kc_ctx {
   size_t cnn_ws_len;
   int64_t launches;
   int fp64_mode;           // 0: every product in FP64; 1: FP64 with float-float offload
+  int staged;              // 1: FP64 basis passes staged through shared memory by bulk copies
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
   kc::TimingRec* trec;
@@ -156,6 +157,8 @@ kc_status launch_scale_to(kc_ctx* ctx, const void* x, void* qcol, int q_dtype, i
 kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_t m,
                         int vec_dtype);
 kc_status ensure_workspace(kc_ctx* ctx, size_t bytes);
+kc_status launch_update_staged(kc_ctx* ctx, double* Q, int64_t ldq, int k, double* w,
+                               const double* v, int64_t m);
 // convolutional preconditioner (kc_cnn.cu)
 kc_status cnn_prep(kc_ctx* ctx, const float* w32, __nv_bfloat16* wf, __nv_bfloat16* wt);
 kc_status cnn_forward(kc_ctx* ctx, const __nv_bfloat16* wf, const float* x, float* y,

@@ -7,6 +7,7 @@
 // FP64 across warps and CTAs).  Basis element types: FP64, FP32, or BF16 (FP32 vectors).
 // Every kernel streams 16-byte groups of rows: 2 rows of FP64, 4 rows of FP32.
 #include "kc_internal.cuh"
+#include "kc_dfloat.cuh"
 
 namespace kc {
 
@@ -497,46 +498,6 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // the FP64 path.
 // ----------------------------------------------------------------------------------------
 
-// x ~ hi + lo (to 2^-46 relative) using integer operations only; returns false when x is
-// outside the range where the split is exact enough (then use FP64 for this element).
-__device__ __forceinline__ bool split_df(double x, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int H = (unsigned int)(b >> 32), L = (unsigned int)b;
-  const unsigned int e = (H >> 20) & 0x7ffu;
-  const unsigned int sgn = H & 0x80000000u;
-  const unsigned int hb = sgn | ((e - 896u) << 23) | ((H & 0xfffffu) << 3) | (L >> 29);
-  const float rf = __uint_as_float(0x4b000000u | ((L >> 6) & 0x7fffffu)) - 8388608.0f;
-  const float sc = __uint_as_float((e - 942u) << 23);
-  const bool zero = e == 0u;
-  hi = zero ? 0.0f : __uint_as_float(hb);
-  lo = zero ? 0.0f : __uint_as_float(__float_as_uint(rf * sc) | sgn);
-  return zero || (e - 943u) <= (1120u - 943u);
-}
-
-// (sh, sl) += (ah + al)(bh + bl), float-float with an exact leading product
-__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
-                                       float bl) {
-  const float p = ah * bh;
-  const float pe = fmaf(ah, bh, -p);
-  const float c = fmaf(ah, bl, fmaf(al, bh, pe));
-  const float t = sh + p;
-  const float bp = t - sh;
-  const float err = (sh - (t - bp)) + (p - bp);
-  sh = t;
-  sl += err + c;
-}
-
-// double from a float, by integer operations (exact for normal floats and zero)
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int e = (u >> 23) & 0xffu;
-  if (e == 0u) return 0.0;
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)d);
-}
-
 // One group of two rows of the offloaded reduction: C in FP64, S in float-float.
 template <int TPW>
 __device__ __forceinline__ void f64x_group(int warp, int k, const double (&xv)[2],
@@ -552,7 +513,9 @@ __device__ __forceinline__ void f64x_group(int warp, int k, const double (&xv)[2
       ac[i] = fma(qv[i][1], xv[1], ac[i]);
       float qh[2], ql[2];
       const bool qs = split_df(qv[i][0], qh[0], ql[0]) & split_df(qv[i][1], qh[1], ql[1]);
-      if (qs && ys) {
+      // warp-uniform choice: a per-lane branch is if-converted, and a predicated-off
+      // FP64 FMA still occupies the FP64 pipe
+      if (__all_sync(__activemask(), qs && ys)) {
         df_mac(sh[i], sl[i], qh[0], ql[0], yh[0], yl[0]);
         df_mac(sh[i], sl[i], qh[1], ql[1], yh[1], yl[1]);
       } else {
@@ -696,11 +659,14 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
       for (int j = 0; j < 2; j++) {
         wn[0] = fma(-q[j][0], sT[i + j], wn[0]);
         wn[1] = fma(-q[j][1], sT[i + j], wn[1]);
-#pragma unroll
-        for (int r = 0; r < 2; r++) {
-          float h0, l0;
-          if (split_df(q[j][r], h0, l0) && cok) df_mac(zh[r], zl[r], h0, l0, cH[i + j], cL[i + j]);
-          else u64[r] = fma(-q[j][r], sC[i + j], u64[r]);
+        float h0, l0, h1, l1;
+        const bool okj = split_df(q[j][0], h0, l0) & split_df(q[j][1], h1, l1) & cok;
+        if (__all_sync(__activemask(), okj)) {        // warp-uniform (see k_reduce_f64x)
+          df_mac(zh[0], zl[0], h0, l0, cH[i + j], cL[i + j]);
+          df_mac(zh[1], zl[1], h1, l1, cH[i + j], cL[i + j]);
+        } else {
+          u64[0] = fma(-q[j][0], sC[i + j], u64[0]);
+          u64[1] = fma(-q[j][1], sC[i + j], u64[1]);
         }
       }
     }
@@ -709,11 +675,14 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
       load_q(Q + (int64_t)i * ldq, g, q0);
       wn[0] = fma(-q0[0], sT[i], wn[0]);
       wn[1] = fma(-q0[1], sT[i], wn[1]);
-#pragma unroll
-      for (int r = 0; r < 2; r++) {
-        float h0, l0;
-        if (split_df(q0[r], h0, l0) && cok) df_mac(zh[r], zl[r], h0, l0, cH[i], cL[i]);
-        else u64[r] = fma(-q0[r], sC[i], u64[r]);
+      float h0, l0, h1, l1;
+      const bool oki = split_df(q0[0], h0, l0) & split_df(q0[1], h1, l1) & cok;
+      if (__all_sync(__activemask(), oki)) {
+        df_mac(zh[0], zl[0], h0, l0, cH[i], cL[i]);
+        df_mac(zh[1], zl[1], h1, l1, cH[i], cL[i]);
+      } else {
+        u64[0] = fma(-q0[0], sC[i], u64[0]);
+        u64[1] = fma(-q0[1], sC[i], u64[1]);
       }
     }
     double qn[2], wo[2];
@@ -1001,6 +970,8 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
 
 kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, int k, void* w,
                               const void* v, int64_t m, int vec_dtype) {
+  if (q_dtype == KC_F64 && ctx->staged)
+    return launch_update_staged(ctx, (double*)Q, ldq, k, (double*)w, (const double*)v, m);
   const int R = vec_dtype == KC_F64 ? 2 : 4;
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_UPDATE);
