@@ -23,6 +23,12 @@ __device__ __forceinline__ bool split_df(double x, float& hi, float& lo) {
   return zero || (e - 943u) <= (1120u - 943u);
 }
 
+// the range test of split_df alone: zero, or a magnitude in [2^-80, 2^98)
+__device__ __forceinline__ bool df_in_range(double x) {
+  const unsigned int e = ((unsigned int)((unsigned long long)__double_as_longlong(x) >> 52)) & 0x7ffu;
+  return e == 0u || (e - 943u) <= (1120u - 943u);
+}
+
 // (sh, sl) += (ah + al)(bh + bl), float-float with an exact leading product
 __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
                                        float bl) {

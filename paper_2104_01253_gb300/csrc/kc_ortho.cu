@@ -498,24 +498,24 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // the FP64 path.
 // ----------------------------------------------------------------------------------------
 
-// One group of two rows of the offloaded reduction: C in FP64, S in float-float.
-template <int TPW>
+// One group of two rows of the offloaded reduction: C in FP64; S in float-float (OFF) or
+// in FP64 (!OFF, the path for operands outside the float-float range).
+template <int TPW, bool OFF>
 __device__ __forceinline__ void f64x_group(int warp, int k, const double (&xv)[2],
                                            const double (&yv)[2], const double (&qv)[TPW][2],
                                            double* ac, double* as64, float* sh, float* sl) {
   float yh[2], yl[2];
-  const bool ys = split_df(yv[0], yh[0], yl[0]) & split_df(yv[1], yh[1], yl[1]);
+  if (OFF) { split_df(yv[0], yh[0], yl[0]); split_df(yv[1], yh[1], yl[1]); }
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
     const int t = warp + RED_WARPS * i;
     if (t < k) {
       ac[i] = fma(qv[i][0], xv[0], ac[i]);
       ac[i] = fma(qv[i][1], xv[1], ac[i]);
-      float qh[2], ql[2];
-      const bool qs = split_df(qv[i][0], qh[0], ql[0]) & split_df(qv[i][1], qh[1], ql[1]);
-      // warp-uniform choice: a per-lane branch is if-converted, and a predicated-off
-      // FP64 FMA still occupies the FP64 pipe
-      if (__all_sync(__activemask(), qs && ys)) {
+      if (OFF) {
+        float qh[2], ql[2];
+        split_df(qv[i][0], qh[0], ql[0]);
+        split_df(qv[i][1], qh[1], ql[1]);
         df_mac(sh[i], sl[i], qh[0], ql[0], yh[0], yl[0]);
         df_mac(sh[i], sl[i], qh[1], ql[1], yh[1], yl[1]);
       } else {
@@ -531,7 +531,22 @@ __device__ __forceinline__ void f64x_group(int warp, int k, const double (&xv)[2
   }
 }
 
-// Fused DCGS2 reduction, FP64 with offload (EPI_DCGS2 only: NRHS = 2)
+// true when every operand of a group lies in the float-float range
+template <int TPW>
+__device__ __forceinline__ bool f64x_in_range(int warp, int k, const double (&yv)[2],
+                                              const double (&qv)[TPW][2]) {
+  bool ok = df_in_range(yv[0]) & df_in_range(yv[1]);
+#pragma unroll
+  for (int i = 0; i < TPW; i++)
+    if (warp + RED_WARPS * i < k) ok = ok & df_in_range(qv[i][0]) & df_in_range(qv[i][1]);
+  return ok;
+}
+
+// Fused DCGS2 reduction, FP64 with offload (EPI_DCGS2 only: NRHS = 2).  The choice
+// between the float-float and the FP64 evaluation of S is made once per loop iteration,
+// warp-uniformly, around the whole iteration: a small per-column branch is turned into
+// predicated code by the compiler, and an FP64 FMA issued with every lane predicated off
+// still holds the FP64 pipe for its full issue time.
 template <int TPW>
 __global__ void __launch_bounds__(RED_THREADS)
 k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
@@ -564,8 +579,14 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
         load_q(Q + (int64_t)t * ldq, g + 32, qb[i]);
       }
     }
-    f64x_group<TPW>(warp, k, xa, ya, qa, ac, as64, sh, sl);
-    f64x_group<TPW>(warp, k, xb, yb, qb, ac, as64, sh, sl);
+    const bool ok = f64x_in_range<TPW>(warp, k, ya, qa) & f64x_in_range<TPW>(warp, k, yb, qb);
+    if (__builtin_expect(__all_sync(__activemask(), ok), 1)) {
+      f64x_group<TPW, true>(warp, k, xa, ya, qa, ac, as64, sh, sl);
+      f64x_group<TPW, true>(warp, k, xb, yb, qb, ac, as64, sh, sl);
+    } else {
+      f64x_group<TPW, false>(warp, k, xa, ya, qa, ac, as64, sh, sl);
+      f64x_group<TPW, false>(warp, k, xb, yb, qb, ac, as64, sh, sl);
+    }
   }
   if (g < g1) {
     double xa[2], ya[2], qa[TPW][2];
@@ -576,7 +597,10 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
       const int t = warp + RED_WARPS * i;
       if (t < k) load_q(Q + (int64_t)t * ldq, g, qa[i]);
     }
-    f64x_group<TPW>(warp, k, xa, ya, qa, ac, as64, sh, sl);
+    if (__all_sync(__activemask(), f64x_in_range<TPW>(warp, k, ya, qa)))
+      f64x_group<TPW, true>(warp, k, xa, ya, qa, ac, as64, sh, sl);
+    else
+      f64x_group<TPW, false>(warp, k, xa, ya, qa, ac, as64, sh, sl);
   }
   if (blockIdx.x == gridDim.x - 1) {           // ragged tail (m odd): FP64
     for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
@@ -606,18 +630,41 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
   reduce_epilogue(partials, k, 2, sc, EPI_DCGS2, sa);
 }
 
+// Two basis columns of the offloaded update for one group of two rows: u -= Q C in
+// float-float (OFF) or FP64 (!OFF).
+template <bool OFF>
+__device__ __forceinline__ void f64x_update_pair(const double (&q)[2][2], const double* sC,
+                                                 const float* cH, const float* cL, int i,
+                                                 double (&u64)[2], float (&zh)[2],
+                                                 float (&zl)[2]) {
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    if (OFF) {
+      float h0, l0, h1, l1;
+      split_df(q[j][0], h0, l0);
+      split_df(q[j][1], h1, l1);
+      df_mac(zh[0], zl[0], h0, l0, cH[i + j], cL[i + j]);
+      df_mac(zh[1], zl[1], h1, l1, cH[i + j], cL[i + j]);
+    } else {
+      u64[0] = fma(-q[j][0], sC[i + j], u64[0]);
+      u64[1] = fma(-q[j][1], sC[i + j], u64[1]);
+    }
+  }
+}
+
 // DCGS2 update, FP64 with offload: u = w - Q C in float-float (C scaled by a power of two
-// into float range), w <- v/alpha - Q T - q T_k in FP64.
+// into float range), w <- v/alpha - Q T - q T_k in FP64.  The float-float / FP64 choice is
+// warp-uniform per pair of columns (see k_reduce_f64x).
 __global__ void __launch_bounds__(UPD_THREADS)
 k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__ w,
                     const double* __restrict__ v, int64_t m, const Scalars* __restrict__ sc) {
   if (sc->stop) return;
-  __shared__ double sC[NMAX], sT[NMAX + 1];
-  __shared__ float cH[NMAX], cL[NMAX];
+  __shared__ double sC[NMAX + 1], sT[NMAX + 1];
+  __shared__ float cH[NMAX + 1], cL[NMAX + 1];
   __shared__ double s_scale;
   __shared__ int s_cok;
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
-    if (i < k) sC[i] = sc->C[i];
+    sC[i] = i < k ? sc->C[i] : 0.0;            // sC[k] = 0 pads an odd k to a column pair
     sT[i] = sc->T[i];
   }
   __syncthreads();
@@ -631,7 +678,7 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
   }
   __syncthreads();
   const double inv_scale = 1.0 / s_scale;     // exact: a power of two
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
     float h, l;
     if (!split_df(sC[i] * inv_scale, h, l)) { h = 0.0f; l = 0.0f; if (sC[i] != 0.0) s_cok = 0; }
     cH[i] = h;
@@ -659,31 +706,26 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
       for (int j = 0; j < 2; j++) {
         wn[0] = fma(-q[j][0], sT[i + j], wn[0]);
         wn[1] = fma(-q[j][1], sT[i + j], wn[1]);
-        float h0, l0, h1, l1;
-        const bool okj = split_df(q[j][0], h0, l0) & split_df(q[j][1], h1, l1) & cok;
-        if (__all_sync(__activemask(), okj)) {        // warp-uniform (see k_reduce_f64x)
-          df_mac(zh[0], zl[0], h0, l0, cH[i + j], cL[i + j]);
-          df_mac(zh[1], zl[1], h1, l1, cH[i + j], cL[i + j]);
-        } else {
-          u64[0] = fma(-q[j][0], sC[i + j], u64[0]);
-          u64[1] = fma(-q[j][1], sC[i + j], u64[1]);
-        }
       }
+      const bool ok = cok & df_in_range(q[0][0]) & df_in_range(q[0][1]) &
+                      df_in_range(q[1][0]) & df_in_range(q[1][1]);
+      if (__builtin_expect(__all_sync(__activemask(), ok), 1))
+        f64x_update_pair<true>(q, sC, cH, cL, i, u64, zh, zl);
+      else
+        f64x_update_pair<false>(q, sC, cH, cL, i, u64, zh, zl);
     }
-    for (; i < k; i++) {
-      double q0[2];
-      load_q(Q + (int64_t)i * ldq, g, q0);
-      wn[0] = fma(-q0[0], sT[i], wn[0]);
-      wn[1] = fma(-q0[1], sT[i], wn[1]);
-      float h0, l0, h1, l1;
-      const bool oki = split_df(q0[0], h0, l0) & split_df(q0[1], h1, l1) & cok;
-      if (__all_sync(__activemask(), oki)) {
-        df_mac(zh[0], zl[0], h0, l0, cH[i], cL[i]);
-        df_mac(zh[1], zl[1], h1, l1, cH[i], cL[i]);
-      } else {
-        u64[0] = fma(-q0[0], sC[i], u64[0]);
-        u64[1] = fma(-q0[1], sC[i], u64[1]);
-      }
+    if (i < k) {                        // odd k: the last column, paired with a zero one
+      double q[2][2];
+      load_q(Q + (int64_t)i * ldq, g, q[0]);
+      q[1][0] = 0.0;
+      q[1][1] = 0.0;
+      wn[0] = fma(-q[0][0], sT[i], wn[0]);
+      wn[1] = fma(-q[0][1], sT[i], wn[1]);
+      const bool ok = cok & df_in_range(q[0][0]) & df_in_range(q[0][1]);
+      if (__all_sync(__activemask(), ok))
+        f64x_update_pair<true>(q, sC, cH, cL, i, u64, zh, zl);
+      else
+        f64x_update_pair<false>(q, sC, cH, cL, i, u64, zh, zl);
     }
     double qn[2], wo[2];
 #pragma unroll
