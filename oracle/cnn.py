@@ -2,15 +2,26 @@
 
 Not in the paper (an addition on top of its GMRES use).  Layers 1..6 map channels
 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 with 3x3 kernels, zero padding and no bias; a ReLU
-follows layers 1..5.  With no bias the network is positively homogeneous, so the
-preconditioner M(r) = rms(r) * net(r / rms(r)) equals net(r) in exact arithmetic; the
-scaling only keeps reduced-precision activations in range.
+follows layers 1..5.  With no bias the network is positively homogeneous:
+s net(x / s) = net(x) for s > 0 in exact arithmetic, so scaling its input by the RMS
+only keeps reduced-precision activations in range.
 
-Training loss for a batch of (residual r_b, correction e_b) pairs:
-    L = (1/B) sum_b ||net(r_b) - e_b||^2 / ||e_b||^2.
+Two training losses for a batch of (residual r_b, correction e_b) pairs, A e_b = r_b:
+    regression:  L = (1/B) sum_b ||net(r_b) - e_b||^2 / ||e_b||^2;
+    residual:    L = (1/B) sum_b ||A (x_b + net(x_b)) - r_b||^2 / ||r_b||^2, with
+                 x_b = D^{-1} r_b the Jacobi-scaled residual: the error of the correction
+                 M(r_b) - e_b measured in the norm ||A .||, which needs no e_b.
+The preconditioner that the residual loss trains (fgmres):
+    M(w) = u + s net(u / s),   u = D^{-1} w,  s = rms(u),
+the Jacobi step plus the learned correction (D = diag(A)).
 
-Pins: tests/test_oracle_cnn.py (central finite differences of L for weight and input
-gradients; a 1x1-equivalent kernel against a hand-computed stencil; homogeneity).
+Pins: tests/test_oracle_cnn.py (central finite differences of both losses for weight and
+input gradients; a 1x1-equivalent kernel against a hand-computed stencil; homogeneity;
+a network that computes c x exactly, giving closed-form losses and M(w) = (1 + c) D^{-1} w;
+zero weights giving the Jacobi preconditioner).
+
+This module is test infrastructure: only tests, the smoke check and the CPU baseline of
+the benchmark use it.
 """
 from __future__ import annotations
 
@@ -82,16 +93,6 @@ def loss_and_grads(ws, r, e):
     return L, grads, g
 
 
-def apply_preconditioner(ws, r_vec, H, W):
-    """M(r) for one residual vector (length H*W, row-major grid), with RMS scaling."""
-    x = np.asarray(r_vec, dtype=np.float64).reshape(1, 1, H, W)
-    s = np.sqrt(np.mean(x * x))
-    if s == 0.0:
-        return np.zeros(H * W)
-    y, _ = forward(ws, x / s)
-    return (y * s).reshape(H * W)
-
-
 def _round_bf16(x):
     """Round float64 values to the nearest bfloat16 (ties to even), as float64."""
     f = np.asarray(x, dtype=np.float32)
@@ -132,3 +133,59 @@ def loss_and_grads_bf16_storage(ws, r, e):
         gW, g = conv3x3_backward(acts[li], wb[li], g)
         grads[li] = gW
     return L, grads, y
+
+
+def backward(ws, acts, gy, bf16=False):
+    """dL/dW per layer and dL/dx from dL/dy, after forward (or forward_bf16_storage when
+    `bf16`: BF16 weights and BF16-rounded hidden-layer gradients, as on the GPU)."""
+    wl = [_round_bf16(W) for W in ws] if bf16 else ws
+    g = gy
+    grads = [None] * len(ws)
+    for li in range(len(ws) - 1, -1, -1):
+        if li < len(ws) - 1:
+            g = g * (acts[li + 1] > 0.0)
+            if bf16:
+                g = _round_bf16(g)
+        gW, g = conv3x3_backward(acts[li], wl[li], g)
+        grads[li] = gW
+    return grads, g
+
+
+def residual_loss_and_grads(ws, x, r, A, bf16=False):
+    """Residual loss of a batch (see the module docstring): x, r (B, 1, H, W) with x the
+    network input and r the residual it should remove; A a sparse or dense (H W x H W)
+    operator shared by the batch.  Returns L, dL/dW per layer, dL/dx (through z = x + y)
+    and the network output y."""
+    B = x.shape[0]
+    y, acts = forward_bf16_storage(ws, x) if bf16 else forward(ws, x)
+    z = (x + y).reshape(B, -1)
+    rr = r.reshape(B, -1)
+    res = np.stack([A @ z[b] for b in range(B)]) - rr
+    rn = np.sum(rr * rr, axis=1)
+    L = float(np.mean(np.sum(res * res, axis=1) / rn))
+    AT = A.T
+    gy = np.stack([AT @ res[b] for b in range(B)]) * (2.0 / B) / rn[:, None]
+    gy = gy.reshape(y.shape)
+    grads, gx = backward(ws, acts, gy, bf16=bf16)
+    return L, grads, gx + gy, y
+
+
+def jacobi_network_preconditioner(ws, w, dinv, H, W, bf16=False):
+    """M(w) = u + s net(u / s) with u = D^{-1} w (dinv: the inverse diagonal) and
+    s = rms(u); the Jacobi step alone when the network output is zero."""
+    u = np.asarray(w, dtype=np.float64) * dinv
+    s = np.sqrt(np.mean(u * u))
+    if s == 0.0:
+        return u
+    x = (u / s).reshape(1, 1, H, W)
+    y, _ = forward_bf16_storage(ws, x) if bf16 else forward(ws, x)
+    return u + y.reshape(H * W) * s
+
+
+def inverse_diagonal(A):
+    """1 / a_ii for every row of a scipy sparse matrix (1 where the diagonal is 0)."""
+    d = np.asarray(A.diagonal(), dtype=np.float64)
+    out = np.ones_like(d)
+    nz = d != 0.0
+    out[nz] = 1.0 / d[nz]
+    return out
