@@ -191,8 +191,14 @@ typedef struct {
   double rtol;            /* relative residual target ||b - A x|| / ||b|| */
   double inner_rtol;      /* IR: inner solve tolerance (relative to its right-hand side) */
   int32_t inner_max_cycles; /* IR: cycles per inner solve */
-  int32_t pad;
+  int32_t precond;        /* fgmres_solve only: a kc_precond_kind (gmres_solve ignores it) */
 } kc_gmres_opts;
+
+/* Right preconditioner of fgmres_solve. */
+typedef enum {
+  KC_PREC_AUTO = 0,       /* the network when weights are given, else the identity */
+  KC_PREC_JACOBI = 1      /* the Jacobi step D^{-1} w alone (network weights ignored) */
+} kc_precond_kind;
 
 typedef struct {
   int32_t iters;          /* matvecs with A (inner iterations for IR) */
@@ -223,6 +229,10 @@ typedef struct {
  * resid: HOST arrays of length nev (largest real part first).  nconv, restarts,
  * matvecs: host outputs (may be NULL).  The small dense Schur step runs on the GPU in
  * FP64.  Synchronises. */
+kc_status krylov_schur_eigs(kc_ctx* ctx, const kc_csr* A, const double* v0,
+                            const kc_ks_opts* opts, double* eig_re, double* eig_im,
+                            double* resid, int* nconv, int* restarts, int* matvecs);
+
 /* ---- learned preconditioner and flexible GMRES (additions; not in the paper) ----------- */
 
 /* The network: 6 layers of 3x3 convolutions, channels 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1,
@@ -246,11 +256,26 @@ kc_status kc_cnn_train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_
                             float lr, const float* x, const float* e, int B, int H, int W,
                             float* y, float* grad, double* loss);
 
-/* Restarted flexible GMRES(opts->restart) with flexible DCGS2 and the network as right
- * preconditioner M(w) = w + rms(w) net(w / rms(w)) on the H x W grid (m = H W,
- * row-major): the identity plus the learned correction, so that directions the network
- * maps to (nearly) zero are not lost to the flexible basis.
- * With w32 == NULL the preconditioner is the identity (the flexible machinery alone).
+/* The same training step with the residual loss of the preconditioner that fgmres_solve
+ * applies: for network inputs x_b (the Jacobi-scaled residuals D^{-1} r_b divided by a
+ * common factor s_b) and residuals r_b (divided by the same s_b),
+ *   L = (1/B) sum_b ||A (x_b + net(x_b)) - r_b||^2 / ||r_b||^2,
+ * i.e. ||A (M(r_b) - e_b)||^2 / ||r_b||^2 for the exact correction e_b = A^{-1} r_b.
+ * A: FP64 CSR operator with m = H W (device), shared by the batch.  dL/dy is formed as
+ * (2/B) A^T res_b / ||r_b||^2 by scattering along the rows of A (FP32 atomics: the
+ * summation order, and so the last bits of grad, vary from run to run). */
+kc_status kc_cnn_train_step_residual(kc_ctx* ctx, float* w32, float* adam_m, float* adam_v,
+                                     int64_t t, float lr, const kc_csr* A, const float* x,
+                                     const float* r, int B, int H, int W, float* y, float* grad,
+                                     double* loss);
+
+/* Restarted flexible GMRES(opts->restart) with flexible DCGS2 and a right preconditioner
+ * chosen by opts->precond:
+ *   KC_PREC_AUTO with w32 != NULL: the network on the H x W grid (m = H W, row-major),
+ *     M(w) = u + s net(u / s), u = D^{-1} w, s = rms(u), D = diag(A) (rows with no or a
+ *     zero diagonal entry are not scaled): the Jacobi step plus the learned correction;
+ *   KC_PREC_AUTO with w32 == NULL: the identity (the flexible machinery alone);
+ *   KC_PREC_JACOBI: M(w) = D^{-1} w.
  * The flexible step stores zhat_k = M(w_k), applies A to it, keeps the single reduction of
  * Algorithm 4, and finalises H(:, k) = T + C_{k+1} (no H C / alpha correction); the update
  * is x += sum_k zhat_k y_k / alpha_k.  FP64 vectors; b, x device, x = x0 on entry.
@@ -258,10 +283,6 @@ kc_status kc_cnn_train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_
 kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, int W,
                        const double* b, double* x, const kc_gmres_opts* opts,
                        kc_gmres_info* info);
-
-kc_status krylov_schur_eigs(kc_ctx* ctx, const kc_csr* A, const double* v0,
-                            const kc_ks_opts* opts, double* eig_re, double* eig_im,
-                            double* resid, int* nconv, int* restarts, int* matvecs);
 
 #ifdef __cplusplus
 }

@@ -249,10 +249,26 @@ def kc_cnn_train_step(ctx: Context, w32, adam_m, adam_v, t: int, lr: float, x, e
     return loss.value
 
 
+def kc_cnn_train_step_residual(ctx: Context, w32, adam_m, adam_v, t: int, lr: float,
+                               A: DeviceCSR, x, r, B: int, H: int, W: int, y, grad=None):
+    """One step on the residual loss ||A (x + net(x)) - r||^2 / ||r||^2 (x: the
+    Jacobi-scaled residuals, r: the residuals, both per sample scaled alike); returns the
+    batch loss."""
+    loss = C.c_double()
+    ctx.check(ctx.lib.kc_cnn_train_step_residual(
+        ctx.handle, _ptr(w32), _ptr(adam_m), _ptr(adam_v), t, lr, C.byref(A.c), _ptr(x),
+        _ptr(r), B, H, W, _ptr(y), _ptr(grad), C.byref(loss)))
+    return loss.value
+
+
+PREC_AUTO, PREC_JACOBI = 0, 1
+
+
 def fgmres_solve(ctx: Context, A: DeviceCSR, w32, H: int, W: int, b, x, restart=40,
-                 rtol=1e-10, maxit=100000):
-    """Flexible GMRES with the network (w32; None = identity) as right preconditioner."""
-    opts = kc_gmres_opts(restart, maxit, 0, 0, rtol, 0.0, 0, 0)
+                 rtol=1e-10, maxit=100000, precond: int = PREC_AUTO):
+    """Flexible GMRES with a right preconditioner: the Jacobi-scaled network (w32), the
+    identity (w32 None) or, with precond=PREC_JACOBI, the Jacobi step alone."""
+    opts = kc_gmres_opts(restart, maxit, 0, 0, rtol, 0.0, 0, precond)
     info = kc_gmres_info()
     st = ctx.lib.fgmres_solve(ctx.handle, C.byref(A.c), _ptr(w32), H, W, _ptr(b), _ptr(x),
                               C.byref(opts), C.byref(info))

@@ -35,7 +35,7 @@ class kc_arnoldi(C.Structure):
 class kc_gmres_opts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("rtol", C.c_double), ("inner_rtol", C.c_double),
-                ("inner_max_cycles", C.c_int32), ("pad", C.c_int32)]
+                ("inner_max_cycles", C.c_int32), ("precond", C.c_int32)]
 
 
 class kc_gmres_info(C.Structure):
@@ -79,6 +79,9 @@ _SIGS = {
     "kc_cnn_forward": ([_P, _P, _P, _P, C.c_int, C.c_int, C.c_int], C.c_int),
     "kc_cnn_train_step": ([_P, _P, _P, _P, C.c_int64, C.c_float, _P, _P, C.c_int, C.c_int,
                            C.c_int, _P, _P, C.POINTER(C.c_double)], C.c_int),
+    "kc_cnn_train_step_residual": ([_P, _P, _P, _P, C.c_int64, C.c_float, C.POINTER(kc_csr), _P,
+                                    _P, C.c_int, C.c_int, C.c_int, _P, _P,
+                                    C.POINTER(C.c_double)], C.c_int),
     "fgmres_solve": ([_P, C.POINTER(kc_csr), _P, C.c_int, C.c_int, _P, _P,
                       C.POINTER(kc_gmres_opts), C.POINTER(kc_gmres_info)], C.c_int),
     "krylov_schur_eigs": ([_P, C.POINTER(kc_csr), _P, C.POINTER(kc_ks_opts),

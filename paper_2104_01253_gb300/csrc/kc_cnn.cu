@@ -413,6 +413,55 @@ k_cnn_loss_grad(const float* __restrict__ y, const float* __restrict__ e,
     g[b * npix + i] = (float)(sc * ((double)y[b * npix + i] - (double)e[b * npix + i]));
 }
 
+// Residual loss (the preconditioner's training loss on an operator A shared by the batch):
+// res_b = A (x_b + y_b) - r_b; sums[2b] += ||res_b||^2, sums[2b+1] += ||r_b||^2.
+__global__ void __launch_bounds__(256)
+k_cnn_res_sums(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+               const double* __restrict__ av, const float* __restrict__ x,
+               const float* __restrict__ y, const float* __restrict__ r, float* __restrict__ res,
+               double* __restrict__ sums, int64_t npix) {
+  const int b = blockIdx.y;
+  const float* xb = x + b * npix;
+  const float* yb = y + b * npix;
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+      const int j = ci[p];
+      acc += av[p] * ((double)xb[j] + (double)yb[j]);
+    }
+    const double ri = (double)r[b * npix + i];
+    const double d = acc - ri;
+    res[b * npix + i] = (float)d;
+    s0 += d * d;
+    s1 += ri * ri;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[2 * b], s0);
+    atomicAdd(&sums[2 * b + 1], s1);
+  }
+}
+
+// g_b = (2/B) A^T res_b / ||r_b||^2, scattered along the rows of A (g zeroed beforehand)
+__global__ void __launch_bounds__(256)
+k_cnn_res_grad(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+               const double* __restrict__ av, const float* __restrict__ res,
+               const double* __restrict__ sums, float* __restrict__ g, int64_t npix, int B) {
+  const int b = blockIdx.y;
+  const double sc = 2.0 / ((double)B * sums[2 * b + 1]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = sc * (double)res[b * npix + i];
+    for (int p = rp[i]; p < rp[i + 1]; p++)
+      atomicAdd(&g[b * npix + ci[p]], (float)(av[p] * t));
+  }
+}
+
 // Adam on the FP32 master weights
 __global__ void k_cnn_adam(float* __restrict__ w, const float* __restrict__ g,
                            float* __restrict__ mo, float* __restrict__ ve, float lr, float b1,
@@ -506,6 +555,23 @@ kc_status cnn_loss_grad(kc_ctx* ctx, const float* y, const float* e, double* sum
   KC_LAUNCHED(ctx);
   timing_begin(ctx, KID_SMALL);
   k_cnn_loss_grad<<<grid, 256, 0, ctx->stream>>>(y, e, sums, g, npix, B);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status cnn_residual_loss_grad(kc_ctx* ctx, const kc_csr* A, const float* x, const float* y,
+                                 const float* r, float* res, double* sums, float* g, int B,
+                                 int64_t npix) {
+  KC_CUDA(ctx, cudaMemsetAsync(sums, 0, 2 * B * sizeof(double), ctx->stream));
+  KC_CUDA(ctx, cudaMemsetAsync(g, 0, (size_t)B * npix * sizeof(float), ctx->stream));
+  dim3 grid((unsigned)((npix + 255) / 256 < 64 ? (npix + 255) / 256 : 64), B);
+  const double* av = (const double*)A->val;
+  timing_begin(ctx, KID_SMALL);
+  k_cnn_res_sums<<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx, av, x, y, r, res, sums,
+                                                npix);
+  KC_LAUNCHED(ctx);
+  timing_begin(ctx, KID_SMALL);
+  k_cnn_res_grad<<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx, av, res, sums, g, npix, B);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }

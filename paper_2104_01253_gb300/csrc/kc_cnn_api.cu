@@ -9,6 +9,8 @@
 // the scalar step), and the solution update is x += Z y.
 #include "kc_internal.cuh"
 
+#include <vector>
+
 namespace kc {
 
 typedef __nv_bfloat16 bf16;
@@ -35,6 +37,7 @@ struct CnnBufs {
   float* g;
   float* dw;
   double* sums;
+  float* res;
 };
 
 // Carve the network workspace for B images of H x W (`train`: keep all activations).
@@ -46,12 +49,13 @@ static kc_status cnn_bufs(kc_ctx* ctx, int B, int H, int W, bool train, CnnBufs*
   size_t o_act[5];
   const int nact = train ? 5 : 2;
   for (int i = 0; i < nact; i++) { o_act[i] = off; off = al256(off + n * 32 * 2); }
-  size_t o_dz[2] = {0, 0}, o_g = 0, o_dw = 0, o_s = 0;
+  size_t o_dz[2] = {0, 0}, o_g = 0, o_dw = 0, o_s = 0, o_res = 0;
   if (train) {
     for (int i = 0; i < 2; i++) { o_dz[i] = off; off = al256(off + n * 32 * 2); }
     o_g = off; off = al256(off + n * 4);
     o_dw = off; off = al256(off + cnn_nparam() * 4);
     o_s = off; off = al256(off + 2 * (size_t)B * 8);
+    o_res = off; off = al256(off + n * 4);
   }
   kc_status s = ensure_cnn_workspace(ctx, off);
   if (s != KC_OK) return s;
@@ -64,6 +68,7 @@ static kc_status cnn_bufs(kc_ctx* ctx, int B, int H, int W, bool train, CnnBufs*
   cb->g = train ? (float*)(p + o_g) : nullptr;
   cb->dw = train ? (float*)(p + o_dw) : nullptr;
   cb->sums = train ? (double*)(p + o_s) : nullptr;
+  cb->res = train ? (float*)(p + o_res) : nullptr;
   return KC_OK;
 }
 
@@ -75,6 +80,28 @@ static kc_status check_grid(kc_ctx* ctx, int B, int H, int W) {
 
 // ---- FGMRES helpers ------------------------------------------------------------------------
 
+// dinv_i = 1 / a_ii (1 where row i stores no diagonal entry or a zero one)
+__global__ void __launch_bounds__(256)
+k_fgm_dinv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+           const double* __restrict__ av, double* __restrict__ dinv, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; p++)
+      if (ci[p] == i) d = av[p];
+    dinv[i] = d != 0.0 ? 1.0 / d : 1.0;
+  }
+}
+
+// u = D^{-1} w
+__global__ void __launch_bounds__(256)
+k_fgm_jacobi(const double* __restrict__ w, const double* __restrict__ dinv,
+             double* __restrict__ u, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = w[i] * dinv[i];
+}
+
 // network input: w / rms(w) in FP32 (rms from the norm kernel's sum of squares)
 __global__ void k_fgm_prep(const double* __restrict__ w, float* __restrict__ x, int64_t m,
                            const Scalars* __restrict__ sc) {
@@ -85,7 +112,8 @@ __global__ void k_fgm_prep(const double* __restrict__ w, float* __restrict__ x, 
     x[i] = (float)(w[i] * inv);
 }
 
-// zhat = w + rms(w) * net(w / rms(w)): the identity plus the learned correction
+// zhat = w + rms(w) * net(w / rms(w)), called with w = u = D^{-1} w: the Jacobi step plus
+// the learned correction
 __global__ void k_fgm_post(const float* __restrict__ y, const double* __restrict__ w,
                            double* __restrict__ z, int64_t m, const Scalars* __restrict__ sc) {
   const double rms = sqrt(sc->norm_sq / (double)m);
@@ -173,20 +201,35 @@ kc_status kc_cnn_forward(kc_ctx* ctx, const float* w32, const float* x, float* y
   return cnn_forward(ctx, cb.wf, x, y, cb.acts, false, B, H, W);
 }
 
-kc_status kc_cnn_train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_v, int64_t t,
-                            float lr, const float* x, const float* e, int B, int H, int W,
-                            float* y, float* grad, double* loss) {
+}  // extern "C"
+
+// One training step: forward, loss and dL/dy, backward, Adam (t > 0).  A == nullptr:
+// regression loss against the targets e; otherwise the residual loss with r = e.
+static kc_status train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_v, int64_t t,
+                            float lr, const kc_csr* A, const float* x, const float* e, int B,
+                            int H, int W, float* y, float* grad, double* loss) {
   if (!ctx) return KC_ERR_INVALID_ARG;
   if (!w32 || !x || !e || !y || (t > 0 && (!adam_m || !adam_v)))
     return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
   kc_status s = check_grid(ctx, B, H, W);
   if (s != KC_OK) return s;
+  const int64_t npix = (int64_t)H * W;
+  if (A) {
+    if ((s = validate_csr(ctx, A)) != KC_OK) return s;
+    if (A->val_dtype != KC_F64) return fail(ctx, KC_ERR_INVALID_ARG, "A must have FP64 values");
+    if (A->m != npix)
+      return fail(ctx, KC_ERR_INVALID_ARG, "grid %d x %d does not match m = %lld", H, W,
+                  (long long)A->m);
+  }
   CnnBufs cb;
   if ((s = cnn_bufs(ctx, B, H, W, true, &cb)) != KC_OK) return s;
   if ((s = cnn_prep(ctx, w32, cb.wf, cb.wt)) != KC_OK) return s;
   if ((s = cnn_forward(ctx, cb.wf, x, y, cb.acts, true, B, H, W)) != KC_OK) return s;
-  const int64_t npix = (int64_t)H * W;
-  if ((s = cnn_loss_grad(ctx, y, e, cb.sums, cb.g, B, npix)) != KC_OK) return s;
+  if (A)
+    s = cnn_residual_loss_grad(ctx, A, x, y, e, cb.res, cb.sums, cb.g, B, npix);
+  else
+    s = cnn_loss_grad(ctx, y, e, cb.sums, cb.g, B, npix);
+  if (s != KC_OK) return s;
   KC_CUDA(ctx, cudaMemsetAsync(cb.dw, 0, cnn_nparam() * sizeof(float), ctx->stream));
   if ((s = cnn_backward(ctx, cb.wf, cb.wt, x, cb.g, cb.acts, cb.dz, cb.dw, B, H, W)) != KC_OK)
     return s;
@@ -196,16 +239,31 @@ kc_status kc_cnn_train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_
   if (t > 0 && (s = cnn_adam(ctx, w32, cb.dw, adam_m, adam_v, t, lr, 0.9f, 0.999f, 1e-8f)) != KC_OK)
     return s;
   if (loss) {
-    double hs[2 * 64];
-    const int nb = B < 64 ? B : 64;
-    KC_CUDA(ctx, cudaMemcpyAsync(hs, cb.sums, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost,
-                                 ctx->stream));
+    std::vector<double> hs(2 * (size_t)B);
+    KC_CUDA(ctx, cudaMemcpyAsync(hs.data(), cb.sums, 2 * (size_t)B * sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
     KC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     double L = 0.0;
-    for (int b = 0; b < nb; b++) L += hs[2 * b] / hs[2 * b + 1];
-    *loss = L / nb;
+    for (int b = 0; b < B; b++) L += hs[2 * b] / hs[2 * b + 1];
+    *loss = L / B;
   }
   return KC_OK;
+}
+
+extern "C" {
+
+kc_status kc_cnn_train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_v, int64_t t,
+                            float lr, const float* x, const float* e, int B, int H, int W,
+                            float* y, float* grad, double* loss) {
+  return train_step(ctx, w32, adam_m, adam_v, t, lr, nullptr, x, e, B, H, W, y, grad, loss);
+}
+
+kc_status kc_cnn_train_step_residual(kc_ctx* ctx, float* w32, float* adam_m, float* adam_v,
+                                     int64_t t, float lr, const kc_csr* A, const float* x,
+                                     const float* r, int B, int H, int W, float* y, float* grad,
+                                     double* loss) {
+  if (ctx && !A) return fail(ctx, KC_ERR_INVALID_ARG, "NULL operator");
+  return train_step(ctx, w32, adam_m, adam_v, t, lr, A, x, r, B, H, W, y, grad, loss);
 }
 
 kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, int W,
@@ -216,7 +274,11 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
   if (s != KC_OK) return s;
   if (!b || !x || !opts || !info) return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
   if (A->val_dtype != KC_F64) return fail(ctx, KC_ERR_INVALID_ARG, "A must have FP64 values");
-  if (w32 && (int64_t)H * W != A->m)
+  if (opts->precond != KC_PREC_AUTO && opts->precond != KC_PREC_JACOBI)
+    return fail(ctx, KC_ERR_INVALID_ARG, "unknown preconditioner kind %d", opts->precond);
+  const bool use_net = w32 && opts->precond == KC_PREC_AUTO;
+  const bool use_jacobi = use_net || opts->precond == KC_PREC_JACOBI;
+  if (use_net && (int64_t)H * W != A->m)
     return fail(ctx, KC_ERR_INVALID_ARG, "grid %d x %d does not match m = %lld", H, W,
                 (long long)A->m);
   const int n = opts->restart;
@@ -236,6 +298,8 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
   const size_t oR = off; off = al256(off + (size_t)n * n * 8);
   const size_t oi = off; off = al256(off + (size_t)ld * 4);
   const size_t oo = off; off = al256(off + (size_t)ld * 4);
+  const size_t od = off; off = al256(off + (size_t)ld * 8);
+  const size_t ou = off; off = al256(off + (size_t)ld * 8);
   if ((s = ensure_workspace(ctx, off)) != KC_OK) return s;
   char* ws = (char*)ctx->ws;
   double* Q = (double*)(ws + oQ);
@@ -247,8 +311,10 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
   double* R = (double*)(ws + oR);
   float* xin = (float*)(ws + oi);
   float* yout = (float*)(ws + oo);
+  double* dinv = (double*)(ws + od);
+  double* u = (double*)(ws + ou);
   CnnBufs cb = {};
-  if (w32) {
+  if (use_net) {
     if ((s = cnn_bufs(ctx, 1, H, W, false, &cb)) != KC_OK) return s;
     if ((s = cnn_prep(ctx, w32, cb.wf, cb.wt)) != KC_OK) return s;
   }
@@ -271,6 +337,11 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
   sa.flags = SF_GIVENS | SF_FLEXIBLE;
   sa.pyth_tol = 0.0;
   const int g = g1d(ctx, m);
+  if (use_jacobi) {
+    timing_begin(ctx, KID_OTHER);
+    k_fgm_dinv<<<g, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx, (const double*)A->val, dinv, m);
+    KC_LAUNCHED(ctx);
+  }
   int matvecs = 0, cycles = 0, last_status = KC_OK;
   double rn = 0.0, est = 0.0;
   kc_status result = KC_ERR_NOT_CONVERGED;
@@ -288,15 +359,22 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
     for (int k = 0; k < n; k++) {
       double* zk = Z + (size_t)k * ld;
       sa.k = k;
-      if (w32) {       // zhat = w + rms(w) net(w / rms(w))
-        StepArgs sn = {};
-        if ((s = launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_INIT, sn)) != KC_OK) return s;
+      if (use_net) {   // zhat = u + rms(u) net(u / rms(u)), u = D^{-1} w
         timing_begin(ctx, KID_OTHER);
-        k_fgm_prep<<<g, 256, 0, ctx->stream>>>(w, xin, m, ctx->scal);
+        k_fgm_jacobi<<<g, 256, 0, ctx->stream>>>(w, dinv, u, m);
+        KC_LAUNCHED(ctx);
+        StepArgs sn = {};
+        if ((s = launch_norm(ctx, u, nullptr, m, KC_F64, NEPI_INIT, sn)) != KC_OK) return s;
+        timing_begin(ctx, KID_OTHER);
+        k_fgm_prep<<<g, 256, 0, ctx->stream>>>(u, xin, m, ctx->scal);
         KC_LAUNCHED(ctx);
         if ((s = cnn_forward(ctx, cb.wf, xin, yout, cb.acts, false, 1, H, W)) != KC_OK) return s;
         timing_begin(ctx, KID_OTHER);
-        k_fgm_post<<<g, 256, 0, ctx->stream>>>(yout, w, zk, m, ctx->scal);
+        k_fgm_post<<<g, 256, 0, ctx->stream>>>(yout, u, zk, m, ctx->scal);
+        KC_LAUNCHED(ctx);
+      } else if (use_jacobi) {   // zhat = D^{-1} w
+        timing_begin(ctx, KID_OTHER);
+        k_fgm_jacobi<<<g, 256, 0, ctx->stream>>>(w, dinv, zk, m);
         KC_LAUNCHED(ctx);
       } else {         // identity: zhat = w
         KC_CUDA(ctx, cudaMemcpyAsync(zk, w, m * 8, cudaMemcpyDeviceToDevice, ctx->stream));

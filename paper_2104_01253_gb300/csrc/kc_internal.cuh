@@ -168,6 +168,9 @@ kc_status cnn_backward(kc_ctx* ctx, const __nv_bfloat16* wf, const __nv_bfloat16
                        __nv_bfloat16* const* dz, float* dw, int B, int H, int W);
 kc_status cnn_loss_grad(kc_ctx* ctx, const float* y, const float* e, double* sums, float* g,
                         int B, int64_t npix);
+kc_status cnn_residual_loss_grad(kc_ctx* ctx, const kc_csr* A, const float* x, const float* y,
+                                 const float* r, float* res, double* sums, float* g, int B,
+                                 int64_t npix);
 kc_status cnn_adam(kc_ctx* ctx, float* w, const float* g, float* m, float* v, int64_t t,
                    float lr, float b1, float b2, float eps);
 int64_t cnn_nparam();

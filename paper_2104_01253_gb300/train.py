@@ -1,26 +1,39 @@
 """Training the convolutional preconditioner on the GPU (orchestration of C-ABI calls).
 
 Data: for each seeded operator of the variable-coefficient family (synth.varcoef_fields_2d),
-plain DCGS2-GMRES(n) solves A x = b to 1e-10 (gmres_solve); a second run from x0 = 0,
-one restart cycle per call, records every iterate x_j; each pair is the residual
-r_j = b - A x_j and the correction e_j = x* - x_j (so A e_j = r_j), both divided by
-rms(r_j).  The preconditioner is M(r) = r + net(r) (fgmres_solve), so the network is
-trained on the target d = e - r: (1/B) sum ||net(r) - d||^2 / ||d||^2 with Adam; every
-forward, backward and update runs in libkrylov (kc_cnn_train_step).
+plain DCGS2-GMRES(n) (gmres_solve), one restart cycle per call, records the residual
+r_j = b - A x_j at every restart.  Each r_j is a (residual, correction) pair with the
+correction e_j = A^{-1} r_j left implicit: the residual loss
+
+    L = (1/B) sum_b ||A (x_b + net(x_b)) - r_b||^2 / ||r_b||^2,   x_b = D^{-1} r_b,
+
+is ||A (M(r_b) - e_b)||^2 / ||r_b||^2 for the preconditioner M that fgmres_solve applies
+(M(w) = D^{-1} w + s net(D^{-1} w / s)), so it needs r_b and A only.  Inputs and residuals
+of a sample are divided by s = rms(D^{-1} r_b) (the network is positively homogeneous).
+Every forward, backward and Adam update runs in libkrylov (kc_cnn_train_step_residual);
+each step draws its batch from one operator, cycling through the training operators.
 """
 from __future__ import annotations
 
 import numpy as np
 import torch
 
-from . import (Context, DeviceCSR, gmres_solve, kc_cnn_param_count, kc_cnn_train_step,
-               kc_spmv)
+from . import (Context, DeviceCSR, gmres_solve, kc_cnn_param_count,
+               kc_cnn_train_step_residual, kc_spmv)
 
 
 def varcoef_operator(N: int, seed: int):
     from synth import convdiff_csr, varcoef_fields_2d
     kappa, wind = varcoef_fields_2d(N, seed)
     return convdiff_csr(N, 2, wind, kappa=kappa)
+
+
+def inverse_diagonal(Ah) -> np.ndarray:
+    """1 / a_ii of a host CSR (1 where the diagonal entry is missing or zero)."""
+    d = np.asarray(Ah.to_scipy().diagonal(), dtype=np.float64)
+    out = np.ones(Ah.m)
+    out[d != 0.0] = 1.0 / d[d != 0.0]
+    return out
 
 
 def he_init(seed: int) -> np.ndarray:
@@ -35,50 +48,60 @@ def he_init(seed: int) -> np.ndarray:
     return w
 
 
-def generate_pairs(ctx: Context, N: int, seeds, restart: int = 40, max_cycles: int = 40,
+def generate_pairs(ctx: Context, N: int, seeds, restart: int = 40, max_cycles: int = 20,
                    rhs_seed_offset: int = 1000):
-    """(residual, correction - residual) pairs from plain GMRES solves, scaled by
-    rms(residual): the training inputs and targets of the network."""
-    rs, es = [], []
-    for seed in seeds:
+    """Restart residuals of plain GMRES solves on the seeded operators.
+
+    Returns (ops, X, R, owner): the device operators, the network inputs
+    X = D^{-1} r / s and residuals R = r / s (float32, (n, 1, N, N), host), and the index
+    of each sample's operator."""
+    from synth import gaussian_vector
+    ops, X, R, owner = [], [], [], []
+    for oi, seed in enumerate(seeds):
         Ah = varcoef_operator(N, seed)
         A = DeviceCSR(Ah)
-        from synth import gaussian_vector
+        ops.append(A)
+        dinv = torch.as_tensor(inverse_diagonal(Ah), device="cuda")
         b = torch.as_tensor(gaussian_vector(Ah.m, rhs_seed_offset + seed), device="cuda")
-        xs = torch.zeros_like(b)
-        gmres_solve(ctx, A, b, xs, restart=restart, rtol=1e-10)
         x = torch.zeros_like(b)
         Ax = torch.empty_like(b)
         for _ in range(max_cycles):
-            info = gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10, maxit=restart)
             kc_spmv(ctx, A, x, Ax)
             r = b - Ax
-            e = xs - x
-            s = torch.sqrt(torch.mean(r * r))
-            if not float(s) > 0 or info["rel_resid_true"] <= 1e-9:
+            if float(torch.linalg.vector_norm(r)) <= 1e-9 * float(torch.linalg.vector_norm(b)):
                 break
-            rs.append((r / s).float().cpu().numpy())
-            es.append(((e - r) / s).float().cpu().numpy())
-    r = np.stack(rs).reshape(-1, 1, N, N)
-    e = np.stack(es).reshape(-1, 1, N, N)
-    return r, e
+            u = r * dinv
+            s = torch.sqrt(torch.mean(u * u))
+            X.append((u / s).float().cpu().numpy())
+            R.append((r / s).float().cpu().numpy())
+            owner.append(oi)
+            gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10, maxit=restart)
+    X = np.stack(X).reshape(-1, 1, N, N)
+    R = np.stack(R).reshape(-1, 1, N, N)
+    return ops, X, R, np.asarray(owner)
 
 
-def train(ctx: Context, r: np.ndarray, e: np.ndarray, steps: int = 400, batch: int = 16,
-          lr: float = 1e-3, seed: int = 0, w0=None):
-    """Adam on the GPU; returns the FP32 weights (device tensor) and the loss history."""
-    n, _, H, W = r.shape
+def train(ctx: Context, ops, X: np.ndarray, R: np.ndarray, owner: np.ndarray,
+          steps: int = 600, batch: int = 16, lr: float = 2e-3, seed: int = 0, w0=None):
+    """Adam on the residual loss; returns the FP32 weights (device tensor) and the loss
+    history.  Step t uses operator t mod len(ops) and a batch of its samples."""
+    n, _, H, W = X.shape
     w = torch.as_tensor(he_init(seed) if w0 is None else w0, device="cuda").contiguous()
     m = torch.zeros_like(w)
     v = torch.zeros_like(w)
-    rd = torch.as_tensor(r, device="cuda")
-    ed = torch.as_tensor(e, device="cuda")
+    xd = torch.as_tensor(X, device="cuda")
+    rd = torch.as_tensor(R, device="cuda")
     y = torch.empty((batch, 1, H, W), dtype=torch.float32, device="cuda")
+    pools = [np.nonzero(owner == o)[0] for o in range(len(ops))]
     rng = np.random.default_rng(seed + 1)
     hist = []
     for t in range(1, steps + 1):
-        idx = torch.as_tensor(rng.choice(n, size=batch, replace=n < batch), device="cuda")
-        xb = rd[idx].contiguous()
-        eb = ed[idx].contiguous()
-        hist.append(kc_cnn_train_step(ctx, w, m, v, t, lr, xb, eb, batch, H, W, y))
+        o = (t - 1) % len(ops)
+        if pools[o].size == 0:
+            continue
+        idx = torch.as_tensor(rng.choice(pools[o], size=batch), device="cuda")
+        xb = xd[idx].contiguous()
+        rb = rd[idx].contiguous()
+        hist.append(kc_cnn_train_step_residual(ctx, w, m, v, t, lr, ops[o], xb, rb, batch,
+                                               H, W, y))
     return w, hist

@@ -100,6 +100,54 @@ def test_adam_steps_reduce_the_loss(kc, ctx):
     assert last < 0.3 * first
 
 
+def test_residual_loss_gradients_match_oracle(kc, ctx):
+    """kc_cnn_train_step_residual against the oracle's residual loss with the GPU's BF16
+    storage rounding, on a variable-coefficient convection-diffusion operator."""
+    N, B = 24, 3
+    Ah = _varcoef(N, 40)
+    A = kc.DeviceCSR(Ah)
+    ws = cnn.init_weights(41)
+    w32 = pack(ws)
+    rng = np.random.default_rng(42)
+    x = rng.standard_normal((B, 1, N, N)).astype(np.float32)
+    r = rng.standard_normal((B, 1, N, N)).astype(np.float32)
+    wd = torch.as_tensor(w32, device="cuda")
+    grad = torch.zeros_like(wd)
+    yd = torch.zeros((B, 1, N, N), dtype=torch.float32, device="cuda")
+    loss = kc.kc_cnn_train_step_residual(ctx, wd, None, None, 0, 0.0, A,
+                                         torch.as_tensor(x, device="cuda"),
+                                         torch.as_tensor(r, device="cuda"), B, N, N, yd, grad)
+    Lo, go, _, yo = cnn.residual_loss_and_grads(unpack(w32, ws), x.astype(np.float64),
+                                                r.astype(np.float64), Ah.to_scipy(), bf16=True)
+    assert abs(loss - Lo) <= 2e-3 * Lo
+    assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) <= 5e-3
+    g = unpack(grad.cpu().numpy(), ws)
+    for li in range(6):
+        rel = np.linalg.norm(g[li] - go[li]) / np.linalg.norm(go[li])
+        assert rel <= 2e-2, (li, rel)
+
+
+def test_residual_training_reduces_the_loss(kc, ctx):
+    """Adam on the residual loss with A = 2 I and r = x: the network can reach zero loss
+    (net(x) = -x / 2), so 200 steps must cut the loss well down."""
+    import scipy.sparse as sp
+    from synth.operators import CSR
+    N, B = 16, 4
+    S = (2.0 * sp.identity(N * N, format="csr")).tocsr()
+    A = kc.DeviceCSR(CSR(N * N, S.indptr.astype(np.int32), S.indices.astype(np.int32),
+                         S.data.astype(np.float64)))
+    wd = torch.as_tensor(pack(cnn.init_weights(43)), device="cuda")
+    m = torch.zeros_like(wd)
+    v = torch.zeros_like(wd)
+    x = torch.as_tensor(np.random.default_rng(44).standard_normal((B, 1, N, N))
+                        .astype(np.float32), device="cuda")
+    yd = torch.zeros_like(x)
+    first = kc.kc_cnn_train_step_residual(ctx, wd, m, v, 1, 1e-3, A, x, x, B, N, N, yd)
+    for t in range(2, 200):
+        last = kc.kc_cnn_train_step_residual(ctx, wd, m, v, t, 1e-3, A, x, x, B, N, N, yd)
+    assert last < 0.3 * first
+
+
 def _varcoef(N, seed):
     kappa, wind = varcoef_fields_2d(N, seed)
     return convdiff_csr(N, 2, wind, kappa=kappa)
@@ -137,14 +185,30 @@ def near_identity_weights(seed, eps=0.02):
     return ws
 
 
+def test_fgmres_jacobi_matches_oracle(kc, ctx):
+    Ah = _varcoef(32, 66)
+    b = gaussian_vector(Ah.m, 73)
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(b, device="cuda")
+    x = torch.zeros_like(bd)
+    info = kc.fgmres_solve(ctx, A, None, 32, 32, bd, x, restart=40, rtol=1e-10,
+                           precond=kc.PREC_JACOBI)
+    assert info["status"] == 0 and info["rel_resid_true"] <= 1e-10
+    dinv = cnn.inverse_diagonal(Ah.to_scipy())
+    xo, io = orc_gmres(Ah.to_scipy(), b, restart=40, rtol=1e-10, precond=lambda w: w * dinv)
+    assert abs(io["iters"] - info["iters"]) <= 1
+    assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
+
+
 def test_fgmres_with_network_converges(kc, ctx):
-    """A perturbed identity network is a nonlinear preconditioner: flexible GMRES must
-    reach 1e-10 with an iteration count close to the oracle's FGMRES on the same
-    BF16-storage network (a random untrained network makes both stagnate)."""
+    """A perturbed linear network (net(x) ~ -x / 2) in the Jacobi-scaled preconditioner is
+    nonlinear: flexible GMRES must reach 1e-10 with an iteration count close to the
+    oracle's FGMRES on the same BF16-storage network."""
     N = 32
     Ah = _varcoef(N, 65)
     b = gaussian_vector(Ah.m, 72)
     ws = near_identity_weights(9)
+    ws[5] *= -0.5
     w32 = pack(ws)
     A = kc.DeviceCSR(Ah)
     bd = torch.as_tensor(b, device="cuda")
@@ -153,39 +217,38 @@ def test_fgmres_with_network_converges(kc, ctx):
                            restart=40, rtol=1e-10)
     assert info["status"] == 0 and info["rel_resid_true"] <= 1e-10
     wo = unpack(w32, ws)
-
-    def M(w):                       # the identity plus the network's correction
-        s = np.sqrt(np.mean(w * w))
-        y, _ = cnn.forward_bf16_storage(wo, (w / s).reshape(1, 1, N, N))
-        return w + y.reshape(-1) * s
-
+    dinv = cnn.inverse_diagonal(Ah.to_scipy())
+    M = lambda w: cnn.jacobi_network_preconditioner(wo, w, dinv, N, N, bf16=True)
     _, io = orc_gmres(Ah.to_scipy(), b, restart=40, rtol=1e-10, precond=M)
     assert io["rel_resid_true"] <= 1e-10
     assert abs(info["iters"] - io["iters"]) <= max(3, 0.1 * io["iters"])
 
 
 def test_trained_network_reduces_fgmres_iterations(kc, ctx):
-    """Train on (residual, correction) pairs from plain GMRES solves on seeded operators
-    0..11 (32 x 32 grids), then solve held-out operators 64..66: the learned
-    preconditioner must cut the matvec count of plain GMRES(40).  (The size of the gain is
-    an empirical result with no closed form.)"""
+    """Train on the restart residuals of plain GMRES solves on seeded operators 0..11
+    (32 x 32 grids) with the residual loss, then solve held-out operators 64..66: the
+    learned preconditioner must cut the iteration count of plain GMRES(40) and of the
+    Jacobi step alone (the part of M without the network).  The size of the gain is an
+    empirical result with no closed form; it is printed."""
     from paper_2104_01253_gb300 import train as tr
     N = 32
-    r, e = tr.generate_pairs(ctx, N, range(12), restart=40, max_cycles=30)
-    assert r.shape[0] >= 100
-    w, hist = tr.train(ctx, r, e, steps=600, batch=16, lr=2e-3, seed=0)
+    ops, X, R, owner = tr.generate_pairs(ctx, N, range(12), restart=40, max_cycles=20)
+    assert X.shape[0] >= 100
+    w, hist = tr.train(ctx, ops, X, R, owner, steps=600, batch=16, lr=2e-3, seed=0)
     assert np.mean(hist[-50:]) < 0.8 * np.mean(hist[:20])
-    gains = []
+    rows = []
     for seed in (64, 65, 66):
         Ah = tr.varcoef_operator(N, seed)
         A = kc.DeviceCSR(Ah)
         b = torch.as_tensor(gaussian_vector(Ah.m, 2000 + seed), device="cuda")
-        x1 = torch.zeros_like(b)
-        x2 = torch.zeros_like(b)
+        x1, x2, x3 = (torch.zeros_like(b) for _ in range(3))
         plain = kc.gmres_solve(ctx, A, b, x1, restart=40, rtol=1e-10)
+        jac = kc.fgmres_solve(ctx, A, None, N, N, b, x3, restart=40, rtol=1e-10,
+                              precond=kc.PREC_JACOBI)
         flex = kc.fgmres_solve(ctx, A, w, N, N, b, x2, restart=40, rtol=1e-10)
-        assert plain["status"] == 0 and flex["status"] == 0
+        assert plain["status"] == 0 and jac["status"] == 0 and flex["status"] == 0
         assert flex["rel_resid_true"] <= 1e-10
-        gains.append(plain["iters"] / flex["iters"])
-    print("held-out iteration ratios plain/learned:", gains)
-    assert min(gains) > 1.0
+        rows.append((plain["iters"], jac["iters"], flex["iters"]))
+    print("held-out iterations (plain, Jacobi, learned):", rows)
+    assert all(f < p for p, _, f in rows)
+    assert all(f < j for _, j, f in rows)
