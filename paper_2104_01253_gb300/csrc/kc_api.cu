@@ -118,7 +118,8 @@ kc_status kc_create(kc_ctx** out, int device, void* cuda_stream) {
   ctx->num_sms = p.multiProcessorCount;
   ctx->fp64_mode = 1;
   ctx->reduce_grid = 2 * p.multiProcessorCount;
-  const size_t plen = (size_t)ctx->reduce_grid * (2 * NMAX + 4) * sizeof(double);
+  const size_t plen =
+      (size_t)PARTIAL_CTAS_PER_SM * p.multiProcessorCount * (2 * NMAX + 4) * sizeof(double);
   bool ok = cudaMalloc(&ctx->partials, plen) == cudaSuccess &&
             cudaMalloc(&ctx->counters, 16 * sizeof(unsigned int)) == cudaSuccess &&
             cudaMalloc(&ctx->scal, sizeof(Scalars)) == cudaSuccess &&

@@ -16,6 +16,7 @@ namespace kc {
 constexpr int NMAX = 128;            // largest basis (ncap) any kernel supports
 constexpr int RED_THREADS = 512;     // threads of a reduction CTA (16 warps)
 constexpr int RED_WARPS = RED_THREADS / 32;
+constexpr int PARTIAL_CTAS_PER_SM = 8;   // reduction CTAs per SM the partials buffer holds
 constexpr int UPD_THREADS = 256;
 
 // Device-resident scalars of the current step, written by the last CTA of a reduction
@@ -87,7 +88,8 @@ struct kc_ctx {
   cudaStream_t stream;
   int num_sms;
   int reduce_grid;
-  double* partials;        // reduce_grid * (2*NMAX + 4) doubles
+  int red_occ[4][33];      // resident CTAs per SM of the offload reduction, by (TPW, warps)
+  double* partials;        // PARTIAL_CTAS_PER_SM * num_sms * (2*NMAX + 4) doubles
   unsigned int* counters;  // ticket counters for last-CTA reductions
   kc::Scalars* scal;       // device scalars
   kc::Scalars* scal_host;  // pinned host mirror for reads

@@ -498,132 +498,147 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // the FP64 path.
 // ----------------------------------------------------------------------------------------
 
-// One group of two rows of the offloaded reduction: C in FP64; S in float-float (OFF) or
-// in FP64 (!OFF, the path for operands outside the float-float range).
+// Offloaded reduction, task layout.  ntask = k + 2 tasks of equal FP64 cost (two FP64
+// FMAs per group of two rows): task t < k is column t (C_t = q_t^T w in FP64 and
+// S_t = q_t^T v in float-float), task k is beta = w^T w and task k + 1 is s = w^T v, both
+// in FP64.  A CTA has nw = ceil(ntask / TPW) warps and warp w takes tasks w, w + nw, ...
+// (TPW slots), so at most TPW - 1 slots of a CTA are idle; all warps of a CTA walk the
+// same rows, and w and v come from L1 after the first warp has loaded them.
+
+// the operand that task t multiplies into w: q_t, w itself (beta) or v (s); null if idle
+__device__ __forceinline__ const double* f64x_operand(const double* Q, int64_t ldq, int k,
+                                                      const double* x, const double* y,
+                                                      int t) {
+  return t < k ? Q + (int64_t)t * ldq : (t == k ? x : (t == k + 1 ? y : nullptr));
+}
+
+// One group of two rows for every slot: ac += a . w (FP64); for columns S += a . v in
+// float-float (OFF) or FP64 (!OFF, operands outside the float-float range).
 template <int TPW, bool OFF>
-__device__ __forceinline__ void f64x_group(int warp, int k, const double (&xv)[2],
-                                           const double (&yv)[2], const double (&qv)[TPW][2],
-                                           double* ac, double* as64, float* sh, float* sl) {
+__device__ __forceinline__ void f64x_group(const int (&tk)[TPW], int k,
+                                           const double (&xv)[2], const double (&yv)[2],
+                                           const double (&av)[TPW][2], double* ac,
+                                           double* as64, float* sh, float* sl) {
   float yh[2], yl[2];
   if (OFF) { split_df(yv[0], yh[0], yl[0]); split_df(yv[1], yh[1], yl[1]); }
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
-    const int t = warp + RED_WARPS * i;
-    if (t < k) {
-      ac[i] = fma(qv[i][0], xv[0], ac[i]);
-      ac[i] = fma(qv[i][1], xv[1], ac[i]);
+    if (tk[i] > k + 1) continue;                 // idle slot (warp-uniform)
+    ac[i] = fma(av[i][0], xv[0], ac[i]);
+    ac[i] = fma(av[i][1], xv[1], ac[i]);
+    if (tk[i] < k) {
       if (OFF) {
-        float qh[2], ql[2];
-        split_df(qv[i][0], qh[0], ql[0]);
-        split_df(qv[i][1], qh[1], ql[1]);
-        df_mac(sh[i], sl[i], qh[0], ql[0], yh[0], yl[0]);
-        df_mac(sh[i], sl[i], qh[1], ql[1], yh[1], yl[1]);
+        float ah[2], al[2];
+        split_df(av[i][0], ah[0], al[0]);
+        split_df(av[i][1], ah[1], al[1]);
+        df_mac(sh[i], sl[i], ah[0], al[0], yh[0], yl[0]);
+        df_mac(sh[i], sl[i], ah[1], al[1], yh[1], yl[1]);
       } else {
-        as64[i] = fma(qv[i][0], yv[0], as64[i]);
-        as64[i] = fma(qv[i][1], yv[1], as64[i]);
+        as64[i] = fma(av[i][0], yv[0], as64[i]);
+        as64[i] = fma(av[i][1], yv[1], as64[i]);
       }
-    } else if (t == k) {     // beta = w^T w and s = w^T v in FP64
-      ac[i] = fma(xv[0], xv[0], ac[i]);
-      ac[i] = fma(xv[1], xv[1], ac[i]);
-      as64[i] = fma(xv[0], yv[0], as64[i]);
-      as64[i] = fma(xv[1], yv[1], as64[i]);
     }
   }
 }
 
-// true when every operand of a group lies in the float-float range
+// true when every operand that the float-float path splits lies in its range
 template <int TPW>
-__device__ __forceinline__ bool f64x_in_range(int warp, int k, const double (&yv)[2],
-                                              const double (&qv)[TPW][2]) {
+__device__ __forceinline__ bool f64x_in_range(const int (&tk)[TPW], int k,
+                                              const double (&yv)[2],
+                                              const double (&av)[TPW][2]) {
   bool ok = df_in_range(yv[0]) & df_in_range(yv[1]);
 #pragma unroll
   for (int i = 0; i < TPW; i++)
-    if (warp + RED_WARPS * i < k) ok = ok & df_in_range(qv[i][0]) & df_in_range(qv[i][1]);
+    if (tk[i] < k) ok = ok & df_in_range(av[i][0]) & df_in_range(av[i][1]);
   return ok;
 }
 
-// Fused DCGS2 reduction, FP64 with offload (EPI_DCGS2 only: NRHS = 2).  The choice
-// between the float-float and the FP64 evaluation of S is made once per loop iteration,
+template <int TPW>
+__device__ __forceinline__ void f64x_load(const double* const (&ap)[TPW], int64_t g,
+                                          double (&av)[TPW][2]) {
+#pragma unroll
+  for (int i = 0; i < TPW; i++)
+    if (ap[i]) load_q(ap[i], g, av[i]);
+}
+
+// Fused DCGS2 reduction, FP64 with offload (EPI_DCGS2 only).  The choice between the
+// float-float and the FP64 evaluation of S is made once per loop iteration,
 // warp-uniformly, around the whole iteration: a small per-column branch is turned into
 // predicated code by the compiler, and an FP64 FMA issued with every lane predicated off
-// still holds the FP64 pipe for its full issue time.
-template <int TPW>
-__global__ void __launch_bounds__(RED_THREADS)
+// still holds the FP64 pipe for its full issue time.  GR row groups per iteration (all
+// loads issued before any arithmetic).
+template <int TPW, int GR>
+__global__ void __launch_bounds__(1024)
 k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
               const double* __restrict__ y, int64_t m, double* __restrict__ partials,
               unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa) {
   if (sc->stop) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ntask = k + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int tk[TPW];
+  const double* ap[TPW];
   double ac[TPW], as64[TPW];
   float sh[TPW], sl[TPW];
 #pragma unroll
-  for (int i = 0; i < TPW; i++) { ac[i] = 0.0; as64[i] = 0.0; sh[i] = 0.0f; sl[i] = 0.0f; }
+  for (int i = 0; i < TPW; i++) {
+    tk[i] = warp + nw * i;
+    ap[i] = f64x_operand(Q, ldq, k, x, y, tk[i]);
+    ac[i] = 0.0; as64[i] = 0.0; sh[i] = 0.0f; sl[i] = 0.0f;
+  }
   const int64_t ngroups = m / 2;
   const int64_t g0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
   const int64_t g1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
-  // two row groups per iteration, every load issued before any arithmetic
   int64_t g = g0 + lane;
-  for (; g + 32 < g1; g += 64) {
-    double xa[2], ya[2], xb[2], yb[2];
-    ldv(x, g, xa);
-    ldv(y, g, ya);
-    ldv(x, g + 32, xb);
-    ldv(y, g + 32, yb);
-    double qa[TPW][2], qb[TPW][2];
-#pragma unroll
-    for (int i = 0; i < TPW; i++) {
-      const int t = warp + RED_WARPS * i;
-      if (t < k) {
-        load_q(Q + (int64_t)t * ldq, g, qa[i]);
-        load_q(Q + (int64_t)t * ldq, g + 32, qb[i]);
+  if (GR == 2) {
+    for (; g + 32 < g1; g += 64) {
+      double xa[2], ya[2], xb[2], yb[2], qa[TPW][2], qb[TPW][2];
+      ldv(x, g, xa);
+      ldv(y, g, ya);
+      ldv(x, g + 32, xb);
+      ldv(y, g + 32, yb);
+      f64x_load<TPW>(ap, g, qa);
+      f64x_load<TPW>(ap, g + 32, qb);
+      const bool ok = f64x_in_range<TPW>(tk, k, ya, qa) & f64x_in_range<TPW>(tk, k, yb, qb);
+      if (__builtin_expect(__all_sync(__activemask(), ok), 1)) {
+        f64x_group<TPW, true>(tk, k, xa, ya, qa, ac, as64, sh, sl);
+        f64x_group<TPW, true>(tk, k, xb, yb, qb, ac, as64, sh, sl);
+      } else {
+        f64x_group<TPW, false>(tk, k, xa, ya, qa, ac, as64, sh, sl);
+        f64x_group<TPW, false>(tk, k, xb, yb, qb, ac, as64, sh, sl);
       }
     }
-    const bool ok = f64x_in_range<TPW>(warp, k, ya, qa) & f64x_in_range<TPW>(warp, k, yb, qb);
-    if (__builtin_expect(__all_sync(__activemask(), ok), 1)) {
-      f64x_group<TPW, true>(warp, k, xa, ya, qa, ac, as64, sh, sl);
-      f64x_group<TPW, true>(warp, k, xb, yb, qb, ac, as64, sh, sl);
-    } else {
-      f64x_group<TPW, false>(warp, k, xa, ya, qa, ac, as64, sh, sl);
-      f64x_group<TPW, false>(warp, k, xb, yb, qb, ac, as64, sh, sl);
-    }
   }
-  if (g < g1) {
+  for (; g < g1; g += 32) {
     double xa[2], ya[2], qa[TPW][2];
     ldv(x, g, xa);
     ldv(y, g, ya);
-#pragma unroll
-    for (int i = 0; i < TPW; i++) {
-      const int t = warp + RED_WARPS * i;
-      if (t < k) load_q(Q + (int64_t)t * ldq, g, qa[i]);
-    }
-    if (__all_sync(__activemask(), f64x_in_range<TPW>(warp, k, ya, qa)))
-      f64x_group<TPW, true>(warp, k, xa, ya, qa, ac, as64, sh, sl);
+    f64x_load<TPW>(ap, g, qa);
+    if (__builtin_expect(__all_sync(__activemask(), f64x_in_range<TPW>(tk, k, ya, qa)), 1))
+      f64x_group<TPW, true>(tk, k, xa, ya, qa, ac, as64, sh, sl);
     else
-      f64x_group<TPW, false>(warp, k, xa, ya, qa, ac, as64, sh, sl);
+      f64x_group<TPW, false>(tk, k, xa, ya, qa, ac, as64, sh, sl);
   }
   if (blockIdx.x == gridDim.x - 1) {           // ragged tail (m odd): FP64
     for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
       const double xs = __ldcg(x + row), ys1 = __ldcg(y + row);
 #pragma unroll
       for (int i = 0; i < TPW; i++) {
-        const int t = warp + RED_WARPS * i;
-        if (t < ntask) {
-          const double q = t < k ? __ldcg(Q + (int64_t)t * ldq + row) : xs;
-          ac[i] = fma(q, xs, ac[i]);
-          as64[i] = fma(q, ys1, as64[i]);
-        }
+        if (!ap[i]) continue;
+        const double a = __ldcg(ap[i] + row);
+        ac[i] = fma(a, xs, ac[i]);
+        as64[i] = fma(a, ys1, as64[i]);
       }
     }
   }
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
-    const int t = warp + RED_WARPS * i;
+    const int t = tk[i];
+    if (t > k + 1) continue;
     const double c = warp_sum(ac[i]);
     const double sv = warp_sum(as64[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])));
-    if (lane == 0 && t < ntask) {
-      partials[(int64_t)blockIdx.x * PSTRIDE + 2 * t] = c;
-      partials[(int64_t)blockIdx.x * PSTRIDE + 2 * t + 1] = sv;
+    if (lane == 0) {
+      double* pp = partials + (int64_t)blockIdx.x * PSTRIDE;
+      if (t < k) { pp[2 * t] = c; pp[2 * t + 1] = sv; }
+      else pp[2 * k + (t - k)] = c;           // beta -> [2k], s -> [2k + 1]
     }
   }
   if (!last_cta(counter)) return;
@@ -698,7 +713,32 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
     double u64[2] = {wv[0], wv[1]};
     float zh[2] = {0.0f, 0.0f}, zl[2] = {0.0f, 0.0f};
     int i = 0;
-    for (; i + 2 <= k; i += 2) {        // two columns' loads in flight before arithmetic
+    for (; i + 4 <= k; i += 4) {        // four columns' loads in flight before arithmetic
+      double q[2][2], q2[2][2];
+#pragma unroll
+      for (int j = 0; j < 2; j++) load_q(Q + (int64_t)(i + j) * ldq, g, q[j]);
+#pragma unroll
+      for (int j = 0; j < 2; j++) load_q(Q + (int64_t)(i + 2 + j) * ldq, g, q2[j]);
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        wn[0] = fma(-q[j][0], sT[i + j], wn[0]);
+        wn[1] = fma(-q[j][1], sT[i + j], wn[1]);
+        wn[0] = fma(-q2[j][0], sT[i + 2 + j], wn[0]);
+        wn[1] = fma(-q2[j][1], sT[i + 2 + j], wn[1]);
+      }
+      const bool ok = cok & df_in_range(q[0][0]) & df_in_range(q[0][1]) &
+                      df_in_range(q[1][0]) & df_in_range(q[1][1]) &
+                      df_in_range(q2[0][0]) & df_in_range(q2[0][1]) &
+                      df_in_range(q2[1][0]) & df_in_range(q2[1][1]);
+      if (__builtin_expect(__all_sync(__activemask(), ok), 1)) {
+        f64x_update_pair<true>(q, sC, cH, cL, i, u64, zh, zl);
+        f64x_update_pair<true>(q2, sC, cH, cL, i + 2, u64, zh, zl);
+      } else {
+        f64x_update_pair<false>(q, sC, cH, cL, i, u64, zh, zl);
+        f64x_update_pair<false>(q2, sC, cH, cL, i + 2, u64, zh, zl);
+      }
+    }
+    for (; i + 2 <= k; i += 2) {
       double q[2][2];
 #pragma unroll
       for (int j = 0; j < 2; j++) load_q(Q + (int64_t)(i + j) * ldq, g, q[j]);
@@ -986,16 +1026,35 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
   timing_begin(ctx, KID_REDUCE);
   if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
       ctx->fp64_mode == 1) {
-    const int ntask = k + 1;
+    // nw <= 16 warps of TPW task slots each (at most TPW - 1 idle slots per CTA), as
+    // many CTAs per SM as registers allow (at most PARTIAL_CTAS_PER_SM)
+    const int ntask = k + 2;
+    const int tpw = ntask <= 16 ? 1 : (ntask <= 32 ? 2 : (ntask <= 128 ? 4 : 8));
+    const int nw = (ntask + tpw - 1) / tpw;
+    const int ti = tpw == 1 ? 0 : (tpw == 2 ? 1 : (tpw == 4 ? 2 : 3));
+    int& occ = ctx->red_occ[ti][nw];
+    if (occ == 0) {
+      int n = 0;
+      cudaError_t e;
+      if (tpw == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<1, 2>, 32 * nw, 0);
+      else if (tpw == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<2, 2>, 32 * nw, 0);
+      else if (tpw == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<4, 1>, 32 * nw, 0);
+      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<8, 1>, 32 * nw, 0);
+      if (e != cudaSuccess || n < 1) n = 1;
+      occ = n > PARTIAL_CTAS_PER_SM ? PARTIAL_CTAS_PER_SM : n;
+    }
+    int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);
+    int64_t gsz = (int64_t)ctx->num_sms * occ;
+    const int g = (int)(gsz < gcap ? gsz : (gcap < 1 ? 1 : gcap));
     auto go = [&](auto kern) {
-      kern<<<grid, RED_THREADS, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
-                                                  (const double*)y, m, ctx->partials,
-                                                  ctx->counters, ctx->scal, sa);
+      kern<<<g, 32 * nw, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
+                                           (const double*)y, m, ctx->partials, ctx->counters,
+                                           ctx->scal, sa);
     };
-    if (ntask <= RED_WARPS) go(k_reduce_f64x<1>);
-    else if (ntask <= 2 * RED_WARPS) go(k_reduce_f64x<2>);
-    else if (ntask <= 4 * RED_WARPS) go(k_reduce_f64x<4>);
-    else go(k_reduce_f64x<8>);
+    if (tpw == 1) go(k_reduce_f64x<1, 2>);
+    else if (tpw == 2) go(k_reduce_f64x<2, 2>);
+    else if (tpw == 4) go(k_reduce_f64x<4, 1>);
+    else go(k_reduce_f64x<8, 1>);
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
     if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
     else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);
