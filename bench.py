@@ -143,6 +143,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest value of x over all ranks (the slowest rank's time); x itself at ws = 1.
+    The process group's backend decides the device of the exchanged tensor (NCCL: cuda)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ws: int, n: int, steps: int, ms_max: float) -> float:
+    """Whole-job Arnoldi steps per second: every rank ran `steps` expansions of n steps,
+    timed by the slowest rank."""
+    return ws * n * steps / (ms_max / 1e3)
+
+
 def cpu_oracle_sample(n, N_sample=126, seed=1002):
     """Time the FP64 oracle on one full n-step expansion of the same operator family at
     N_sample^3 rows; returns (steps/s scaled to the full-size m, seconds, m_sample)."""
@@ -315,14 +333,9 @@ def main():
     kern = ctx.timing_read()
     ctx.timing_enable(False)
     launches = ctx.launch_count() - launches0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-
+    ms_total = max_over_ranks(ms_total, ws)
     ms_per = ms_total / args.steps
-    value = ws * n * args.steps / (ms_total / 1e3)
+    value = replica_rate(ws, n, args.steps, ms_total)
     total_bytes, per_kernel_bytes = algorithmic_bytes(m, nnz, n)
     hbm_peak, peak_kind = peaks()
     gbs = total_bytes / (ms_per / 1e3) / 1e9
@@ -407,13 +420,8 @@ def main():
             H_host.copy_(st.Hbuf[:n, :n + 1], non_blocking=True)
         e3.record(stream)
         barrier()
-        ms_e2e = e2.elapsed_time(e3)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": ws * n * args.steps / (ms_e2e / 1e3), "unit": "steps/s",
+        ms_e2e = max_over_ranks(e2.elapsed_time(e3), ws)
+        e2e = {"value": replica_rate(ws, n, args.steps, ms_e2e), "unit": "steps/s",
                "h2d_bytes_per_step": m * 8, "d2h_bytes_per_step": n * (n + 1) * 8}
 
     solvers = None
