@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--no-solvers", action="store_true",
                    help="skip the GMRES time-to-1e-10 runs (plain FP64 vs FP32/BF16 IR)")
     p.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1])
+    p.add_argument("--staged", type=int, default=None, choices=[0, 1, 2, 3],
+                   help="kernel variants of the basis passes (kc_set_staged flags); "
+                        "default: the library's")
     p.add_argument("--no-check", action="store_true",
                    help="skip the loss-of-orthogonality / Arnoldi-relation check")
     return p.parse_args()
@@ -291,6 +294,8 @@ def main():
     r0_host = gaussian_vector(m, 1002)
     ctx = kc.Context(local)
     ctx.set_fp64_mode(args.fp64_mode)
+    if args.staged is not None:
+        ctx.set_staged(args.staged)
     A = kc.DeviceCSR(Ah)
     del Ah
     n = args.n

@@ -103,10 +103,13 @@ const char* kc_last_error(const kc_ctx* ctx);
  *     so Q and H keep FP64 accuracy while half of the FP64 FMAs leave the FP64 pipe. */
 kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode);
 int kc_get_fp64_mode(const kc_ctx* ctx);
-/* Kernel variant of the FP64 basis passes: 0 streams the basis through registers; 1 stages
- * basis tiles in shared memory with bulk asynchronous copies (one producer thread and an
- * mbarrier ring per SM).  Same arithmetic either way. */
-kc_status kc_set_staged(kc_ctx* ctx, int on);
+/* Kernel variants of the FP64 basis passes (bit flags; same arithmetic either way):
+ *  1: the DCGS2 update stages basis tiles in shared memory with bulk asynchronous copies
+ *     (one producer thread and an mbarrier ring per SM);
+ *  2: the fused DCGS2 reduction stages 2D tiles of the basis with tensor-memory copies
+ *     (cp.async.bulk.tensor, one producer thread, sixteen consumer warps per SM).
+ * 0 streams both passes through registers. */
+kc_status kc_set_staged(kc_ctx* ctx, int flags);
 /* Number of SMs and the persistent grid size used for reductions. */
 kc_status kc_device_info(const kc_ctx* ctx, int* num_sms, int* reduce_grid);
 /* Number of kernels this context has launched since creation (host-side counter). */

@@ -52,9 +52,12 @@ class Context:
         """0: all FP64 products; 1: FP64 with float-float offload (default)."""
         self.check(self.lib.kc_set_fp64_mode(self.handle, mode))
 
-    def set_staged(self, on: bool):
-        """Stage the FP64 basis passes through shared memory with bulk copies."""
-        self.check(self.lib.kc_set_staged(self.handle, 1 if on else 0))
+    STAGED_UPDATE, STAGED_REDUCE = 1, 2
+
+    def set_staged(self, flags: int):
+        """Kernel variants of the FP64 basis passes: STAGED_UPDATE (bulk-copy ring) and/or
+        STAGED_REDUCE (tensor-copy ring); 0 streams both through registers."""
+        self.check(self.lib.kc_set_staged(self.handle, int(flags)))
 
     @property
     def fp64_mode(self) -> int:

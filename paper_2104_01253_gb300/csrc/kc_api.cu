@@ -163,9 +163,9 @@ kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode) {
 
 int kc_get_fp64_mode(const kc_ctx* ctx) { return ctx ? ctx->fp64_mode : -1; }
 
-kc_status kc_set_staged(kc_ctx* ctx, int on) {
-  if (!ctx || on < 0 || on > 1) return KC_ERR_INVALID_ARG;
-  ctx->staged = on;
+kc_status kc_set_staged(kc_ctx* ctx, int flags) {
+  if (!ctx || flags < 0 || flags > 3) return KC_ERR_INVALID_ARG;
+  ctx->staged = flags;
   return KC_OK;
 }
 

@@ -101,7 +101,7 @@ struct kc_ctx {
   size_t cnn_ws_len;
   int64_t launches;
   int fp64_mode;           // 0: every product in FP64; 1: FP64 with float-float offload
-  int staged;              // 1: FP64 basis passes staged through shared memory by bulk copies
+  int staged;              // bit 0: staged FP64 update; bit 1: tensor-copy staged reduction
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
   kc::TimingRec* trec;

@@ -982,6 +982,12 @@ static int reduce_grid_for(const kc_ctx* ctx, int64_t ngroups) {
   return (int)b;
 }
 
+}  // namespace kc
+
+#include "kc_reduce_tma.cuh"
+
+namespace kc {
+
 kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype) {
   int grid = grid_for(ctx, A->m, 256, 8);
   if ((A->val_dtype == KC_F64) != (vec_dtype == KC_F64))
@@ -1025,6 +1031,11 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     return fail(ctx, KC_ERR_INVALID_ARG, "reduce: unsupported basis/vector types %d/%d", q_dtype, vec_dtype);
   timing_begin(ctx, KID_REDUCE);
   if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
+      (ctx->staged & 2) && reduce_tma_supported(k, m)) {
+    kc_status st = launch_reduce_tma(ctx, (const double*)Q, ldq, k, (const double*)x,
+                                     (const double*)y, m, ctx->fp64_mode == 1, sa);
+    if (st != KC_OK) return st;
+  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
       ctx->fp64_mode == 1) {
     // nw <= 16 warps of TPW task slots each (at most TPW - 1 idle slots per CTA), as
     // many CTAs per SM as registers allow (at most PARTIAL_CTAS_PER_SM)
@@ -1071,7 +1082,7 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
 
 kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, int k, void* w,
                               const void* v, int64_t m, int vec_dtype) {
-  if (q_dtype == KC_F64 && ctx->staged)
+  if (q_dtype == KC_F64 && (ctx->staged & 1))
     return launch_update_staged(ctx, (double*)Q, ldq, k, (double*)w, (const double*)v, m);
   const int R = vec_dtype == KC_F64 ? 2 : 4;
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);

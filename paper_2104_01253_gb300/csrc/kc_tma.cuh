@@ -37,6 +37,25 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// The same wait polling with test_wait (never suspends the thread).
+__device__ __forceinline__ bool mbar_wait_spin(unsigned long long* bar, unsigned int parity,
+                                               long long budget) {
+  const long long t0 = clock64();
+  while (!mbar_test_wait(bar, parity))
+    if (clock64() - t0 > budget) return false;
+  return true;
+}
+
 // Wait for the phase with the given parity; gives up after `budget` clock cycles
 // (returns false).
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity,

@@ -70,16 +70,23 @@ def test_spmv_matches_scipy(kc, ctx, name, make):
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("staged", [0, 2, 3])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name,make", CASES)
 @pytest.mark.parametrize("n", [1, 2, 17, 50])
-def test_dcgs2_matches_oracle(kc, ctx, name, make, n, mode):
-    """Both FP64 modes: all-FP64 products (0) and FP64 with float-float offload (1)."""
+def test_dcgs2_matches_oracle(kc, ctx, name, make, n, mode, staged):
+    """Both FP64 modes: all-FP64 products (0) and FP64 with float-float offload (1); the
+    register-streaming kernels (staged 0), the tensor-copy staged reduction (2) and that
+    with the bulk-copy staged update (3)."""
     Ah = make()
     r0 = gaussian_vector(Ah.m, 1002)
     ctx.set_fp64_mode(mode)
-    st = _run_dcgs2(kc, ctx, Ah, r0, n)
-    ctx.set_fp64_mode(1)
+    ctx.set_staged(staged)
+    try:
+        st = _run_dcgs2(kc, ctx, Ah, r0, n)
+    finally:
+        ctx.set_fp64_mode(1)
+        ctx.set_staged(0)
     Qg = st.Q(n + 1).cpu().numpy()
     Hg = st.H(n + 1, n).cpu().numpy()
     Qo, Ho = orc.dcgs2_arnoldi(Ah.to_scipy(), r0, n)
