@@ -36,6 +36,10 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 FMA peak derived from unit counts and the maximum clock: 152 SMs x 2 DFMA/clk/SM
 # x 2 flop x 2.070 GHz (a DFMA throughput probe measured 1.20 TFLOP/s at 2.0 GHz)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) over algorithmic bytes of the offload-mode register-streaming
+# kernels, from the ncu capture summarised in profiles/dram_f64x_m4096000_n50.md (all 50
+# launches of an expansion at m = 4,096,000).  Valid only for those kernels as captured.
+TRAFFIC_RATIO = {"reduce": 1.005, "dcgs2_update": 0.945}
 
 
 def parse():
@@ -236,6 +240,52 @@ def solver_suite(kc, ctx, A, m, stream):
             ctx, A, b, x, restart=50, rtol=1e-10, precision=prec, A32=A32, inner_rtol=1e-4,
             inner_max_cycles=3))
     del A32
+    out.update(learned_suite(kc, ctx, timed_solve))
+    return out
+
+
+def learned_suite(kc, ctx, timed_solve):
+    """Config-5 family (2D variable coefficients, kappa log-normal, random smooth wind):
+    the network is trained on the GPU from restart residuals of plain GMRES(40) on seeded
+    operators, then plain GMRES(40), FGMRES(40) with the Jacobi step alone and FGMRES(40)
+    with the learned preconditioner solve held-out operator 64 to 1e-10.  256^2: every
+    method converges; 1024^2 (the config-5 grid): plain and Jacobi stop at an iteration
+    cap.  Training time (data generation + 600 Adam steps) is reported separately."""
+    import torch
+    from paper_2104_01253_gb300 import train as tr
+    out = {}
+    for N, nops, cycles, batch, cap in ((256, 12, 20, 4, 40000), (1024, 16, 10, 2, 20000)):
+        t0 = time.time()
+        ops, X, R, owner = tr.generate_pairs(ctx, N, range(nops), restart=40, max_cycles=cycles)
+        npairs = int(X.shape[0])
+        w, hist = tr.train(ctx, ops, X, R, owner, steps=600, batch=batch, lr=2e-3, seed=0)
+        torch.cuda.synchronize()
+        train_s = time.time() - t0
+        del X, R, ops
+        Ah = tr.varcoef_operator(N, 64)
+        A = kc.DeviceCSR(Ah)
+        b = torch.as_tensor(gaussian_vector(Ah.m, 2064), device="cuda")
+        res = {"grid": "%d^2" % N, "training": {"operators": nops, "pairs": npairs,
+                                                "adam_steps": 600, "batch": batch,
+                                                "seconds": train_s,
+                                                "loss_first": float(np.mean(hist[:20])),
+                                                "loss_last": float(np.mean(hist[-50:]))}}
+        for name, fn in (
+                ("plain_gmres40", lambda x: kc.gmres_solve(ctx, A, b, x, restart=40,
+                                                           rtol=1e-10, maxit=cap)),
+                ("jacobi_fgmres40", lambda x: kc.fgmres_solve(ctx, A, None, N, N, b, x,
+                                                              restart=40, rtol=1e-10,
+                                                              maxit=cap,
+                                                              precond=kc.PREC_JACOBI)),
+                ("learned_fgmres40", lambda x: kc.fgmres_solve(ctx, A, w, N, N, b, x,
+                                                               restart=40, rtol=1e-10,
+                                                               maxit=40000))):
+            x = torch.zeros_like(b)
+            info = timed_solve(lambda: fn(x))
+            info["converged"] = info["rel_resid_true"] <= 1e-10
+            res[name] = info
+        out["config5_learned_%d" % N] = res
+        del A, b, w
     return out
 
 
@@ -375,7 +425,12 @@ def main():
         roofline = {"bound": "alu", "achieved": d["tflops"], "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": f_alu,
                     "peak_kind": "derived FP64 FMA peak (152 SMs x 2 DFMA/clk x 2.07 GHz)"}
-    roofline.update({"kernel": dom, "traffic": None,
+    traffic = None
+    if ctx.fp64_mode == 1 and not args.staged and dom in TRAFFIC_RATIO:
+        traffic = TRAFFIC_RATIO[dom] * per_kernel_bytes[dom] * args.steps / max(d["cnt"], 1)
+    roofline.update({"kernel": dom, "traffic": traffic,
+                     "traffic_note": "bytes per launch: the ncu DRAM/algorithmic ratio at "
+                                     "m = 4.1 M times this run's algorithmic bytes per launch",
                      "avg_launch_ms": d["ms"] / max(d["cnt"], 1),
                      "fp64_tflops": d["tflops"], "fp64_frac": f_alu,
                      "hbm_gbs": d["gbs"], "hbm_frac": f_hbm,

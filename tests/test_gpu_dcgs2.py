@@ -97,6 +97,28 @@ def test_dcgs2_matches_oracle(kc, ctx, name, make, n, mode, staged):
     assert ctx.read_status() == 0
 
 
+@pytest.mark.parametrize("case", ["tiny_entries", "huge_operator"])
+def test_offload_falls_back_to_fp64_outside_the_float_range(kc, ctx, case):
+    """Operands outside [2^-80, 2^98) take the FP64 path of the offload kernels: a start
+    vector with entries of 1e-30 (basis entries far below 2^-80) and an operator scaled by
+    1e35 (v = A w above 2^98).  The result must still match the oracle to 1e-12."""
+    Ah = convdiff_csr(12, 3, [1.0, 0.5, 0.25])                           # m = 1728
+    r0 = gaussian_vector(Ah.m, 1005)
+    if case == "tiny_entries":
+        r0[::3] *= 1e-30
+    else:
+        Ah = CSR(Ah.m, Ah.row_ptr, Ah.col_idx, Ah.val * 1e35)
+    n = 20
+    ctx.set_fp64_mode(1)
+    st = _run_dcgs2(kc, ctx, Ah, r0, n)
+    Hg = st.H(n + 1, n).cpu().numpy()
+    Qg = st.Q(n + 1).cpu().numpy()
+    Qo, Ho = orc.dcgs2_arnoldi(Ah.to_scipy(), r0, n)
+    assert np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho) <= H_TOL
+    assert loo(Qg) <= 1e-13
+    assert ctx.read_status() == 0
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_dcgs2_stepwise_state_matches_oracle(kc, ctx, mode):
     """After every step: pending w, the lagged H columns and alpha agree with the oracle.
