@@ -110,6 +110,10 @@ int kc_get_fp64_mode(const kc_ctx* ctx);
  *     (cp.async.bulk.tensor, one producer thread, sixteen consumer warps per SM).
  * 0 streams both passes through registers. */
 kc_status kc_set_staged(kc_ctx* ctx, int flags);
+/* Kernel of the network's 32 -> 32 convolutions: 0 mma.sync (m16n8k16, registers);
+ * 1 tcgen05 (default: tensor-copy fed, accumulator in tensor memory, operands in shared
+ * memory).  Same arithmetic: BF16 products, FP32 accumulation (summation order differs). */
+kc_status kc_set_conv_kernel(kc_ctx* ctx, int kind);
 /* Number of SMs and the persistent grid size used for reductions. */
 kc_status kc_device_info(const kc_ctx* ctx, int* num_sms, int* reduce_grid);
 /* Number of kernels this context has launched since creation (host-side counter). */

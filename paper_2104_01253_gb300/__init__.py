@@ -52,6 +52,12 @@ class Context:
         """0: all FP64 products; 1: FP64 with float-float offload (default)."""
         self.check(self.lib.kc_set_fp64_mode(self.handle, mode))
 
+    CONV_MMA_SYNC, CONV_TCGEN05 = 0, 1
+
+    def set_conv_kernel(self, kind: int):
+        """Kernel of the network's 32 -> 32 convolutions (CONV_MMA_SYNC or CONV_TCGEN05)."""
+        self.check(self.lib.kc_set_conv_kernel(self.handle, int(kind)))
+
     STAGED_UPDATE, STAGED_REDUCE = 1, 2
 
     def set_staged(self, flags: int):

@@ -117,6 +117,7 @@ kc_status kc_create(kc_ctx** out, int device, void* cuda_stream) {
   if (cudaGetDeviceProperties(&p, device) != cudaSuccess) { delete ctx; return KC_ERR_CUDA; }
   ctx->num_sms = p.multiProcessorCount;
   ctx->fp64_mode = 1;
+  ctx->conv_tc = 1;
   ctx->reduce_grid = 2 * p.multiProcessorCount;
   const size_t plen =
       (size_t)PARTIAL_CTAS_PER_SM * p.multiProcessorCount * (2 * NMAX + 4) * sizeof(double);
@@ -162,6 +163,12 @@ kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode) {
 }
 
 int kc_get_fp64_mode(const kc_ctx* ctx) { return ctx ? ctx->fp64_mode : -1; }
+
+kc_status kc_set_conv_kernel(kc_ctx* ctx, int kind) {
+  if (!ctx || kind < 0 || kind > 1) return KC_ERR_INVALID_ARG;
+  ctx->conv_tc = kind;
+  return KC_OK;
+}
 
 kc_status kc_set_staged(kc_ctx* ctx, int flags) {
   if (!ctx || flags < 0 || flags > 3) return KC_ERR_INVALID_ARG;

@@ -177,72 +177,93 @@ namespace kc {
 
 // ---- end layers and their backward passes (FP32 CUDA cores) ------------------------------
 
-// layer 0: x (1 channel, FP32) -> a1 = ReLU(conv), BF16 NHWC.  One thread per pixel.
+// layer 0: x (1 channel, FP32) -> a1 = ReLU(conv), BF16 NHWC.  A CTA computes an
+// 8 x 32 pixel tile: the haloed input tile and the weights sit in shared memory, each
+// thread computes one pixel's 32 channels into a shared output tile, and the tile rows
+// (2 KB each) leave in coalesced 16-byte stores.
 __global__ void __launch_bounds__(256)
 k_cnn_in(const float* __restrict__ x, bf16* __restrict__ a1, const bf16* __restrict__ wf,
          int H, int W, int B) {
   __shared__ float w0[CNN_C * CNN_TAPS];
+  __shared__ float sx[(CT_H + 2) * (CT_W + 2)];
+  __shared__ __align__(16) unsigned int so[CT_H * CT_W * 16];
   for (int i = threadIdx.x; i < CNN_C * CNN_TAPS; i += blockDim.x) w0[i] = bfload(&wf[CNN_W0 + i]);
+  const int b = blockIdx.z, ty0 = blockIdx.y * CT_H, tx0 = blockIdx.x * CT_W;
+  const float* xb = x + (size_t)b * H * W;
+  for (int i = threadIdx.x; i < (CT_H + 2) * (CT_W + 2); i += blockDim.x) {
+    const int gy = ty0 + i / (CT_W + 2) - 1, gx = tx0 + i % (CT_W + 2) - 1;
+    sx[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? xb[(size_t)gy * W + gx] : 0.0f;
+  }
   __syncthreads();
-  const int64_t n = (int64_t)B * H * W;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = p / ((int64_t)H * W);
-    const int yx = (int)(p % ((int64_t)H * W)), y = yx / W, xx = yx % W;
-    float nb[9];
+  const int py = threadIdx.x / CT_W, px = threadIdx.x % CT_W;
+  float nb[9];
+#pragma unroll
+  for (int t = 0; t < 9; t++) nb[t] = sx[(py + t / 3) * (CT_W + 2) + px + t % 3];
+#pragma unroll
+  for (int c = 0; c < CNN_C; c += 2) {
+    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
     for (int t = 0; t < 9; t++) {
-      const int yy = y + t / 3 - 1, xc = xx + t % 3 - 1;
-      nb[t] = (yy >= 0 && yy < H && xc >= 0 && xc < W) ? x[(b * H + yy) * W + xc] : 0.0f;
+      s0 = fmaf(w0[c * 9 + t], nb[t], s0);
+      s1 = fmaf(w0[(c + 1) * 9 + t], nb[t], s1);
     }
-    unsigned int o[16];
-#pragma unroll
-    for (int c = 0; c < CNN_C; c += 2) {
-      float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-      for (int t = 0; t < 9; t++) {
-        s0 = fmaf(w0[c * 9 + t], nb[t], s0);
-        s1 = fmaf(w0[(c + 1) * 9 + t], nb[t], s1);
-      }
-      o[c / 2] = pack_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
-    }
-    uint4* dst = reinterpret_cast<uint4*>(a1 + p * CNN_C);
-#pragma unroll
-    for (int q = 0; q < 4; q++) dst[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    // word (c / 2) of pixel threadIdx.x, rotated by the pixel index against bank conflicts
+    so[threadIdx.x * 16 + ((c / 2 + threadIdx.x) & 15)] = pack_bf16x2(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+  }
+  __syncthreads();
+  bf16* ob = a1 + (size_t)b * H * W * CNN_C;
+  for (int i = threadIdx.x; i < CT_H * CT_W * 4; i += blockDim.x) {      // 16-byte pieces
+    const int pix = i >> 2, q = i & 3;
+    const int gy = ty0 + pix / CT_W, gx = tx0 + pix % CT_W;
+    if (gy >= H || gx >= W) continue;
+    uint4 v;
+    v.x = so[pix * 16 + ((4 * q + 0 + pix) & 15)];
+    v.y = so[pix * 16 + ((4 * q + 1 + pix) & 15)];
+    v.z = so[pix * 16 + ((4 * q + 2 + pix) & 15)];
+    v.w = so[pix * 16 + ((4 * q + 3 + pix) & 15)];
+    *reinterpret_cast<uint4*>(ob + ((size_t)gy * W + gx) * CNN_C + q * 8) = v;
   }
 }
 
-// layer 5: a5 (32 channels, BF16) -> y (1 channel, FP32), no activation.
+// layer 5: a5 (32 channels, BF16) -> y (1 channel, FP32), no activation.  A CTA loads the
+// haloed 10 x 34 input tile into shared memory in coalesced 16-byte pieces (pixel stride
+// 40 BF16: conflict-free 16-byte reads) and each thread computes one output pixel.
 __global__ void __launch_bounds__(256)
 k_cnn_out(const bf16* __restrict__ a5, float* __restrict__ y, const bf16* __restrict__ wf,
           int H, int W, int B) {
   __shared__ float w5[CNN_K];
+  __shared__ __align__(16) bf16 sIn[HALO_PIX * CPAD];
   for (int i = threadIdx.x; i < CNN_K; i += blockDim.x) w5[i] = bfload(&wf[CNN_W5 + i]);
+  const int b = blockIdx.z, ty0 = blockIdx.y * CT_H, tx0 = blockIdx.x * CT_W;
+  const bf16* ab = a5 + (size_t)b * H * W * CNN_C;
+  for (int i = threadIdx.x; i < HALO_PIX * 4; i += blockDim.x) {
+    const int pix = i >> 2, ch = i & 3;
+    const int gy = ty0 + pix / (CT_W + 2) - 1, gx = tx0 + pix % (CT_W + 2) - 1;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+      v = *reinterpret_cast<const uint4*>(&ab[((size_t)gy * W + gx) * CNN_C + ch * 8]);
+    *reinterpret_cast<uint4*>(&sIn[pix * CPAD + ch * 8]) = v;
+  }
   __syncthreads();
-  const int64_t n = (int64_t)B * H * W;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = p / ((int64_t)H * W);
-    const int yx = (int)(p % ((int64_t)H * W)), yy0 = yx / W, x0 = yx % W;
-    float s = 0.f;
-    for (int t = 0; t < 9; t++) {
-      const int yy = yy0 + t / 3 - 1, xc = x0 + t % 3 - 1;
-      if (yy < 0 || yy >= H || xc < 0 || xc >= W) continue;
-      const uint4* src = reinterpret_cast<const uint4*>(a5 + ((b * H + yy) * W + xc) * CNN_C);
+  const int py = threadIdx.x / CT_W, px = threadIdx.x % CT_W;
+  const int gy = ty0 + py, gx = tx0 + px;
+  float s = 0.f;
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const uint4 v = src[q];
-        const unsigned int u[4] = {v.x, v.y, v.z, v.w};
+  for (int t = 0; t < 9; t++) {
+    const bf16* src = &sIn[((py + t / 3) * (CT_W + 2) + px + t % 3) * CPAD];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const int ci = q * 8 + e * 2;
-          s = fmaf(w5[t * CNN_C + ci], bf_lo(u[e]), s);
-          s = fmaf(w5[t * CNN_C + ci + 1], bf_hi(u[e]), s);
-        }
+    for (int q = 0; q < 4; q++) {
+      const uint4 v = *reinterpret_cast<const uint4*>(src + q * 8);
+      const unsigned int u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int ci = q * 8 + e * 2;
+        s = fmaf(w5[t * CNN_C + ci], bf_lo(u[e]), s);
+        s = fmaf(w5[t * CNN_C + ci + 1], bf_hi(u[e]), s);
       }
     }
-    y[p] = s;
   }
+  if (gy < H && gx < W) y[((size_t)b * H + gy) * W + gx] = s;
 }
 
 // backward of layer 5: dz4 = (conv^T(g, w5)) * (a5 > 0), BF16 NHWC
@@ -284,39 +305,106 @@ k_cnn_out_bwd(const float* __restrict__ g, const bf16* __restrict__ a5, bf16* __
   }
 }
 
-// weight gradient of layer 5: dw5[tap][ci] += sum_p g[p] * a5[p + off(tap)][ci]
-// (CTA: 256 pixels; thread (tap, ci) pairs; FP32 atomics into the gradient)
-__global__ void __launch_bounds__(288)
-k_cnn_dw_out(const float* __restrict__ g, const bf16* __restrict__ a5, float* __restrict__ dw,
-             int H, int W, int B) {
-  const int t = threadIdx.x / CNN_C, ci = threadIdx.x % CNN_C;
-  const int dy = t / 3 - 1, dx = t % 3 - 1;
-  const int64_t n = (int64_t)B * H * W;
-  float s = 0.f;
-  for (int64_t p = blockIdx.x * 256; p < n && p < (int64_t)(blockIdx.x + 1) * 256; p++) {
-    const int64_t b = p / ((int64_t)H * W);
-    const int yx = (int)(p % ((int64_t)H * W)), yy = yx / W + dy, xc = yx % W + dx;
-    if (yy < 0 || yy >= H || xc < 0 || xc >= W) continue;
-    s = fmaf(g[p], bfload(&a5[((b * H + yy) * W + xc) * CNN_C + ci]), s);
+// Weight gradients of the two 1-channel layers.  A thread owns (pixel, chunk of 8
+// channels) pairs in a grid-stride loop and keeps 9 x 8 partial sums in registers; the CTA
+// adds its threads' sums in shared memory (fixed order) and commits them with one atomic
+// per weight.
+constexpr int DW1_THREADS = 256;
+
+// CTA-wide sum of acc[9][8] over the threads with the same chunk, then dw[off(t, j)] += sum
+template <typename F>
+__device__ __forceinline__ void dw1_commit(float (&acc)[9][8], int chunk, F index,
+                                           float* __restrict__ dw) {
+  __shared__ float red[DW1_THREADS / 32][4][72];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // lanes with equal chunk (lane % 4) first: xor 4, 8, 16
+#pragma unroll
+  for (int t = 0; t < 9; t++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      float v = acc[t][j];
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      acc[t][j] = v;
+    }
+  if (lane < 4)
+#pragma unroll
+    for (int t = 0; t < 9; t++)
+#pragma unroll
+      for (int j = 0; j < 8; j++) red[warp][chunk][t * 8 + j] = acc[t][j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * 72; i += blockDim.x) {
+    const int c = i / 72, tj = i % 72;
+    float s = 0.f;
+    for (int w = 0; w < DW1_THREADS / 32; w++) s += red[w][c][tj];
+    atomicAdd(&dw[index(c * 8 + tj % 8, tj / 8)], s);
   }
-  atomicAdd(&dw[CNN_W5 + t * CNN_C + ci], s);
 }
 
-// weight gradient of layer 0: dw0[co][tap] += sum_p dz0[p][co] * x[p + off(tap)]
-__global__ void __launch_bounds__(288)
+// layer 5: dw5[tap][ci] += sum_p g[p] * a5[p + off(tap)][ci]; over input pixels q = p + off:
+// sum_q a5[q][ci] * g[q - off(tap)]
+__global__ void __launch_bounds__(DW1_THREADS)
+k_cnn_dw_out(const float* __restrict__ g, const bf16* __restrict__ a5, float* __restrict__ dw,
+             int H, int W, int B) {
+  const int chunk = threadIdx.x & 3;
+  float acc[9][8];
+#pragma unroll
+  for (int t = 0; t < 9; t++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[t][j] = 0.f;
+  const int64_t n = (int64_t)B * H * W;
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2; q < n;
+       q += ((int64_t)gridDim.x * blockDim.x) >> 2) {
+    const int64_t b = q / ((int64_t)H * W);
+    const int yx = (int)(q - b * H * W), y = yx / W, xx = yx % W;
+    const uint4 av = *reinterpret_cast<const uint4*>(a5 + q * CNN_C + chunk * 8);
+    const unsigned int u[4] = {av.x, av.y, av.z, av.w};
+    float a[8];
+#pragma unroll
+    for (int e = 0; e < 4; e++) { a[2 * e] = bf_lo(u[e]); a[2 * e + 1] = bf_hi(u[e]); }
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      const int py = y - (t / 3 - 1), px = xx - (t % 3 - 1);
+      if (py < 0 || py >= H || px < 0 || px >= W) continue;
+      const float gv = g[(b * H + py) * W + px];
+#pragma unroll
+      for (int j = 0; j < 8; j++) acc[t][j] = fmaf(gv, a[j], acc[t][j]);
+    }
+  }
+  dw1_commit(acc, chunk, [](int ci, int t) { return CNN_W5 + t * CNN_C + ci; }, dw);
+}
+
+// layer 0: dw0[co][tap] += sum_p dz0[p][co] * x[p + off(tap)]
+__global__ void __launch_bounds__(DW1_THREADS)
 k_cnn_dw_in(const bf16* __restrict__ dz0, const float* __restrict__ x, float* __restrict__ dw,
             int H, int W, int B) {
-  const int co = threadIdx.x / CNN_TAPS, t = threadIdx.x % CNN_TAPS;
-  const int dy = t / 3 - 1, dx = t % 3 - 1;
+  const int chunk = threadIdx.x & 3;
+  float acc[9][8];
+#pragma unroll
+  for (int t = 0; t < 9; t++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) acc[t][j] = 0.f;
   const int64_t n = (int64_t)B * H * W;
-  float s = 0.f;
-  for (int64_t p = blockIdx.x * 256; p < n && p < (int64_t)(blockIdx.x + 1) * 256; p++) {
+  for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 2; p < n;
+       p += ((int64_t)gridDim.x * blockDim.x) >> 2) {
     const int64_t b = p / ((int64_t)H * W);
-    const int yx = (int)(p % ((int64_t)H * W)), yy = yx / W + dy, xc = yx % W + dx;
-    if (yy < 0 || yy >= H || xc < 0 || xc >= W) continue;
-    s = fmaf(bfload(&dz0[p * CNN_C + co]), x[(b * H + yy) * W + xc], s);
+    const int yx = (int)(p - b * H * W), y = yx / W, xx = yx % W;
+    const uint4 dv = *reinterpret_cast<const uint4*>(dz0 + p * CNN_C + chunk * 8);
+    const unsigned int u[4] = {dv.x, dv.y, dv.z, dv.w};
+    float d[8];
+#pragma unroll
+    for (int e = 0; e < 4; e++) { d[2 * e] = bf_lo(u[e]); d[2 * e + 1] = bf_hi(u[e]); }
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+      const int qy = y + t / 3 - 1, qx = xx + t % 3 - 1;
+      if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;
+      const float xv = x[(b * H + qy) * W + qx];
+#pragma unroll
+      for (int j = 0; j < 8; j++) acc[t][j] = fmaf(d[j], xv, acc[t][j]);
+    }
   }
-  atomicAdd(&dw[CNN_W0 + co * CNN_TAPS + t], s);
+  dw1_commit(acc, chunk, [](int co, int t) { return CNN_W0 + co * CNN_TAPS + t; }, dw);
 }
 
 }  // namespace kc
@@ -481,9 +569,24 @@ __global__ void k_cnn_adam(float* __restrict__ w, const float* __restrict__ g,
 static dim3 conv_grid(int H, int W, int B) {
   return dim3((W + CT_W - 1) / CT_W, (H + CT_H - 1) / CT_H, B);
 }
+// pixel-chunk threads (4 per pixel), at most 4 CTAs per SM
+static int dw1_grid(const kc_ctx* ctx, int64_t n) {
+  int64_t g = (4 * n + DW1_THREADS - 1) / DW1_THREADS, cap = (int64_t)ctx->num_sms * 4;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
 static int pix_grid(const kc_ctx* ctx, int64_t n) {
   int64_t g = (n + 255) / 256, cap = (int64_t)ctx->num_sms * 16;
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+// One 32 -> 32 layer on the kernel the context selects (tcgen05 or mma.sync).
+static kc_status conv32(kc_ctx* ctx, const bf16* in, bf16* out, const bf16* w, int B, int H,
+                        int W, int epi, const bf16* mask) {
+  if (ctx->conv_tc) return cnn_conv32_tc(ctx, in, out, w, B, H, W, epi, mask);
+  timing_begin(ctx, KID_OTHER);
+  k_cnn_conv32<<<conv_grid(H, W, B), 256, 0, ctx->stream>>>(in, out, w, H, W, epi, mask);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
 }
 
 // Forward pass.  wf/wt: BF16 weights prepared by cnn_prep.  acts: 5 activation buffers of
@@ -492,18 +595,17 @@ kc_status cnn_forward(kc_ctx* ctx, const bf16* wf, const float* x, float* y, bf1
                       bool keep, int B, int H, int W) {
   const int64_t n = (int64_t)B * H * W;
   timing_begin(ctx, KID_OTHER);
-  k_cnn_in<<<pix_grid(ctx, n), 256, 0, ctx->stream>>>(x, acts[0], wf, H, W, B);
+  k_cnn_in<<<conv_grid(H, W, B), 256, 0, ctx->stream>>>(x, acts[0], wf, H, W, B);
   KC_LAUNCHED(ctx);
   for (int l = 0; l < 4; l++) {
     const bf16* src = keep ? acts[l] : acts[l & 1];
     bf16* dst = keep ? acts[l + 1] : acts[(l + 1) & 1];
-    timing_begin(ctx, KID_OTHER);
-    k_cnn_conv32<<<conv_grid(H, W, B), 256, 0, ctx->stream>>>(
-        src, dst, wf + CNN_WMID + l * CNN_WMID_SZ, H, W, CONV_RELU, nullptr);
-    KC_LAUNCHED(ctx);
+    kc_status s = conv32(ctx, src, dst, wf + CNN_WMID + l * CNN_WMID_SZ, B, H, W, CONV_RELU,
+                         nullptr);
+    if (s != KC_OK) return s;
   }
   timing_begin(ctx, KID_OTHER);
-  k_cnn_out<<<pix_grid(ctx, n), 256, 0, ctx->stream>>>(keep ? acts[4] : acts[0], y, wf, H, W, B);
+  k_cnn_out<<<conv_grid(H, W, B), 256, 0, ctx->stream>>>(keep ? acts[4] : acts[0], y, wf, H, W, B);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }
@@ -523,7 +625,7 @@ kc_status cnn_backward(kc_ctx* ctx, const bf16* wf, const bf16* wt, const float*
   const int64_t n = (int64_t)B * H * W;
   const int nblk = (int)((n + 255) / 256);
   timing_begin(ctx, KID_OTHER);
-  k_cnn_dw_out<<<nblk, 288, 0, ctx->stream>>>(g, acts[4], dw, H, W, B);
+  k_cnn_dw_out<<<dw1_grid(ctx, n), DW1_THREADS, 0, ctx->stream>>>(g, acts[4], dw, H, W, B);
   KC_LAUNCHED(ctx);
   timing_begin(ctx, KID_OTHER);
   k_cnn_out_bwd<<<pix_grid(ctx, n), 256, 0, ctx->stream>>>(g, acts[4], dz[0], wf, H, W, B);
@@ -534,14 +636,13 @@ kc_status cnn_backward(kc_ctx* ctx, const bf16* wf, const bf16* wt, const float*
     k_cnn_dw32<<<conv_grid(H, W, B), 256, 0, ctx->stream>>>(
         dz[cur], acts[l], dw + CNN_WMID + l * CNN_WMID_SZ, H, W);
     KC_LAUNCHED(ctx);
-    timing_begin(ctx, KID_OTHER);
-    k_cnn_conv32<<<conv_grid(H, W, B), 256, 0, ctx->stream>>>(
-        dz[cur], dz[cur ^ 1], wt + l * CNN_WMID_SZ, H, W, CONV_MASK, acts[l]);
-    KC_LAUNCHED(ctx);
+    kc_status s = conv32(ctx, dz[cur], dz[cur ^ 1], wt + l * CNN_WMID_SZ, B, H, W, CONV_MASK,
+                         acts[l]);
+    if (s != KC_OK) return s;
     cur ^= 1;
   }
   timing_begin(ctx, KID_OTHER);
-  k_cnn_dw_in<<<nblk, 288, 0, ctx->stream>>>(dz[cur], x, dw, H, W, B);
+  k_cnn_dw_in<<<dw1_grid(ctx, n), DW1_THREADS, 0, ctx->stream>>>(dz[cur], x, dw, H, W, B);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }

@@ -102,6 +102,7 @@ struct kc_ctx {
   int64_t launches;
   int fp64_mode;           // 0: every product in FP64; 1: FP64 with float-float offload
   int staged;              // bit 0: staged FP64 update; bit 1: tensor-copy staged reduction
+  int conv_tc;             // 32 -> 32 convolutions: 0 mma.sync, 1 tcgen05 (tensor memory)
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
   kc::TimingRec* trec;
@@ -170,6 +171,9 @@ kc_status cnn_backward(kc_ctx* ctx, const __nv_bfloat16* wf, const __nv_bfloat16
                        __nv_bfloat16* const* dz, float* dw, int B, int H, int W);
 kc_status cnn_loss_grad(kc_ctx* ctx, const float* y, const float* e, double* sums, float* g,
                         int B, int64_t npix);
+kc_status cnn_conv32_tc(kc_ctx* ctx, const __nv_bfloat16* in, __nv_bfloat16* out,
+                        const __nv_bfloat16* w, int B, int H, int W, int epi,
+                        const __nv_bfloat16* mask);
 kc_status cnn_residual_loss_grad(kc_ctx* ctx, const kc_csr* A, const float* x, const float* y,
                                  const float* r, float* res, double* sums, float* g, int B,
                                  int64_t npix);

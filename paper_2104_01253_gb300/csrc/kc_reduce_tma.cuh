@@ -246,31 +246,11 @@ k_reduce_tma(const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUt
 
 // ---- host side --------------------------------------------------------------------------
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 // FP64 tensor of `cols` columns of `rows` elements (column stride ld elements), box
 // RT_TR x box_cols; cols == 0 encodes a 1D tensor of `rows` elements with box RT_TR.
 static bool encode_f64(CUtensorMap* map, const double* p, int64_t rows, int64_t ld, int cols,
                        int box_cols) {
-  EncodeTiledFn fn = encode_fn();
+  EncodeTiledFn fn = tensor_map_encoder();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)(cols > 0 ? cols : 1)};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
@@ -300,7 +280,7 @@ static kc_status launch_tma_inst(kc_ctx* ctx, int grid, const CUtensorMap& tq,
 }
 
 bool reduce_tma_supported(int k, int64_t m) {
-  return k + 2 <= 17 * RT_CH && m >= RT_TR && m < ((int64_t)1 << 31) && encode_fn() != nullptr;
+  return k + 2 <= 17 * RT_CH && m >= RT_TR && m < ((int64_t)1 << 31) && tensor_map_encoder() != nullptr;
 }
 
 kc_status launch_reduce_tma(kc_ctx* ctx, const double* Q, int64_t ldq, int k, const double* x,

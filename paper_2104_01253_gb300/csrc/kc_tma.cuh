@@ -2,6 +2,8 @@
 // bounded waits.  Used by the staged basis-pass kernels.
 #pragma once
 
+#include <cuda.h>
+
 #include "kc_internal.cuh"
 
 namespace kc {
@@ -75,5 +77,27 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned in
 }
 
 constexpr long long WAIT_LIMIT = 4000000000LL;  // cycles (about 2 s) before a wait fails
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime (no link against the driver library)
+static inline EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
 
 }  // namespace kc

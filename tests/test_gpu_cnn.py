@@ -44,8 +44,26 @@ def unpack(flat, template):
     return out
 
 
+def test_tcgen05_conv_single_tile(kc, ctx):
+    """The tcgen05 convolution on one 16 x 8 tile (one MMA group) against the oracle."""
+    B, H, W = 1, 16, 8
+    ws = cnn.init_weights(21)
+    w32 = pack(ws)
+    x = np.random.default_rng(22).standard_normal((B, 1, H, W)).astype(np.float32)
+    ctx.set_conv_kernel(ctx.CONV_TCGEN05)
+    yd = torch.zeros((B, 1, H, W), dtype=torch.float32, device="cuda")
+    kc.kc_cnn_forward(ctx, torch.as_tensor(w32, device="cuda"),
+                      torch.as_tensor(x, device="cuda"), yd, B, H, W)
+    torch.cuda.synchronize()
+    assert ctx.read_status() == 0
+    yo, _ = cnn.forward_bf16_storage(unpack(w32, ws), x.astype(np.float64))
+    y = yd.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 5e-3
+
+
+@pytest.mark.parametrize("conv", [0, 1])
 @pytest.mark.parametrize("B,H,W", [(2, 40, 40), (1, 37, 50), (3, 8, 33)])
-def test_forward_matches_oracle(kc, ctx, B, H, W):
+def test_forward_matches_oracle(kc, ctx, B, H, W, conv):
     ws = cnn.init_weights(3)
     w32 = pack(ws)
     assert w32.size == kc.kc_cnn_param_count()
@@ -53,13 +71,18 @@ def test_forward_matches_oracle(kc, ctx, B, H, W):
     wd = torch.as_tensor(w32, device="cuda")
     xd = torch.as_tensor(x, device="cuda")
     yd = torch.zeros_like(xd)
-    kc.kc_cnn_forward(ctx, wd, xd, yd, B, H, W)
+    ctx.set_conv_kernel(conv)
+    try:
+        kc.kc_cnn_forward(ctx, wd, xd, yd, B, H, W)
+    finally:
+        ctx.set_conv_kernel(ctx.CONV_TCGEN05)
     y = yd.cpu().numpy().astype(np.float64)
     yo, _ = cnn.forward_bf16_storage(unpack(w32, ws), x.astype(np.float64))
     assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 5e-3
 
 
-def test_gradients_match_oracle(kc, ctx):
+@pytest.mark.parametrize("conv", [0, 1])
+def test_gradients_match_oracle(kc, ctx, conv):
     B, H, W = 2, 24, 40
     ws = cnn.init_weights(5)
     w32 = pack(ws)
@@ -69,8 +92,12 @@ def test_gradients_match_oracle(kc, ctx):
     wd = torch.as_tensor(w32, device="cuda")
     grad = torch.zeros_like(wd)
     yd = torch.zeros((B, 1, H, W), dtype=torch.float32, device="cuda")
-    loss = kc.kc_cnn_train_step(ctx, wd, None, None, 0, 0.0, torch.as_tensor(x, device="cuda"),
-                                torch.as_tensor(e, device="cuda"), B, H, W, yd, grad)
+    ctx.set_conv_kernel(conv)
+    try:
+        loss = kc.kc_cnn_train_step(ctx, wd, None, None, 0, 0.0, torch.as_tensor(x, device="cuda"),
+                                    torch.as_tensor(e, device="cuda"), B, H, W, yd, grad)
+    finally:
+        ctx.set_conv_kernel(ctx.CONV_TCGEN05)
     Lo, go, _ = cnn.loss_and_grads_bf16_storage(unpack(w32, ws), x.astype(np.float64),
                                                 e.astype(np.float64))
     assert abs(loss - Lo) <= 1e-3 * Lo
