@@ -223,11 +223,12 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rp,
 // Last CTA of a reduction: deterministic sum of the per-CTA partials, then either a plain
 // store of Q^T x or the scalar step of Algorithm 4 (lines 4-6, 10-12).
 __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int NRHS,
-                                Scalars* __restrict__ sc, int epilogue, const StepArgs& sa) {
+                                Scalars* __restrict__ sc, int epilogue, const StepArgs& sa,
+                                int nparts = -1) {
   __shared__ double tot[PSTRIDE];
   __shared__ double s_alpha;
   const int nval = (k + 1) * NRHS;
-  sum_partials(partials, gridDim.x, nval, tot);
+  sum_partials(partials, nparts < 0 ? (int)gridDim.x : nparts, nval, tot);
   __syncthreads();
 
   if (epilogue != EPI_DCGS2) {
@@ -501,9 +502,12 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // Offloaded reduction, task layout.  ntask = k + 2 tasks of equal FP64 cost (two FP64
 // FMAs per group of two rows): task t < k is column t (C_t = q_t^T w in FP64 and
 // S_t = q_t^T v in float-float), task k is beta = w^T w and task k + 1 is s = w^T v, both
-// in FP64.  A CTA has nw = ceil(ntask / TPW) warps and warp w takes tasks w, w + nw, ...
-// (TPW slots), so at most TPW - 1 slots of a CTA are idle; all warps of a CTA walk the
-// same rows, and w and v come from L1 after the first warp has loaded them.
+// in FP64.  The tasks are cut into nsplit subsets of at most 32 (nt each); the grid is
+// nsplit CTAs per row block, CTA (row block r, subset h) has nw = ceil(nt / TPW) warps and
+// warp w takes the subset's tasks w, w + nw, ... (TPW slots, TPW <= 2), so at most TPW - 1
+// slots of a CTA are idle and every CTA has at most 16 warps (two or more CTAs per SM
+// with 64 registers).  All warps of a CTA walk the same rows; w and v come from L1 after
+// the first warp has loaded them (and from L2 for the other subsets of the row block).
 
 // the operand that task t multiplies into w: q_t, w itself (beta) or v (s); null if idle
 __device__ __forceinline__ const double* f64x_operand(const double* Q, int64_t ldq, int k,
@@ -571,22 +575,25 @@ template <int TPW, int GR>
 __global__ void __launch_bounds__(1024)
 k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
               const double* __restrict__ y, int64_t m, double* __restrict__ partials,
-              unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa) {
+              unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa,
+              int nsplit, int nt) {
   if (sc->stop) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int h = blockIdx.x % nsplit, r = blockIdx.x / nsplit, nr = gridDim.x / nsplit;
   int tk[TPW];
   const double* ap[TPW];
   double ac[TPW], as64[TPW];
   float sh[TPW], sl[TPW];
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
-    tk[i] = warp + nw * i;
+    const int tl = warp + nw * i;                      // task within the subset
+    tk[i] = tl < nt ? h * nt + tl : k + 2;             // k + 2 and above: idle slot
     ap[i] = f64x_operand(Q, ldq, k, x, y, tk[i]);
     ac[i] = 0.0; as64[i] = 0.0; sh[i] = 0.0f; sl[i] = 0.0f;
   }
   const int64_t ngroups = m / 2;
-  const int64_t g0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
-  const int64_t g1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
+  const int64_t g0 = (int64_t)r * ngroups / nr;
+  const int64_t g1 = (int64_t)(r + 1) * ngroups / nr;
   int64_t g = g0 + lane;
   if (GR == 2) {
     for (; g + 32 < g1; g += 64) {
@@ -617,7 +624,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
     else
       f64x_group<TPW, false>(tk, k, xa, ya, qa, ac, as64, sh, sl);
   }
-  if (blockIdx.x == gridDim.x - 1) {           // ragged tail (m odd): FP64
+  if (r == nr - 1) {                             // ragged tail (m odd): FP64
     for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
       const double xs = __ldcg(x + row), ys1 = __ldcg(y + row);
 #pragma unroll
@@ -636,13 +643,13 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
     const double c = warp_sum(ac[i]);
     const double sv = warp_sum(as64[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])));
     if (lane == 0) {
-      double* pp = partials + (int64_t)blockIdx.x * PSTRIDE;
+      double* pp = partials + (int64_t)r * PSTRIDE;  // row block r: one writer per task
       if (t < k) { pp[2 * t] = c; pp[2 * t + 1] = sv; }
       else pp[2 * k + (t - k)] = c;           // beta -> [2k], s -> [2k + 1]
     }
   }
   if (!last_cta(counter)) return;
-  reduce_epilogue(partials, k, 2, sc, EPI_DCGS2, sa);
+  reduce_epilogue(partials, k, 2, sc, EPI_DCGS2, sa, nr);
 }
 
 // Two basis columns of the offloaded update for one group of two rows: u -= Q C in
@@ -1037,35 +1044,52 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     if (st != KC_OK) return st;
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
       ctx->fp64_mode == 1) {
-    // nw <= 16 warps of TPW task slots each (at most TPW - 1 idle slots per CTA), as
-    // many CTAs per SM as registers allow (at most PARTIAL_CTAS_PER_SM)
+    // Task layout: nsplit = ceil(ntask / 32) subsets of nt tasks, CTAs of nw <= 16 warps
+    // with tpw <= 2 slots, tpw chosen (once per k) to maximise resident warps x used slots.
+    // (Three subsets and more, or more subsets than needed, measured slower.)
     const int ntask = k + 2;
-    const int tpw = ntask <= 16 ? 1 : (ntask <= 32 ? 2 : (ntask <= 128 ? 4 : 8));
-    const int nw = (ntask + tpw - 1) / tpw;
-    const int ti = tpw == 1 ? 0 : (tpw == 2 ? 1 : (tpw == 4 ? 2 : 3));
-    int& occ = ctx->red_occ[ti][nw];
-    if (occ == 0) {
-      int n = 0;
-      cudaError_t e;
-      if (tpw == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<1, 2>, 32 * nw, 0);
-      else if (tpw == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<2, 2>, 32 * nw, 0);
-      else if (tpw == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<4, 1>, 32 * nw, 0);
-      else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<8, 1>, 32 * nw, 0);
-      if (e != cudaSuccess || n < 1) n = 1;
-      occ = n > PARTIAL_CTAS_PER_SM ? PARTIAL_CTAS_PER_SM : n;
+    int nsplit, nt, tpw, nw, occ;
+    {
+      int* pick = ctx->red_pick[k];
+      if (pick[0] == 0) {
+        double best = -1.0;
+        const int s0 = (ntask + 31) / 32;
+        for (int ns = s0; ns <= s0; ns++)
+          for (int tp = 1; tp <= 2; tp++) {
+            const int ntt = (ntask + ns - 1) / ns;
+            const int nww = (ntt + tp - 1) / tp;
+            if (nww > 16) continue;
+            int& o = ctx->red_occ[tp - 1][nww];
+            if (o == 0) {
+              int n = 0;
+              cudaError_t e = tp == 1
+                  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<1, 2>, 32 * nww, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<2, 2>, 32 * nww, 0);
+              if (e != cudaSuccess || n < 1) n = 1;
+              o = n > PARTIAL_CTAS_PER_SM ? PARTIAL_CTAS_PER_SM : n;
+            }
+            const int warps = o * nww < 32 ? o * nww : 32;
+            const double score = warps * (double)ntask / ((double)ns * nww * tp) /
+                                 (1.0 + 0.03 * (ns - s0));
+            if (score > best) {
+              best = score;
+              pick[0] = ns; pick[1] = ntt; pick[2] = tp; pick[3] = nww; pick[4] = o;
+            }
+          }
+      }
+      nsplit = pick[0]; nt = pick[1]; tpw = pick[2]; nw = pick[3]; occ = pick[4];
     }
-    int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);
-    int64_t gsz = (int64_t)ctx->num_sms * occ;
-    const int g = (int)(gsz < gcap ? gsz : (gcap < 1 ? 1 : gcap));
+    int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);            // row blocks: >= 4 groups/lane
+    int64_t nr = ((int64_t)ctx->num_sms * occ + nsplit - 1) / nsplit;
+    if (nr > gcap) nr = gcap < 1 ? 1 : gcap;
+    const int g = (int)(nr * nsplit);
     auto go = [&](auto kern) {
       kern<<<g, 32 * nw, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
                                            (const double*)y, m, ctx->partials, ctx->counters,
-                                           ctx->scal, sa);
+                                           ctx->scal, sa, nsplit, nt);
     };
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
-    else if (tpw == 2) go(k_reduce_f64x<2, 2>);
-    else if (tpw == 4) go(k_reduce_f64x<4, 1>);
-    else go(k_reduce_f64x<8, 1>);
+    else go(k_reduce_f64x<2, 2>);
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
     if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
     else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);
