@@ -201,7 +201,8 @@ def solver_suite(kc, ctx, A, m, stream):
     """GMRES time to a 1e-10 relative residual, measured with CUDA events around the
     C-ABI call (device-resident b and x): config 1 (2D, 100^2, GMRES(30)) and, on the
     config-2 matrix, plain FP64 DCGS2-GMRES(50) against FP32- and BF16-basis GMRES(50)
-    inner solves in FP64 iterative refinement (b ~ N(0,1), seed 1004)."""
+    inner solves in FP64 iterative refinement (b ~ N(0,1), seed 1004); the DCGS2 QR of an
+    m x 50 matrix; the learned preconditioner (config-5 family)."""
     import torch
     from synth import config1_operator
     from synth import config2_operator  # noqa: F401  (same operator as A)
@@ -240,8 +241,45 @@ def solver_suite(kc, ctx, A, m, stream):
             ctx, A, b, x, restart=50, rtol=1e-10, precision=prec, A32=A32, inner_rtol=1e-4,
             inner_max_cycles=3))
     del A32
+    out.update(qr_suite(kc, ctx, m, stream))
     out.update(learned_suite(kc, ctx, timed_solve))
     return out
+
+
+def qr_suite(kc, ctx, m, stream, n=50, reps=3):
+    """DCGS2 QR (Algorithm 2) of an m x n matrix of seeded N(0,1) entries generated on the
+    GPU (torch, seed 2021): columns per second, algorithmic HBM bytes per second and the
+    loss of orthogonality of Q.  Algorithmic bytes per column k < n - 1: reduction
+    8 m k + 16 m (Q_k, w, a_{k+1}), update 8 m k + 32 m (Q_k, w, a_{k+1} read; q_k, w
+    written); the CGS2 finish: 2 (8 m k + 8 m) + 2 (8 m k + 16 m) + 8 m + 16 m at k = n - 1."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(2021)
+    ld = m + (m & 1)
+    A = torch.randn((n, ld), dtype=torch.float64, device="cuda", generator=g)
+    Q = torch.empty_like(A)
+    R = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    kc.dcgs2_qr(ctx, A, Q, R)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(reps):
+        kc.dcgs2_qr(ctx, A, Q, R)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    sec = t0.elapsed_time(t1) / 1e3 / reps
+    byts = sum(16 * m * k + 48 * m for k in range(n - 1))
+    k = n - 1
+    byts += 2 * (8 * m * k + 8 * m) + 2 * (8 * m * k + 16 * m) + 8 * m + 16 * m
+    Qv = Q[:, :m]
+    loo = float(torch.linalg.norm(torch.eye(n, device="cuda", dtype=torch.float64) - Qv @ Qv.T))
+    res = float(torch.linalg.norm(A[:, :m] - R @ Qv) / torch.linalg.norm(A[:, :m]))
+    status = ctx.read_status()
+    del A, Q, R
+    return {"dcgs2_qr_m%d_n%d" % (m, n): {
+        "seconds": sec, "columns_per_s": n / sec, "hbm_gbs": byts / sec / 1e9,
+        "algorithmic_bytes": byts, "loo": loo, "rel_residual_A_minus_QR": res,
+        "device_status": status}}
 
 
 def learned_suite(kc, ctx, timed_solve):

@@ -184,6 +184,17 @@ kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st, void* cuda
 /* CGS2-Arnoldi (Algorithm 3) and MGS-Arnoldi (Section 2, "MGS Level 1"): init sets
  * q_0 = r0/||r0|| (k = 1); each step appends column k-1 of H and q_k.  CGS2 does three
  * reductions per step (two projections + norm), MGS one per inner product. */
+/* DCGS2 QR of a tall-skinny matrix (Algorithm 2, Section 3): A (m x n, column-major, leading
+ * dimension lda) = Q R with Q (m x n, ldq) orthonormal and R (n x n, ldr, upper triangular;
+ * the strictly lower part is set to zero).  One fused reduction per column, the delayed
+ * reorthogonalisation of the previous column inside it, the last column by CGS2 with an
+ * explicit norm; the same kernels and FP64 mode as the Arnoldi step.  Device pointers, FP64;
+ * A and Q 16-byte aligned with even leading dimensions; 1 <= n <= 127.  A is not modified.
+ * Asynchronous on the context stream; a rank-deficient A is reported by kc_read_status as
+ * KC_ERR_BREAKDOWN (alpha_j <= 1e-13 ||R(:, j)||) or KC_ERR_PYTHAGORAS_NEG. */
+kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, double* Q,
+                   int64_t ldq, double* R, int ldr);
+
 kc_status cgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0);
 kc_status cgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 kc_status mgs_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);

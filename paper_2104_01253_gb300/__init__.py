@@ -181,6 +181,15 @@ def kc_spmv(ctx: Context, A: DeviceCSR, x, y):
     ctx.check(ctx.lib.kc_spmv(ctx.handle, C.byref(A.c), _ptr(x), _ptr(y)))
 
 
+def dcgs2_qr(ctx: Context, A, Q, R):
+    """DCGS2 QR (Algorithm 2) of the m x n matrix whose columns are the rows of A
+    (a device tensor of shape (n, lda), FP64); writes Q (shape (n, ldq)) and R (shape
+    (n, ldr): R[j, i] is entry (i, j) of the upper-triangular factor)."""
+    n, m = A.shape
+    ctx.check(ctx.lib.dcgs2_qr(ctx.handle, _ptr(A), A.stride(0), m, n, _ptr(Q), Q.stride(0),
+                               _ptr(R), R.stride(0)))
+
+
 def dcgs2_arnoldi_init(ctx: Context, A: DeviceCSR, st: ArnoldiState, r0):
     ctx.check(ctx.lib.dcgs2_arnoldi_init(ctx.handle, C.byref(A.c), C.byref(st.c), _ptr(r0)))
 

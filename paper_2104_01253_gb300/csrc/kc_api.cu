@@ -296,6 +296,57 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
   return KC_OK;
 }
 
+// DCGS2 QR of given columns (Algorithm 2): the Arnoldi step's kernels with v = a_{k+1}
+// (SF_QR in the scalar step), H pointing one column before R so that H(:, k - 1) is
+// R(:, k), and the CGS2 finish for the last column.
+kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, double* Q,
+                   int64_t ldq, double* R, int ldr) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  if (!A || !Q || !R) return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
+  if (m < 1 || n < 1 || n + 1 > NMAX)
+    return fail(ctx, KC_ERR_INVALID_ARG, "dcgs2_qr: need m >= 1 and 1 <= n <= %d", NMAX - 1);
+  if (lda < m || ldq < m || ldr < n)
+    return fail(ctx, KC_ERR_INVALID_ARG, "dcgs2_qr: leading dimensions too small");
+  if ((lda & 1) || (ldq & 1) || ((uintptr_t)A & 15) || ((uintptr_t)Q & 15))
+    return fail(ctx, KC_ERR_INVALID_ARG,
+                "dcgs2_qr: A, Q must be 16-byte aligned with even leading dimensions");
+  const int64_t ldw = (m + 31) / 32 * 32;
+  const size_t kbytes = (size_t)(n + 1) * n * 8;
+  KC_TRY(ensure_workspace(ctx, (size_t)ldw * 8 + kbytes));
+  double* w = (double*)ctx->ws;
+  double* K = w + ldw;
+  KC_CUDA(ctx, cudaMemsetAsync(K, 0, kbytes, ctx->stream));
+  KC_CUDA(ctx, cudaMemset2DAsync(R, (size_t)ldr * 8, 0, (size_t)n * 8, (size_t)n, ctx->stream));
+  KC_CUDA(ctx, cudaMemcpyAsync(w, A, (size_t)m * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  StepArgs sa = {};
+  sa.H = R + ldr;                      // H(i, j) = R(i, j + 1)
+  sa.ldh = ldr;
+  sa.K = K;
+  sa.ldk = n + 1;
+  sa.flags = SF_QR;
+  if (n == 1) {                        // q_0 = a_0 / ||a_0||, R(0, 0) = ||a_0||
+    KC_TRY(launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_INIT, sa));
+    KC_TRY(launch_scale_to(ctx, w, Q, KC_F64, m, KC_F64));
+    KC_CUDA(ctx, cudaMemcpyAsync(R, &ctx->scal->alpha, 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    return KC_OK;
+  }
+  for (int k = 0; k + 1 < n; k++) {    // step k: q_k and R(:, k); pending a_{k+1}
+    const double* v = A + (int64_t)(k + 1) * lda;
+    sa.k = k;
+    KC_TRY(launch_reduce(ctx, Q, ldq, KC_F64, k, w, v, m, KC_F64, EPI_DCGS2, sa));
+    KC_TRY(launch_dcgs2_update(ctx, Q, ldq, KC_F64, k, w, v, m, KC_F64));
+  }
+  const int k = n - 1;                 // last column: CGS2 with an explicit norm
+  sa.k = k;
+  KC_TRY(launch_reduce(ctx, Q, ldq, KC_F64, k, w, nullptr, m, KC_F64, EPI_STORE_C, sa));
+  KC_TRY(launch_gemv_sub(ctx, Q, ldq, KC_F64, k, w, m, KC_F64, 0));
+  KC_TRY(launch_reduce(ctx, Q, ldq, KC_F64, k, w, nullptr, m, KC_F64, EPI_STORE_C2, sa));
+  KC_TRY(launch_gemv_sub(ctx, Q, ldq, KC_F64, k, w, m, KC_F64, 1));
+  KC_TRY(launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_FINISH, sa));
+  KC_TRY(launch_scale_to(ctx, w, Q + (int64_t)k * ldq, KC_F64, m, KC_F64));
+  return KC_OK;
+}
+
 kc_status cgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0) {
   if (!ctx) return KC_ERR_INVALID_ARG;
   KC_TRY(validate_csr(ctx, A));

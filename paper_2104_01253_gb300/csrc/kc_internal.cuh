@@ -27,6 +27,7 @@ struct Scalars {
   double T[NMAX + 1];   // T_{0:k}: scaled projection (Alg. 4 lines 5-6)
   double C2[NMAX];      // second CGS2 pass coefficients (finish / CGS2 baseline)
   double alpha, inv_alpha, beta, s;
+  double vscale;        // factor of v in the update: 1/alpha (Arnoldi), 1 (QR of given columns)
   double cs;            // C^T S (Stephen's trick)
   double h;             // last MGS inner product
   double norm_sq;       // last explicit squared norm
@@ -71,7 +72,11 @@ struct StepArgs {
   double pyth_tol;      // relative threshold on (beta - C^T C)/beta
 };
 
-enum StepFlags : int { SF_FLEXIBLE = 1, SF_GIVENS = 2, SF_FALLBACK = 4 };
+// SF_QR: DCGS2 QR of given columns (Algorithm 2): v is the next column a_{k+1}, not A w,
+// so T = S, T_k = (s - C^T S) / alpha, the update takes v unscaled, and the pending
+// column is T (no representation correction, as SF_FLEXIBLE); H(k, k-1) is written for
+// k = 0 too (H points one column before R).
+enum StepFlags : int { SF_FLEXIBLE = 1, SF_GIVENS = 2, SF_FALLBACK = 4, SF_QR = 8 };
 
 }  // namespace kc
 

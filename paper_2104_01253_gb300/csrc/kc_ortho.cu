@@ -173,13 +173,15 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
   if (threadIdx.x == 0) {
     sc->alpha = alpha;
     sc->inv_alpha = 1.0 / alpha;
-    sc->T[k] = (sc->s - sc->cs) / (alpha * alpha);
+    const bool qr = (sa.flags & SF_QR) != 0;
+    sc->vscale = qr ? 1.0 : 1.0 / alpha;
+    sc->T[k] = qr ? (sc->s - sc->cs) / alpha : (sc->s - sc->cs) / (alpha * alpha);
     if ((sa.flags & SF_GIVENS) && k == 0) { sc->g[0] = alpha; sc->ncols = 0; }
     if (sa.flags & SF_FLEXIBLE) sc->zscale[k] = 1.0 / alpha;
-    if (k >= 1) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;
+    if (k >= 1 || qr) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;
   }
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    sc->T[i] = sc->S[i] / alpha;
+    sc->T[i] = (sa.flags & SF_QR) ? sc->S[i] : sc->S[i] / alpha;
     sa.H[i + (int64_t)(k - 1) * sa.ldh] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + sc->C[i];
   }
   __syncthreads();
@@ -193,7 +195,7 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
   }
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
     double hc = 0.0;
-    if (!(sa.flags & SF_FLEXIBLE))
+    if (!(sa.flags & (SF_FLEXIBLE | SF_QR)))
       for (int j = 0; j < k; j++) hc += sa.H[i + (int64_t)j * sa.ldh] * sc->C[j];
     sa.K[i + (int64_t)k * sa.ldk] = sc->T[i] - hc / alpha;
   }
@@ -375,6 +377,7 @@ k_dcgs2_update(TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ w,
     sT[i] = (TA)sc->T[i];
   }
   const TA inva = (TA)sc->inv_alpha;
+  const TA vsc = (TA)sc->vscale;
   __syncthreads();
   TQ* qk = Q + (int64_t)k * ldq;
   const int64_t ngroups = m / R;
@@ -385,7 +388,7 @@ k_dcgs2_update(TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ w,
     ldv_cg(v, g, vv);
     TA u[R], wn[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) { u[r] = wv[r]; wn[r] = vv[r] * inva; }
+    for (int r = 0; r < R; r++) { u[r] = wv[r]; wn[r] = vv[r] * vsc; }
     int i = 0;
     for (; i + 4 <= k; i += 4) {
       TA q0[R], q1[R], q2[R], q3[R];
@@ -419,7 +422,7 @@ k_dcgs2_update(TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ w,
   // ragged tail
   if (blockIdx.x == 0) {
     for (int64_t row = ngroups * R + threadIdx.x; row < m; row += blockDim.x) {
-      TA u = (TA)w[row], wn = (TA)v[row] * inva;
+      TA u = (TA)w[row], wn = (TA)v[row] * vsc;
       for (int i = 0; i < k; i++) {
         TA q = (TA)ld1(Q + (int64_t)i * ldq, row);
         u -= q * sC[i];
@@ -708,7 +711,7 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
   }
   __syncthreads();
   const bool cok = s_cok;
-  const double inva = sc->inv_alpha, scale = s_scale;
+  const double inva = sc->inv_alpha, vsc = sc->vscale, scale = s_scale;
   double* qk = Q + (int64_t)k * ldq;
   const int64_t ngroups = m / 2;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
@@ -716,7 +719,7 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
     double wv[2], vv[2];
     ldv_cg(w, g, wv);
     ldv_cg(v, g, vv);
-    double wn[2] = {vv[0] * inva, vv[1] * inva};
+    double wn[2] = {vv[0] * vsc, vv[1] * vsc};
     double u64[2] = {wv[0], wv[1]};
     float zh[2] = {0.0f, 0.0f}, zl[2] = {0.0f, 0.0f};
     int i = 0;
@@ -786,7 +789,7 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
   }
   if (blockIdx.x == 0) {        // ragged tail: FP64
     for (int64_t row = ngroups * 2 + threadIdx.x; row < m; row += blockDim.x) {
-      double u = w[row], wn1 = v[row] * inva;
+      double u = w[row], wn1 = v[row] * vsc;
       for (int i = 0; i < k; i++) {
         const double q = __ldcg(Q + (int64_t)i * ldq + row);
         u = fma(-q, sC[i], u);
@@ -917,6 +920,7 @@ k_norm(const TV* __restrict__ x, const TV* __restrict__ y, int64_t m,
   double alpha = sqrt(xx);
   sc->alpha = alpha;
   sc->inv_alpha = 1.0 / alpha;
+  sc->vscale = 1.0 / alpha;
   if (nepi == NEPI_INIT) {
     if (!(alpha > 0.0)) set_status(sc, KC_ERR_BREAKDOWN);
     return;

@@ -120,7 +120,7 @@ k_update_staged(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__
     return;
   }
   // ---- consumers ----
-  const double inva = sc->inv_alpha;
+  const double inva = sc->inv_alpha, vsc = sc->vscale;
   const double scale = OFF ? s_scale : 1.0;
   const bool cok = OFF ? (s_cok != 0) : false;
   const int warp = tid >> 5, lane = tid & 31;
@@ -147,7 +147,7 @@ k_update_staged(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__
           const double2 wv = *reinterpret_cast<const double2*>(st + ST_CH * ST_TR + lr);
           const double2 vv = *reinterpret_cast<const double2*>(st + (ST_CH + 1) * ST_TR + lr);
           u64[0] = wv.x; u64[1] = wv.y;
-          wn[0] = vv.x * inva; wn[1] = vv.y * inva;
+          wn[0] = vv.x * vsc; wn[1] = vv.y * vsc;
         }
         const int c0 = c * ST_CH;
         const int ncol = k - c0 < ST_CH ? (k - c0 > 0 ? k - c0 : 0) : ST_CH;
@@ -190,7 +190,7 @@ k_update_staged(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__
       *reinterpret_cast<double2*>(w + r0 + lr) = make_double2(wo[0], wo[1]);
     } else if ((rows & 1) && lr == (rows & ~1)) {     // the odd last row of the last tile
       const int64_t row = r0 + lr;
-      double u = __ldcg(w + row), wn1 = __ldcg(v + row) * inva;
+      double u = __ldcg(w + row), wn1 = __ldcg(v + row) * vsc;
       for (int i = 0; i < k; i++) {
         const double q = __ldcg(Q + (int64_t)i * ldq + row);
         u = fma(-q, sC[i], u);
