@@ -95,12 +95,6 @@ static StepArgs step_args(const kc_arnoldi* st, int k, int flags) {
   return sa;
 }
 
-#define KC_TRY(x)                 \
-  do {                            \
-    kc_status s_ = (x);           \
-    if (s_ != KC_OK) return s_;   \
-  } while (0)
-
 extern "C" {
 
 kc_status kc_create(kc_ctx** out, int device, void* cuda_stream) {

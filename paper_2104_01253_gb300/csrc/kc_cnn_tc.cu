@@ -293,13 +293,8 @@ k_cnn_conv32_tc(const __grid_constant__ CUtensorMap tin, bf16* __restrict__ out,
 
 kc_status cnn_conv32_tc(kc_ctx* ctx, const bf16* in, bf16* out, const bf16* w, int B, int H,
                         int W, int epi, const bf16* mask) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_cnn_conv32_tc,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM);
-    if (e != cudaSuccess) return fail(ctx, KC_ERR_CUDA, "conv: %s", cudaGetErrorString(e));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  KC_TRY(smem_attr_once(ctx, attr_done, k_cnn_conv32_tc, TP_SMEM, "conv"));
   EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return fail(ctx, KC_ERR_CUDA, "conv: no tensor map encoder");
   CUtensorMap tin;

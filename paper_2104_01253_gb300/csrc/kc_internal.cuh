@@ -1,6 +1,8 @@
 // Internal declarations shared by the libkrylov translation units (not part of the ABI).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -138,6 +140,26 @@ inline kc_status fail(kc_ctx* ctx, kc_status st, const char* fmt, ...) {
 // Timing bracket around one launch (no-op unless kc_timing_enable was called).
 void timing_begin(kc_ctx* ctx, int kid);
 void timing_end(kc_ctx* ctx);
+
+// Raise a kernel's dynamic shared-memory limit on the context's device, once per device
+// (the attribute is per device; `done` holds one bit per device id).
+template <typename Kernel>
+inline kc_status smem_attr_once(kc_ctx* ctx, std::atomic<unsigned long long>& done,
+                                Kernel kernel, int bytes, const char* what) {
+  const unsigned long long bit = 1ull << (ctx->device & 63);
+  if (done.load(std::memory_order_acquire) & bit) return KC_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return fail(ctx, KC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  done.fetch_or(bit, std::memory_order_release);
+  return KC_OK;
+}
+
+// return the status of a kc_status-valued call if it is not KC_OK
+#define KC_TRY(x)                 \
+  do {                            \
+    kc_status s_ = (x);           \
+    if (s_ != KC_OK) return s_;   \
+  } while (0)
 
 #define KC_LAUNCHED(ctx)                                                               \
   do {                                                                                 \

@@ -267,13 +267,8 @@ template <bool OFF, int MAXCH>
 static kc_status launch_tma_inst(kc_ctx* ctx, int grid, const CUtensorMap& tq,
                                  const CUtensorMap& tx, const CUtensorMap& ty, int k, int64_t m,
                                  const StepArgs& sa) {
-  static bool attr_set = false;       // once per instantiation (dynamic shared memory > 48 KB)
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_reduce_tma<OFF, MAXCH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM);
-    if (e != cudaSuccess) return fail(ctx, KC_ERR_CUDA, "reduce: %s", cudaGetErrorString(e));
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0};   // per instantiation and device
+  KC_TRY(smem_attr_once(ctx, attr_done, k_reduce_tma<OFF, MAXCH>, (int)RT_SMEM, "reduce"));
   k_reduce_tma<OFF, MAXCH><<<grid, RT_THREADS, RT_SMEM, ctx->stream>>>(
       tq, tx, ty, k, m, ctx->partials, ctx->counters, ctx->scal, sa);
   return KC_OK;

@@ -206,16 +206,10 @@ k_update_staged(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__
 
 kc_status launch_update_staged(kc_ctx* ctx, double* Q, int64_t ldq, int k, double* w,
                                const double* v, int64_t m) {
-  static bool attr_set[2] = {false, false};
+  static std::atomic<unsigned long long> attr_done[2];
   const int off = ctx->fp64_mode == 1 ? 1 : 0;
-  if (!attr_set[off]) {
-    cudaError_t e = off ? cudaFuncSetAttribute(k_update_staged<true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ST_SMEM)
-                        : cudaFuncSetAttribute(k_update_staged<false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ST_SMEM);
-    if (e != cudaSuccess) return fail(ctx, KC_ERR_CUDA, "staged update: %s", cudaGetErrorString(e));
-    attr_set[off] = true;
-  }
+  if (off) KC_TRY(smem_attr_once(ctx, attr_done[1], k_update_staged<true>, (int)ST_SMEM, "staged update"));
+  else KC_TRY(smem_attr_once(ctx, attr_done[0], k_update_staged<false>, (int)ST_SMEM, "staged update"));
   const int64_t ntiles = (m + ST_TR - 1) / ST_TR;
   const int grid = (int)(ntiles < ctx->num_sms ? ntiles : ctx->num_sms);
   timing_begin(ctx, KID_UPDATE);
