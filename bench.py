@@ -294,17 +294,27 @@ def learned_suite(kc, ctx, timed_solve):
     out = {}
     for N, nops, cycles, batch, cap in ((256, 12, 20, 4, 40000), (1024, 16, 10, 2, 20000)):
         t0 = time.time()
-        ops, X, R, owner = tr.generate_pairs(ctx, N, range(nops), restart=40, max_cycles=cycles)
+        host_ops = [tr.varcoef_operator(N, seed) for seed in range(nops)]    # synthetic inputs
+        setup_s = time.time() - t0
+        t0 = time.time()
+        ops, X, R, owner = tr.generate_pairs(ctx, N, range(nops), restart=40, max_cycles=cycles,
+                                             host_ops=host_ops)
         npairs = int(X.shape[0])
+        torch.cuda.synchronize()
+        pairs_s = time.time() - t0
+        t0 = time.time()
         w, hist = tr.train(ctx, ops, X, R, owner, steps=600, batch=batch, lr=2e-3, seed=0)
         torch.cuda.synchronize()
         train_s = time.time() - t0
+        del host_ops
         del X, R, ops
         Ah = tr.varcoef_operator(N, 64)
         A = kc.DeviceCSR(Ah)
         b = torch.as_tensor(gaussian_vector(Ah.m, 2064), device="cuda")
         res = {"grid": "%d^2" % N, "training": {"operators": nops, "pairs": npairs,
                                                 "adam_steps": 600, "batch": batch,
+                                                "host_operator_setup_seconds": setup_s,
+                                                "pair_generation_seconds": pairs_s,
                                                 "seconds": train_s,
                                                 "loss_first": float(np.mean(hist[:20])),
                                                 "loss_last": float(np.mean(hist[-50:]))}}

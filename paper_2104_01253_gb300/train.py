@@ -49,8 +49,9 @@ def he_init(seed: int) -> np.ndarray:
 
 
 def generate_pairs(ctx: Context, N: int, seeds, restart: int = 40, max_cycles: int = 20,
-                   rhs_seed_offset: int = 1000):
-    """Restart residuals of plain GMRES solves on the seeded operators.
+                   rhs_seed_offset: int = 1000, host_ops=None):
+    """Restart residuals of plain GMRES solves on the seeded operators (host_ops: the host
+    CSR operators of `seeds`, if already built).
 
     Returns (ops, X, R, owner): the device operators, the network inputs
     X = D^{-1} r / s and residuals R = r / s (float32, (n, 1, N, N), host), and the index
@@ -58,7 +59,7 @@ def generate_pairs(ctx: Context, N: int, seeds, restart: int = 40, max_cycles: i
     from synth import gaussian_vector
     ops, X, R, owner = [], [], [], []
     for oi, seed in enumerate(seeds):
-        Ah = varcoef_operator(N, seed)
+        Ah = host_ops[oi] if host_ops is not None else varcoef_operator(N, seed)
         A = DeviceCSR(Ah)
         ops.append(A)
         dinv = torch.as_tensor(inverse_diagonal(Ah), device="cuda")
