@@ -36,7 +36,9 @@ constexpr int TP_STAGE = 4 * TP_PLANE;
 constexpr int TP_BOX_BYTES = 4 * TC_HH * TC_HW * 16;      // 11520 bytes copied per stage
 constexpr int TP_NS = 4;                                  // ring stages
 constexpr int TC_WREGION = 20480;                         // weights (18432 B), 128-aligned
-constexpr int TP_SMEM = 128 + TC_WREGION + TP_NS * TP_STAGE;
+constexpr int TP_OUT = 4 * 32 * 64;                       // epilogue staging: 4 warps x 32 pixels
+static_assert(TC_TW == 8 && TC_TH * TC_TW == 4 * 32, "each epilogue warp owns four 8-pixel tile rows");
+constexpr int TP_SMEM = 128 + TC_WREGION + TP_NS * TP_STAGE + TP_OUT;
 constexpr int TP_THREADS = 192;
 constexpr int TP_TMEM_COLS = 64;                          // two 32-column accumulators
 constexpr int TC_CTAS_PER_SM = 2;
@@ -126,6 +128,7 @@ k_cnn_conv32_tc(const __grid_constant__ CUtensorMap tin, bf16* __restrict__ out,
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
   unsigned char* sW = base;
   unsigned char* sStage = base + TC_WREGION;
+  unsigned char* sOut = base + TC_WREGION + TP_NS * TP_STAGE;
   __shared__ unsigned long long full[TP_NS], empty[TP_NS], tfull[2], tempty[2];
   __shared__ unsigned int tmem_sh;
   __shared__ int s_err;
@@ -252,33 +255,44 @@ k_cnn_conv32_tc(const __grid_constant__ CUtensorMap tin, bf16* __restrict__ out,
       const int y0 = (rem / tiles_x) * TC_TH, x0 = (rem % tiles_x) * TC_TW;
       const int m = q * 32 + lane;
       const int gy = y0 + m / TC_TW, gx = x0 + m % TC_TW;
-      if (gy < H && gx < W) {
+      // this warp's 32 pixels = tile rows 4q .. 4q + 3; stage them in shared memory (16-byte
+      // chunks swizzled by pixel, conflict-free) and write whole 512-byte rows
+      unsigned char* so = sOut + q * 32 * 64;
+      if (epi == 0) {
+#pragma unroll
+        for (int c = 0; c < 32; c++) v[c] = fmaxf(v[c], 0.0f);
+      } else if (gy < H && gx < W) {
         const size_t p = (((size_t)b * H + gy) * W + gx) * 32;
-        if (epi == 0) {
-#pragma unroll
-          for (int c = 0; c < 32; c++) v[c] = fmaxf(v[c], 0.0f);
-        } else {
-#pragma unroll
-          for (int qq = 0; qq < 4; qq++) {
-            const uint4 mk = *reinterpret_cast<const uint4*>(mask + p + qq * 8);
-            const unsigned int mw[4] = {mk.x, mk.y, mk.z, mk.w};
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-              if (!(__uint_as_float(mw[t] << 16) > 0.0f)) v[qq * 8 + 2 * t] = 0.0f;
-              if (!(__uint_as_float(mw[t] & 0xffff0000u) > 0.0f)) v[qq * 8 + 2 * t + 1] = 0.0f;
-            }
-          }
-        }
 #pragma unroll
         for (int qq = 0; qq < 4; qq++) {
-          uint4 o;
-          o.x = tc_bfbits(v[qq * 8 + 0]) | (tc_bfbits(v[qq * 8 + 1]) << 16);
-          o.y = tc_bfbits(v[qq * 8 + 2]) | (tc_bfbits(v[qq * 8 + 3]) << 16);
-          o.z = tc_bfbits(v[qq * 8 + 4]) | (tc_bfbits(v[qq * 8 + 5]) << 16);
-          o.w = tc_bfbits(v[qq * 8 + 6]) | (tc_bfbits(v[qq * 8 + 7]) << 16);
-          *reinterpret_cast<uint4*>(out + p + qq * 8) = o;
+          const uint4 mk = *reinterpret_cast<const uint4*>(mask + p + qq * 8);
+          const unsigned int mw[4] = {mk.x, mk.y, mk.z, mk.w};
+#pragma unroll
+          for (int t = 0; t < 4; t++) {
+            if (!(__uint_as_float(mw[t] << 16) > 0.0f)) v[qq * 8 + 2 * t] = 0.0f;
+            if (!(__uint_as_float(mw[t] & 0xffff0000u) > 0.0f)) v[qq * 8 + 2 * t + 1] = 0.0f;
+          }
         }
       }
+#pragma unroll
+      for (int qq = 0; qq < 4; qq++) {
+        uint4 o;
+        o.x = tc_bfbits(v[qq * 8 + 0]) | (tc_bfbits(v[qq * 8 + 1]) << 16);
+        o.y = tc_bfbits(v[qq * 8 + 2]) | (tc_bfbits(v[qq * 8 + 3]) << 16);
+        o.z = tc_bfbits(v[qq * 8 + 4]) | (tc_bfbits(v[qq * 8 + 5]) << 16);
+        o.w = tc_bfbits(v[qq * 8 + 6]) | (tc_bfbits(v[qq * 8 + 7]) << 16);
+        *reinterpret_cast<uint4*>(so + lane * 64 + ((qq ^ ((lane >> 1) & 3)) * 16)) = o;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int row = 0; row < 4; row++) {
+        const int pix = row * 8 + (lane >> 2), qq = lane & 3;
+        const int ry = y0 + 4 * q + row, rx = x0 + (lane >> 2);
+        const uint4 o = *reinterpret_cast<const uint4*>(so + pix * 64 + ((qq ^ ((pix >> 1) & 3)) * 16));
+        if (ry < H && rx < W)
+          *reinterpret_cast<uint4*>(out + (((size_t)b * H + ry) * W + rx) * 32 + qq * 8) = o;
+      }
+      __syncwarp();
       bb ^= 1;
       if (bb == 0) tph ^= 1u;
     }
