@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import config2_operator, convdiff_csr, gaussian_vector  # noqa: E402
+from synth import config2_operator, config2_stencil, convdiff_csr, gaussian_vector  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-baselines", action="store_true")
+    p.add_argument("--no-stencil", action="store_true",
+                   help="skip the matrix-free stencil expansions and solves")
     p.add_argument("--no-solvers", action="store_true",
                    help="skip the GMRES time-to-1e-10 runs (plain FP64 vs FP32/BF16 IR)")
     p.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1])
@@ -401,11 +403,14 @@ def main():
     r0 = torch.as_tensor(r0_host, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def expansion(src):
-        kc.dcgs2_arnoldi_init(ctx, A, st, src)
+    def expansion_on(op, src):
+        kc.dcgs2_arnoldi_init(ctx, op, st, src)
         for _ in range(n):
-            kc.dcgs2_arnoldi_step(ctx, A, st)
-        kc.dcgs2_arnoldi_finish(ctx, A, st)
+            kc.dcgs2_arnoldi_step(ctx, op, st)
+        kc.dcgs2_arnoldi_finish(ctx, op, st)
+
+    def expansion(src):
+        expansion_on(A, src)
 
     for _ in range(args.warmup):
         expansion(r0)
@@ -512,6 +517,54 @@ def main():
         baselines["note"] = ("same m, n and GPU; CGS2 = Algorithm 3 (3 reductions/step), "
                              "MGS level 1 (one reduction per inner product)")
 
+    # the same expansions on the matrix-free stencil form of the operator (same matrix, bit
+    # for bit): the basis generation reads w and writes v (16 bytes a row) instead of the
+    # CSR arrays; 7 FP64 FMAs a row keep the stencil kernel on the FP64 pipe
+    matrix_free = None
+    if not args.no_stencil:
+        As = kc.DeviceStencil7(config2_stencil(args.N))
+        reps = max(args.steps, 2)
+        expansion_on(As, r0)
+        torch.cuda.synchronize()
+        ctx.timing_enable(True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            expansion_on(As, r0)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ks = ctx.timing_read()
+        ctx.timing_enable(False)
+        ms_sp, cnt_sp = ks.get("spmv", (0.0, 0))
+        per_launch = ms_sp / max(cnt_sp, 1)
+        gbs_sp = 16 * m / (per_launch / 1e3) / 1e9
+        tf_sp = 14 * m / (per_launch / 1e3) / 1e12
+        matrix_free = {
+            "operator": "7-point stencil %d^3, coefficients of the CSR matrix (no matrix in "
+                        "HBM)" % args.N,
+            "dcgs2_steps_per_s": n * reps / (t0.elapsed_time(t1) / 1e3),
+            "stencil_kernel": {"avg_launch_ms": per_launch, "launches": cnt_sp,
+                               "hbm_gbs": gbs_sp, "hbm_frac": gbs_sp / hbm_peak,
+                               "fp64_tflops": tf_sp, "fp64_frac": tf_sp / FP64_PEAK_TFLOPS,
+                               "algorithmic_bytes_per_launch": 16 * m,
+                               "fp64_flop_per_launch": 14 * m},
+            "csr_spmv_avg_launch_ms": kern["spmv"][0] / max(kern["spmv"][1], 1),
+        }
+        if not args.no_solvers:
+            b4 = torch.as_tensor(gaussian_vector(m, 1004), device="cuda")
+            As32 = kc.DeviceStencil7(config2_stencil(args.N), dtype=torch.float32)
+            for name, prec in (("config4_fp64_gmres50", 0), ("config4_ir_fp32_gmres50", 1)):
+                x4 = torch.zeros_like(b4)
+                t0.record(stream)
+                info = kc.gmres_solve(ctx, As, b4, x4, restart=50, rtol=1e-10, precision=prec,
+                                      A32=As32, inner_rtol=1e-4, inner_max_cycles=3)
+                t1.record(stream)
+                torch.cuda.synchronize()
+                info["seconds"] = t0.elapsed_time(t1) / 1e3
+                matrix_free[name] = info
+            del b4, x4
+
     # end to end through the C ABI with host buffers: H2D of r0, expansion, D2H of H
     e2e = None
     if not args.no_e2e:
@@ -564,7 +617,7 @@ def main():
             "fp64_mode": ["all-fp64", "fp64-with-float-float-offload"][ctx.fp64_mode],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "same_gpu_baselines": baselines,
             "gpu_launches": launches, "clocks": clocks,
-            "gmres_time_to_1e-10": solvers,
+            "gmres_time_to_1e-10": solvers, "matrix_free": matrix_free,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -46,9 +46,27 @@ typedef enum { KC_F64 = 0, KC_F32 = 1, KC_BF16 = 2 } kc_dtype;
 
 typedef struct kc_ctx kc_ctx;
 
-/* CSR matrix, m x m, int32 indices (nnz < 2^31), caller-owned device arrays.
- * row_ptr[m+1] non-decreasing with row_ptr[0] = 0, col_idx[nnz] in [0, m),
- * val[nnz] of type val_dtype (KC_F64 or KC_F32). */
+/* The operator A (m x m), in one of two forms chosen by grid[0]:
+ *
+ *  - CSR matrix (grid[0] == 0; a zero-initialised struct is a CSR): int32 indices
+ *    (nnz < 2^31), caller-owned device arrays.  row_ptr[m+1] non-decreasing with
+ *    row_ptr[0] = 0, col_idx[nnz] in [0, m), val[nnz] of type val_dtype (KC_F64 or KC_F32).
+ *
+ *  - Matrix-free 7-point stencil (grid[0] > 0; row_ptr, col_idx, val and nnz are ignored):
+ *    on an nx x ny x nz grid, grid = {nx, ny, nz}, m = nx ny nz, row i = ix + nx (iy + ny iz)
+ *    (x fastest), with zero (homogeneous Dirichlet) values outside the grid:
+ *      (A x)_i = c0 x_i + c1 x_{i-1} + c2 x_{i+1} + c3 x_{i-nx} + c4 x_{i+nx}
+ *              + c5 x_{i-nx ny} + c6 x_{i+nx ny},   stencil = {c0, ..., c6},
+ *    each neighbour term present only when that neighbour lies in the grid.  This is the
+ *    constant-coefficient form of the h^2-scaled upwind convection-diffusion operators
+ *    (2D with nz = 1) and of the Manteuffel matrix of Section 5.1; with it the basis
+ *    generation v = A w of Algorithm 4 reads w once and writes v once instead of streaming
+ *    the matrix.  val_dtype KC_F64: FP64 vectors, seven FP64 FMAs per row in both FP64
+ *    modes (an error in v, unlike one in S or Q C, is not removed by the next
+ *    reorthogonalisation: it enters A Q = Q H); KC_F32: FP32 vectors, coefficients rounded
+ *    to FP32.  Accepted wherever a kc_csr is, except by the entry points that read the
+ *    matrix entries themselves (fgmres_solve, kc_cnn_train_step_residual,
+ *    dcgs2_arnoldi_step_noalloc), which return KC_ERR_INVALID_ARG for a stencil. */
 typedef struct {
   int64_t m;
   int64_t nnz;
@@ -56,6 +74,8 @@ typedef struct {
   const int32_t* col_idx;
   const void* val;
   int32_t val_dtype;
+  int32_t grid[3];
+  double stencil[7];
 } kc_csr;
 
 /* Arnoldi state (caller-owned device buffers).
@@ -134,7 +154,8 @@ kc_status kc_last_scalars(kc_ctx* ctx, double* alpha, double* beta, double* s);
 
 /* ---- building blocks ---------------------------------------------------------------- */
 
-/* y = A x (K4': CSR SpMV).  x, y: m-vectors of the matrix value type (FP64 or FP32). */
+/* y = A x (K4': CSR SpMV, or the matrix-free stencil).  x, y: m-vectors of the matrix
+ * value type (FP64 or FP32); x and y must not overlap. */
 kc_status kc_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y);
 
 /* ---- DCGS2-Arnoldi (Algorithm 4) ----------------------------------------------------- */
@@ -181,9 +202,6 @@ kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st, void* cuda
 
 /* ---- baselines ---------------------------------------------------------------------- */
 
-/* CGS2-Arnoldi (Algorithm 3) and MGS-Arnoldi (Section 2, "MGS Level 1"): init sets
- * q_0 = r0/||r0|| (k = 1); each step appends column k-1 of H and q_k.  CGS2 does three
- * reductions per step (two projections + norm), MGS one per inner product. */
 /* DCGS2 QR of a tall-skinny matrix (Algorithm 2, Section 3): A (m x n, column-major, leading
  * dimension lda) = Q R with Q (m x n, ldq) orthonormal and R (n x n, ldr, upper triangular;
  * the strictly lower part is set to zero).  One fused reduction per column, the delayed
@@ -195,6 +213,9 @@ kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st, void* cuda
 kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, double* Q,
                    int64_t ldq, double* R, int ldr);
 
+/* CGS2-Arnoldi (Algorithm 3) and MGS-Arnoldi (Section 2, "MGS Level 1"): init sets
+ * q_0 = r0/||r0|| (k = 1); each step appends column k-1 of H and q_k.  CGS2 does three
+ * reductions per step (two projections + norm), MGS one per inner product. */
 kc_status cgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0);
 kc_status cgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 kc_status mgs_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);

@@ -13,6 +13,8 @@ Modules
                 inside FP64 iterative refinement
   krylov_schur  Krylov-Schur eigenvalues (Stewart) on DCGS2-Arnoldi, Arnoldi residual test
   cnn           the 6-layer 3x3 convolutional preconditioner, forward and backward in FP64
+  stencil       the matrix-free 7-point stencil operator (padded shifts; Kronecker assembly)
+  partitioned   DCGS2-Arnoldi on row blocks of simulated ranks (one all-reduce per step)
 
 Parity status per function is listed in each module header; the learned preconditioner's
 benefit (an empirical quantity) is the one "parity unpinned" item.

@@ -15,8 +15,8 @@ from . import _lib
 from ._lib import (KC_BF16, KC_F32, KC_F64, KrylovError, kc_arnoldi, kc_csr, kc_gmres_info,
                    kc_gmres_opts, kc_ks_opts)
 
-__all__ = ["Context", "DeviceCSR", "ArnoldiState", "kc_spmv", "dcgs2_arnoldi_init",
-           "dcgs2_arnoldi_step", "dcgs2_arnoldi_finish", "cgs2_arnoldi_init",
+__all__ = ["Context", "DeviceCSR", "DeviceStencil7", "ArnoldiState", "kc_spmv",
+           "dcgs2_arnoldi_init", "dcgs2_arnoldi_step", "dcgs2_arnoldi_finish", "cgs2_arnoldi_init",
            "cgs2_arnoldi_step", "mgs_arnoldi_step", "gmres_solve", "krylov_schur_eigs",
            "KrylovError", "KC_F64", "KC_F32", "KC_BF16"]
 
@@ -132,6 +132,26 @@ class DeviceCSR:
     def nbytes(self):
         return (self.row_ptr.numel() * 4 + self.col_idx.numel() * 4 +
                 self.val.numel() * self.val.element_size())
+
+
+class DeviceStencil7:
+    """Matrix-free 7-point stencil operator (the kc_csr form with grid[0] > 0): nothing is
+    stored on the GPU.  ``stencil`` has ``grid`` = (nx, ny, nz) and ``c`` = (centre, x-1,
+    x+1, y-1, y+1, z-1, z+1), e.g. ``synth.config2_stencil()``; dtype selects FP64 or FP32
+    vectors (FP32 rounds the coefficients)."""
+
+    def __init__(self, stencil, dtype=torch.float64):
+        nx, ny, nz = (int(g) for g in stencil.grid)
+        self.m = nx * ny * nz
+        self.grid = (nx, ny, nz)
+        self.coef = tuple(float(v) for v in stencil.c)
+        self.nnz = int(getattr(stencil, "nnz", 0))
+        self.val_dtype = KC_F64 if dtype == torch.float64 else KC_F32
+        self.c = kc_csr(self.m, self.nnz, None, None, None, self.val_dtype,
+                        (C.c_int32 * 3)(nx, ny, nz), (C.c_double * 7)(*self.coef))
+
+    def nbytes(self):
+        return 0
 
 
 class ArnoldiState:

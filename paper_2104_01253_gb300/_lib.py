@@ -22,7 +22,8 @@ KC_F64, KC_F32, KC_BF16 = 0, 1, 2
 
 class kc_csr(C.Structure):
     _fields_ = [("m", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
-                ("col_idx", C.c_void_p), ("val", C.c_void_p), ("val_dtype", C.c_int32)]
+                ("col_idx", C.c_void_p), ("val", C.c_void_p), ("val_dtype", C.c_int32),
+                ("grid", C.c_int32 * 3), ("stencil", C.c_double * 7)]
 
 
 class kc_arnoldi(C.Structure):

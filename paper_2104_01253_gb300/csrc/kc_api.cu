@@ -12,12 +12,26 @@ kc_status validate_csr(kc_ctx* ctx, const kc_csr* A) {
   if (!A) return fail(ctx, KC_ERR_INVALID_ARG, "A is NULL");
   if (A->m <= 0 || A->m >= (int64_t)1 << 31)
     return fail(ctx, KC_ERR_INVALID_ARG, "matrix size m = %lld out of range", (long long)A->m);
+  if (A->val_dtype != KC_F64 && A->val_dtype != KC_F32)
+    return fail(ctx, KC_ERR_INVALID_ARG, "matrix values must be KC_F64 or KC_F32");
+  if (A->grid[0] != 0) {
+    if (A->grid[0] < 0 || A->grid[1] <= 0 || A->grid[2] <= 0 ||
+        (int64_t)A->grid[0] * A->grid[1] * A->grid[2] != A->m)
+      return fail(ctx, KC_ERR_INVALID_ARG, "stencil grid %d x %d x %d does not have m = %lld points",
+                  A->grid[0], A->grid[1], A->grid[2], (long long)A->m);
+    return KC_OK;
+  }
   if (A->nnz < 0 || A->nnz >= (int64_t)1 << 31)
     return fail(ctx, KC_ERR_INVALID_ARG, "nnz = %lld does not fit int32 indices", (long long)A->nnz);
   if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val)))
     return fail(ctx, KC_ERR_INVALID_ARG, "CSR arrays must be non-NULL device pointers");
-  if (A->val_dtype != KC_F64 && A->val_dtype != KC_F32)
-    return fail(ctx, KC_ERR_INVALID_ARG, "CSR values must be KC_F64 or KC_F32");
+  return KC_OK;
+}
+
+kc_status validate_csr_entries(kc_ctx* ctx, const kc_csr* A) {
+  KC_TRY(validate_csr(ctx, A));
+  if (is_stencil(A))
+    return fail(ctx, KC_ERR_INVALID_ARG, "this entry point reads matrix entries: A must be CSR");
   return KC_OK;
 }
 

@@ -215,7 +215,7 @@ static kc_status train_step(kc_ctx* ctx, float* w32, float* adam_m, float* adam_
   if (s != KC_OK) return s;
   const int64_t npix = (int64_t)H * W;
   if (A) {
-    if ((s = validate_csr(ctx, A)) != KC_OK) return s;
+    if ((s = validate_csr_entries(ctx, A)) != KC_OK) return s;
     if (A->val_dtype != KC_F64) return fail(ctx, KC_ERR_INVALID_ARG, "A must have FP64 values");
     if (A->m != npix)
       return fail(ctx, KC_ERR_INVALID_ARG, "grid %d x %d does not match m = %lld", H, W,
@@ -270,7 +270,7 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
                        const double* b, double* x, const kc_gmres_opts* opts,
                        kc_gmres_info* info) {
   if (!ctx) return KC_ERR_INVALID_ARG;
-  kc_status s = validate_csr(ctx, A);
+  kc_status s = validate_csr_entries(ctx, A);
   if (s != KC_OK) return s;
   if (!b || !x || !opts || !info) return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
   if (A->val_dtype != KC_F64) return fail(ctx, KC_ERR_INVALID_ARG, "A must have FP64 values");

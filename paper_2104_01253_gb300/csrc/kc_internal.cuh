@@ -208,7 +208,11 @@ kc_status cnn_residual_loss_grad(kc_ctx* ctx, const kc_csr* A, const float* x, c
 kc_status cnn_adam(kc_ctx* ctx, float* w, const float* g, float* m, float* v, int64_t t,
                    float lr, float b1, float b2, float eps);
 int64_t cnn_nparam();
+// the operator is the matrix-free 7-point stencil rather than a CSR matrix
+inline bool is_stencil(const kc_csr* A) { return A->grid[0] > 0; }
 kc_status validate_csr(kc_ctx* ctx, const kc_csr* A);
+// validate_csr, and A must be a CSR matrix (for callers that read its entries)
+kc_status validate_csr_entries(kc_ctx* ctx, const kc_csr* A);
 kc_status validate_state(kc_ctx* ctx, const kc_csr* A, const kc_arnoldi* st);
 
 }  // namespace kc

@@ -222,6 +222,40 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rp,
   }
 }
 
+// ----------------------------------------------------------------------------------------
+// K4'': the matrix-free 7-point stencil, one thread per row.  The terms are summed in
+// increasing column order (z-, y-, x-, centre, x+, y+, z+), the order of a CSR row, so on
+// the same coefficients the result is bitwise that of k_spmv.  The x-neighbours come from
+// the warp's own lines (L1), the y- and z-neighbours from L2 (one plane is nx ny elements).
+// ----------------------------------------------------------------------------------------
+template <typename T>
+struct Stencil7 {
+  T c[7];       // centre, x-1, x+1, y-1, y+1, z-1, z+1
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __restrict__ y,
+                                                  int nx, int ny, int nz, Stencil7<T> c,
+                                                  const Scalars* __restrict__ sc) {
+  if (sc->stop) return;
+  const int64_t m = (int64_t)nx * ny * nz, pl = (int64_t)nx * ny;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = r / nx;
+    const int ix = (int)(r - t * nx);
+    const int iy = (int)(t % ny), iz = (int)(t / ny);
+    T s = 0;
+    if (iz > 0) s += c.c[5] * __ldcg(x + r - pl);
+    if (iy > 0) s += c.c[3] * __ldcg(x + r - nx);
+    if (ix > 0) s += c.c[1] * __ldcg(x + r - 1);
+    s += c.c[0] * __ldcg(x + r);
+    if (ix < nx - 1) s += c.c[2] * __ldcg(x + r + 1);
+    if (iy < ny - 1) s += c.c[4] * __ldcg(x + r + nx);
+    if (iz < nz - 1) s += c.c[6] * __ldcg(x + r + pl);
+    y[r] = s;
+  }
+}
+
 // Last CTA of a reduction: deterministic sum of the per-CTA partials, then either a plain
 // store of Q^T x or the scalar step of Algorithm 4 (lines 4-6, 10-12).
 __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int NRHS,
@@ -1005,7 +1039,20 @@ kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int 
     return fail(ctx, KC_ERR_INVALID_ARG, "spmv: matrix value type %d does not match vector type %d",
                 A->val_dtype, vec_dtype);
   timing_begin(ctx, KID_SPMV);
-  if (A->val_dtype == KC_F64 && vec_dtype == KC_F64)
+  if (is_stencil(A)) {
+    const int nx = A->grid[0], ny = A->grid[1], nz = A->grid[2];
+    if (vec_dtype == KC_F64) {
+      Stencil7<double> c;
+      for (int i = 0; i < 7; i++) c.c[i] = A->stencil[i];
+      k_stencil7<double><<<grid, 256, 0, ctx->stream>>>((const double*)x, (double*)y, nx, ny,
+                                                        nz, c, ctx->scal);
+    } else {
+      Stencil7<float> c;
+      for (int i = 0; i < 7; i++) c.c[i] = (float)A->stencil[i];
+      k_stencil7<float><<<grid, 256, 0, ctx->stream>>>((const float*)x, (float*)y, nx, ny, nz,
+                                                       c, ctx->scal);
+    }
+  } else if (A->val_dtype == KC_F64 && vec_dtype == KC_F64)
     k_spmv<double, double><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
         (const double*)A->val, (const double*)x, (double*)y, A->m, ctx->scal);
   else if (A->val_dtype == KC_F32 && vec_dtype == KC_F32)
@@ -1244,7 +1291,7 @@ static kc_status noalloc_setup(NoAllocScratch** out) {
 extern "C" kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st,
                                                 void* cuda_stream) {
   using namespace kc;
-  if (validate_csr(nullptr, A) != KC_OK || validate_state(nullptr, A, st) != KC_OK)
+  if (validate_csr_entries(nullptr, A) != KC_OK || validate_state(nullptr, A, st) != KC_OK)
     return KC_ERR_INVALID_ARG;
   if (st->q_dtype != KC_F64 || A->val_dtype != KC_F64) return KC_ERR_INVALID_ARG;
   const int k = st->k;

@@ -4,10 +4,13 @@ This package holds input construction only (operators, right-hand sides, start v
 random fields): none of the Gram-Schmidt, Arnoldi, GMRES or Krylov-Schur arithmetic lives
 here, so both sides can import it without sharing any of the method's code.
 """
-from .operators import (CSR, convdiff_csr, manteuffel_csr, config1_operator,
-                        config2_operator, config3_operator, config5_operator,
-                        varcoef_fields_2d)
-from .vectors import gaussian_vector
+from .operators import (CSR, Stencil7, convdiff_csr, convdiff_stencil7, manteuffel_csr,
+                        manteuffel_stencil7, config1_operator, config1_stencil,
+                        config2_operator, config2_stencil, config3_operator,
+                        config5_operator, varcoef_fields_2d)
+from .vectors import gaussian_vector, graded_factors, graded_matrix
 
-__all__ = ["CSR", "convdiff_csr", "manteuffel_csr", "config1_operator", "config2_operator",
-           "config3_operator", "config5_operator", "varcoef_fields_2d", "gaussian_vector"]
+__all__ = ["CSR", "Stencil7", "convdiff_csr", "convdiff_stencil7", "manteuffel_csr",
+           "manteuffel_stencil7", "config1_operator", "config1_stencil", "config2_operator",
+           "config2_stencil", "config3_operator", "config5_operator", "varcoef_fields_2d",
+           "gaussian_vector", "graded_factors", "graded_matrix"]

@@ -150,6 +150,59 @@ def manteuffel_csr(k: int, beta: float = 0.5) -> CSR:
     return _assemble(m, offsets, values, masks)
 
 
+@dataclass
+class Stencil7:
+    """Constant-coefficient 7-point stencil on an nx x ny x nz grid (x fastest), zero outside.
+
+    c = (centre, x-1, x+1, y-1, y+1, z-1, z+1): row i = ix + nx (iy + ny iz) has c[0] on the
+    diagonal and each neighbour coefficient where that neighbour lies in the grid."""
+    grid: tuple
+    c: tuple
+
+    @property
+    def m(self) -> int:
+        nx, ny, nz = self.grid
+        return nx * ny * nz
+
+    @property
+    def nnz(self) -> int:
+        """Number of stored entries of the equivalent CSR matrix (zero coefficients count)."""
+        nx, ny, nz = self.grid
+        m = self.m
+        return m + 2 * (m - ny * nz) + 2 * (m - nx * nz) + 2 * (m - nx * ny)
+
+
+def convdiff_stencil7(N: int, dim: int, wind) -> Stencil7:
+    """The operator of ``convdiff_csr(N, dim, wind)`` with kappa = 1 and a constant wind, as a
+    stencil.  Every row of that matrix carries the same coefficients (the harmonic mean of
+    two unit kappas is 1, and a boundary face uses the interior kappa 1), so the stencil
+    with zero values outside the grid is the same matrix; the coefficients are formed by the
+    same floating-point expressions, so they equal the CSR values bit for bit."""
+    if dim not in (2, 3):
+        raise ValueError("dim must be 2 or 3")
+    h = 1.0 / (N + 1)
+    wind = np.asarray(wind, dtype=np.float64)
+    diag = 0.0
+    lo = [0.0, 0.0, 0.0]
+    up = [0.0, 0.0, 0.0]
+    for a in range(dim):
+        kl = ku = 1.0
+        bpos = max(float(wind[a]), 0.0) * h
+        bneg = max(-float(wind[a]), 0.0) * h
+        diag += kl + ku + bpos + bneg
+        lo[a] = -(kl + bpos)
+        up[a] = -(ku + bneg)
+    grid = (N, N, N) if dim == 3 else (N, N, 1)
+    return Stencil7(grid, (diag, lo[0], up[0], lo[1], up[1], lo[2], up[2]))
+
+
+def manteuffel_stencil7(k: int, beta: float = 0.5) -> Stencil7:
+    """``manteuffel_csr(k, beta)`` as a 5-point stencil on a k x k grid (nz = 1)."""
+    lo = -1.0 - beta / 2.0
+    up = -1.0 + beta / 2.0
+    return Stencil7((k, k, 1), (4.0, lo, up, lo, up, 0.0, 0.0))
+
+
 def _unit(v):
     v = np.asarray(v, dtype=np.float64)
     return v / np.linalg.norm(v)
@@ -163,6 +216,16 @@ def config1_operator() -> CSR:
 def config2_operator(N: int = 252) -> CSR:
     """3D, N = 252 (m = 16,003,008), constant wind along (1, 0.5, 0.25), Peclet 50."""
     return convdiff_csr(N, 3, 50.0 * _unit([1.0, 0.5, 0.25]))
+
+
+def config1_stencil() -> Stencil7:
+    """``config1_operator()`` in matrix-free form."""
+    return convdiff_stencil7(100, 2, 10.0 * _unit([1.0, 1.0]))
+
+
+def config2_stencil(N: int = 252) -> Stencil7:
+    """``config2_operator(N)`` in matrix-free form."""
+    return convdiff_stencil7(N, 3, 50.0 * _unit([1.0, 0.5, 0.25]))
 
 
 def config3_operator(N: int = 1000, seed: int = 1003) -> CSR:
