@@ -9,6 +9,9 @@ Pins (tests/test_oracle_arnoldi.py): Arnoldi relation and loss of orthogonality 
 agreement of DCGS2, CGS2 and MGS Hessenbergs on well-conditioned problems, agreement with
 Householder QR (LAPACK) of the Krylov matrix, the k = 0 start, breakdown on A = I, the
 diagonal-matrix Lanczos case, and the Manteuffel spectrum through Krylov-Schur.
+The QR variants (tests/test_oracle_stability.py): the loss-of-orthogonality classes of
+Table 3 over graded condition numbers (CGS eps kappa^2, MGS eps kappa, CGS2 and DCGS2 at
+O(eps)), the representation error at O(eps), agreement with Householder QR.
 """
 from __future__ import annotations
 
@@ -150,6 +153,39 @@ def mgs_arnoldi(A, r0, n: int):
         H[j + 1, j] = alpha
         Q[:, j + 1] = v / alpha
     return Q, H
+
+
+def cgs_qr(B):
+    """Classical Gram-Schmidt QR, one projection pass (Algorithm 1 without its second
+    projection): the O(eps) kappa^2 loss-of-orthogonality class of Table 3."""
+    m, n = B.shape
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    for j in range(n):
+        a = B[:, j]
+        S = Q[:, :j].T @ a
+        u = a - Q[:, :j] @ S
+        alpha = np.sqrt(u @ u)
+        Q[:, j] = u / alpha
+        R[:j, j] = S
+        R[j, j] = alpha
+    return Q, R
+
+
+def mgs_qr(B):
+    """Modified Gram-Schmidt QR, level 1 (Section 2: the rank-1 projections I - q_i q_i^T
+    applied one after another, one inner product each): the O(eps) kappa class of Table 3."""
+    m, n = B.shape
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    for j in range(n):
+        u = np.array(B[:, j], dtype=np.float64)
+        for i in range(j):
+            R[i, j] = Q[:, i] @ u
+            u = u - R[i, j] * Q[:, i]
+        R[j, j] = np.sqrt(u @ u)
+        Q[:, j] = u / R[j, j]
+    return Q, R
 
 
 def cgs2_qr(B):
