@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import arnoldi as orc  # noqa: E402
 from oracle.metrics import loo  # noqa: E402
-from synth import gaussian_vector  # noqa: E402
+from synth import gaussian_vector, graded_factors, graded_matrix  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -75,3 +75,24 @@ def test_dcgs2_qr_rejects_bad_arguments(kc, ctx):
         kc.dcgs2_qr(ctx, At, Qt, torch.zeros((4, 3), dtype=torch.float64, device="cuda"))
     with pytest.raises(kc.KrylovError):                 # odd leading dimension of A
         kc.dcgs2_qr(ctx, torch.zeros((4, 101), dtype=torch.float64, device="cuda"), Qt, Rt)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_dcgs2_qr_orthogonality_over_condition_numbers(kc, ctx, mode):
+    """Table 3: DCGS2 (QR) keeps the loss of orthogonality at O(eps) whatever kappa(A), and
+    the representation error at O(eps).  Graded matrices with kappa from 1e2 to 1e14 (one
+    pair of orthonormal factors, seed 900); R against the oracle at every kappa, Q where it
+    is well determined (kappa <= 1e5)."""
+    eps = 2.0 ** -52
+    m, n = 20000, 40
+    factors = graded_factors(m, n, 900)
+    for e in (2, 5, 8, 11, 14):
+        B = graded_matrix(m, n, 10.0 ** e, 900, factors=factors)
+        Qg, Rg = _run(kc, ctx, B, mode)
+        assert loo(Qg) <= 100 * eps, (e, loo(Qg))
+        assert np.linalg.norm(B - Qg @ Rg) / np.linalg.norm(B) <= 10 * eps
+        assert ctx.read_status() == 0
+        Qo, Ro = orc.dcgs2_qr(B)
+        assert np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro) <= 1e-12
+        if e <= 5:
+            assert np.abs(Qg - Qo).max() <= 1e-9
