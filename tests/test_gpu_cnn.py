@@ -82,8 +82,8 @@ def test_forward_matches_oracle(kc, ctx, B, H, W, conv):
 
 
 @pytest.mark.parametrize("conv", [0, 1])
-def test_gradients_match_oracle(kc, ctx, conv):
-    B, H, W = 2, 24, 40
+@pytest.mark.parametrize("B,H,W", [(2, 24, 40), (3, 13, 37)])
+def test_gradients_match_oracle(kc, ctx, conv, B, H, W):
     ws = cnn.init_weights(5)
     w32 = pack(ws)
     rng = np.random.default_rng(6)
