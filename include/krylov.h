@@ -134,6 +134,15 @@ kc_status kc_set_staged(kc_ctx* ctx, int flags);
  * 1 tcgen05 (default: tensor-copy fed, accumulator in tensor memory, operands in shared
  * memory).  Same arithmetic: BF16 products, FP32 accumulation (summation order differs). */
 kc_status kc_set_conv_kernel(kc_ctx* ctx, int kind);
+/* Execution path of an FP64 gmres_solve (precision 0): 0 (default) chooses by size, 1 the
+ * multi-kernel path (three launches per Arnoldi step, the host reads the Givens state once
+ * per cycle), 2 the one-cluster path: the whole restarted solve in ONE launch of a
+ * thread-block cluster (16 CTAs, or 8) that owns the rows in blocks and replaces kernel
+ * boundaries by cluster barriers and the cross-CTA sums by distributed-shared-memory reads;
+ * it is latency-optimal for small m and limited to the cluster's SMs for large m, so 0
+ * takes it when each CTA's rows of the basis fit in its shared memory (about 12,000 rows
+ * at GMRES(30)).  Both give the same iterates up to rounding. */
+kc_status kc_set_gmres_path(kc_ctx* ctx, int path);
 /* Number of SMs and the persistent grid size used for reductions. */
 kc_status kc_device_info(const kc_ctx* ctx, int* num_sms, int* reduce_grid);
 /* Number of kernels this context has launched since creation (host-side counter). */

@@ -178,6 +178,12 @@ kc_status kc_set_conv_kernel(kc_ctx* ctx, int kind) {
   return KC_OK;
 }
 
+kc_status kc_set_gmres_path(kc_ctx* ctx, int path) {
+  if (!ctx || path < 0 || path > 2) return KC_ERR_INVALID_ARG;
+  ctx->gmres_path = path;
+  return KC_OK;
+}
+
 kc_status kc_set_staged(kc_ctx* ctx, int flags) {
   if (!ctx || flags < 0 || flags > 3) return KC_ERR_INVALID_ARG;
   ctx->staged = flags;

@@ -1,0 +1,503 @@
+// Restarted FP64 DCGS2-GMRES(n) for small problems in ONE thread-block cluster and ONE
+// launch per solve.
+//
+// At m = 10^4 (the 2D convection-diffusion problem of the GMRES benchmark) a DCGS2 step of
+// the multi-kernel path is three launches whose cost is latency, not bytes: the fused
+// reduction alone takes 12-30 us of partial sums, last-CTA ticket and serial scalar work
+// for 2.5 MB of basis.  Here the CTAs of one cluster (16, or 8 where 16 cannot be
+// scheduled) own contiguous row blocks of Q, w, v and x and run every phase of the solve
+// in place:
+//   per Arnoldi step (Algorithm 4): v = A w on the CTA's rows; the partial sums of
+//   [Q_k, w]^T [w, v]; one cluster barrier; every CTA adds the partials of all CTAs in the
+//   same rank order (distributed shared memory), so every CTA holds bitwise the same C, S,
+//   beta, s and takes the same decisions; alpha by Pythagoras, T by Stephen's trick; the
+//   row-local update of q_k and w; CTA 0 alone forms the lagged H and K columns and
+//   rotates the finalised column (Givens, stop test); a second cluster barrier makes w
+//   (read across row blocks by the next matvec) and CTA 0's stop flag visible;
+//   per cycle: the CGS2 finish of the last column (two projections and a norm), the
+//   triangular solve y = R^{-1} g in CTA 0 (column-parallel back substitution), x += Q y,
+//   and the FP64 residual b - A x with its norm for the restart test.
+// Where they fit, a CTA keeps its rows of the basis, of v and of w in shared memory
+// (config 1: 625 rows x 31 columns, 155 KB; w is also written to global memory for the
+// other CTAs' matvecs) and CTA 0 keeps H, K, R there, so the step's dependent chains run at
+// shared-memory latency; otherwise the same code addresses them in global memory.  The
+// partial-sum buffers alternate between reductions, so one barrier per reduction is enough:
+// a CTA writes a buffer again only after the next reduction's barrier, which every CTA
+// reaches after it has read that buffer.  Vectors other CTAs write (w, x)
+// are read through L2 (ld.global.cg), never from a stale L1 line; a last barrier keeps
+// every CTA (and its shared memory) alive until all remote reads are done.  There are no
+// spin-waits: the cluster barriers are the hardware's.
+#include "kc_internal.cuh"
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+namespace kc {
+
+constexpr int GC_THREADS = 1024;       // one thread per row at config 1 (625 rows per CTA)
+constexpr int GC_WARPS = GC_THREADS / 32;
+constexpr int GC_PART = 2 * NMAX + 2;
+constexpr int GC_DYN_SMEM_MAX = 200 * 1024;   // dynamic shared memory the kernel may use
+
+struct GcArgs {
+  // operator: CSR (stencil == 0) or the 7-point stencil
+  const int32_t* rp;
+  const int32_t* ci;
+  const double* val;
+  int nx, ny, nz, stencil;
+  double c7[7];
+  const double* b;
+  double* x;
+  double* Q;        // global basis (used when the rows do not fit in shared memory)
+  int64_t ldq;
+  double* w;
+  double* v;
+  double* H;        // (n+1) x n, ld n+1   (global copies, used when not in shared memory)
+  double* K;        // (n+1) x n, ld n+1
+  double* R;        // n x n, ld n
+  int n;
+  int maxit;
+  int64_t m;
+  int rc;           // rows per CTA, at most (the shared-memory row capacity)
+  int smem_q;       // the CTA's rows of Q, v and w live in shared memory
+  int smem_h;       // CTA 0 keeps H, K, R in shared memory
+  double rtol;
+  double* out;      // matvecs, cycles, est, rn, bnorm, result, last status
+};
+
+__device__ __forceinline__ double gc_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// (A y)_r with y read through L2 (its entries outside this CTA's rows are written by others)
+__device__ __forceinline__ double gc_apply_row(const GcArgs& a, const double* y, int64_t r) {
+  double s = 0.0;
+  if (a.stencil) {
+    const int64_t pl = (int64_t)a.nx * a.ny;
+    const int64_t t = r / a.nx;
+    const int ix = (int)(r - t * a.nx), iy = (int)(t % a.ny), iz = (int)(t / a.ny);
+    if (iz > 0) s += a.c7[5] * __ldcg(y + r - pl);
+    if (iy > 0) s += a.c7[3] * __ldcg(y + r - a.nx);
+    if (ix > 0) s += a.c7[1] * __ldcg(y + r - 1);
+    s += a.c7[0] * __ldcg(y + r);
+    if (ix < a.nx - 1) s += a.c7[2] * __ldcg(y + r + 1);
+    if (iy < a.ny - 1) s += a.c7[4] * __ldcg(y + r + a.nx);
+    if (iz < a.nz - 1) s += a.c7[6] * __ldcg(y + r + pl);
+    return s;
+  }
+  for (int j = a.rp[r]; j < a.rp[r + 1]; j++) s += a.val[j] * __ldcg(y + a.ci[j]);
+  return s;
+}
+
+// Sum over the cluster of the nval partials each CTA left in `mine`, in rank order, into
+// `tot` (identical in every CTA).  Includes the cluster barrier; ends with __syncthreads.
+__device__ void gc_cluster_sum(cg::cluster_group& cl, double* mine, double* tot, int nval) {
+  __threadfence();
+  cl.sync();
+  const int nb = (int)cl.num_blocks();
+  for (int i = threadIdx.x; i < nval; i += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nb; c++) s += cl.map_shared_rank(mine, c)[i];
+    tot[i] = s;
+  }
+  __syncthreads();
+}
+
+// this thread's partial of a scalar sum -> part[0] of the CTA (fixed order)
+__device__ void gc_block_sum(double val, double* part, double* scratch) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  val = gc_warp_sum(val);
+  if (lane == 0) scratch[warp] = val;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < GC_WARPS; i++) s += scratch[i];
+    part[0] = s;
+  }
+}
+
+__device__ __forceinline__ void gc_set_status(int* st, int v) {
+  if (*st == KC_OK) *st = v;
+}
+
+__global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t r0 = a.m * rank / nb, r1 = a.m * (rank + 1) / nb;
+  const int nrow = (int)(r1 - r0);
+  const int n = a.n, ldh = n + 1, ldk = n + 1, ldr = n;
+  extern __shared__ __align__(16) double gc_dyn[];
+  __shared__ double part[2][GC_PART];
+  __shared__ double tot[GC_PART];
+  __shared__ double sC[NMAX], sC2[NMAX], sT[NMAX + 1], sy[NMAX];
+  __shared__ double s_g[NMAX + 1], s_gc[NMAX], s_gs[NMAX];   // CTA 0: Givens state
+  __shared__ double scratch[GC_WARPS];
+  __shared__ double s_alpha, s_inv_alpha, s_est;
+  __shared__ int s_status, s_stop, s_ncols;                   // CTA 0: cycle state
+  // this CTA's rows of the basis (column j at Qb + j * qs, row r at index r - r0), of v
+  // and of w, and CTA 0's H, K, R: in shared memory where they fit, else in global memory.
+  // w is also kept in global memory (wg), where the other CTAs' matvecs read it.
+  double* const dyn = gc_dyn;
+  double* const Qb = a.smem_q ? dyn : a.Q + r0;
+  const int64_t qs = a.smem_q ? (int64_t)a.rc : a.ldq;
+  double* const vb = a.smem_q ? dyn + (int64_t)(n + 1) * a.rc : a.v + r0;
+  double* const wg = a.w + r0;
+  double* const wb = a.smem_q ? vb + a.rc : wg;
+  double* const hb = a.smem_q ? wb + a.rc : dyn;
+  double* const Hm = a.smem_h ? hb : a.H;
+  double* const Km = a.smem_h ? hb + (n + 1) * n : a.K;
+  double* const Rm = a.smem_h ? hb + 2 * (n + 1) * n : a.R;
+  int pb = 0;                             // partial-sum buffer of the next reduction
+
+  // ||b|| and the absolute tolerance
+  {
+    double acc = 0.0;
+    for (int64_t r = r0 + tid; r < r1; r += GC_THREADS) acc += a.b[r] * a.b[r];
+    gc_block_sum(acc, part[pb], scratch);
+    gc_cluster_sum(cl, part[pb], tot, 1);
+    pb ^= 1;
+  }
+  const double bnorm = sqrt(tot[0]);
+  if (!(bnorm > 0.0)) {
+    for (int64_t r = r0 + tid; r < r1; r += GC_THREADS) a.x[r] = 0.0;
+    if (rank == 0 && tid == 0) {
+      a.out[0] = 0; a.out[1] = 0; a.out[2] = 0.0; a.out[3] = 0.0; a.out[4] = 0.0;
+      a.out[5] = KC_OK; a.out[6] = KC_OK;
+    }
+    cl.sync();                              // no CTA exits while its partials may be read
+    return;
+  }
+  const double target = a.rtol * bnorm;
+  int matvecs = 0, cycles = 0, last_status = KC_OK, result = KC_ERR_NOT_CONVERGED;
+  double rn = 0.0, est = 0.0;
+  const int* stop0 = cl.map_shared_rank(&s_stop, 0);
+  const int* ncols0 = cl.map_shared_rank(&s_ncols, 0);
+  const double* est0 = cl.map_shared_rank(&s_est, 0);
+
+  for (;;) {
+    // ---- FP64 residual w = r = b - A x and its norm (x is written by every CTA) ----
+    __threadfence();
+    cl.sync();
+    {
+      double acc = 0.0;
+      for (int i = tid; i < nrow; i += GC_THREADS) {
+        const double rr = a.b[r0 + i] - gc_apply_row(a, a.x, r0 + i);
+        wb[i] = rr;
+        if (a.smem_q) wg[i] = rr;
+        acc += rr * rr;
+      }
+      gc_block_sum(acc, part[pb], scratch);
+      gc_cluster_sum(cl, part[pb], tot, 1);
+      pb ^= 1;
+    }
+    rn = sqrt(tot[0]);
+    if (rn <= target) { result = KC_OK; break; }
+    if (matvecs >= a.maxit) break;
+
+    // ---- one GMRES(n) cycle ----
+    if (rank == 0 && tid == 0) {
+      s_stop = 0;
+      s_ncols = 0;
+      s_est = 0.0;
+      s_status = KC_OK;
+    }
+    bool stopped = false;
+    for (int k = 0; k < n; k++) {
+      // v = A w on this CTA's rows (w of the neighbouring rows comes from other CTAs)
+      for (int i = tid; i < nrow; i += GC_THREADS) vb[i] = gc_apply_row(a, a.w, r0 + i);
+      __syncthreads();
+      // partial sums: task t < k gives (q_t^T w, q_t^T v), task k (w^T w, w^T v)
+      for (int t = warp; t <= k; t += GC_WARPS) {
+        const double* q = t < k ? Qb + (int64_t)t * qs : wb;
+        double s0 = 0.0, s1 = 0.0;
+        for (int i = lane; i < nrow; i += 32) {
+          const double qi = q[i];
+          s0 += qi * wb[i];
+          s1 += qi * vb[i];
+        }
+        s0 = gc_warp_sum(s0);
+        s1 = gc_warp_sum(s1);
+        if (lane == 0) {
+          part[pb][2 * t] = s0;
+          part[pb][2 * t + 1] = s1;
+        }
+      }
+      gc_cluster_sum(cl, part[pb], tot, 2 * k + 2);
+      pb ^= 1;
+      // scalar step (every CTA): Pythagoras (Alg. 4 line 4), T (lines 5-6, eq. 30)
+      if (warp == 0) {
+        double cc = 0.0, cs = 0.0;
+        for (int i = lane; i < k; i += 32) {
+          cc += tot[2 * i] * tot[2 * i];
+          cs += tot[2 * i] * tot[2 * i + 1];
+        }
+        cc = gc_warp_sum(cc);
+        cs = gc_warp_sum(cs);
+        if (lane == 0) {
+          const double beta = tot[2 * k], s = tot[2 * k + 1];
+          double a2 = beta - cc;
+          if (!isfinite(a2) || !isfinite(s)) {
+            if (rank == 0) gc_set_status(&s_status, KC_ERR_NONFINITE);
+          } else if (!(a2 > 0.0)) {
+            if (rank == 0) gc_set_status(&s_status, KC_ERR_PYTHAGORAS_NEG);
+            a2 = fmax(a2, 1e-300);
+          }
+          const double alpha = sqrt(a2), ia = 1.0 / alpha;
+          s_alpha = alpha;
+          s_inv_alpha = ia;
+          sT[k] = (s - cs) * ia * ia;
+        }
+      }
+      __syncthreads();
+      const double alpha = s_alpha, inv_alpha = s_inv_alpha;
+      for (int i = tid; i < k; i += GC_THREADS) {
+        sC[i] = tot[2 * i];
+        sT[i] = tot[2 * i + 1] * inv_alpha;
+      }
+      __syncthreads();
+      // update of this CTA's rows: q_k = (w - Q C)/alpha, w <- v/alpha - Q T - q_k T_k
+      for (int i = tid; i < nrow; i += GC_THREADS) {
+        double qc = 0.0, qt = 0.0;
+        for (int j = 0; j < k; j++) {
+          const double qj = Qb[(int64_t)j * qs + i];
+          qc += qj * sC[j];
+          qt += qj * sT[j];
+        }
+        const double q = (wb[i] - qc) * inv_alpha;
+        Qb[(int64_t)k * qs + i] = q;
+        const double wn = vb[i] * inv_alpha - qt - q * sT[k];
+        wb[i] = wn;
+        if (a.smem_q) wg[i] = wn;
+      }
+      // CTA 0: H(0:k, k-1) = K(0:k, k-1) + C, H(k, k-1) = alpha (lines 10, 12);
+      // K(0:k, k) = T - H(0:k, 0:k-1) C / alpha (line 11); Givens of column k-1
+      if (rank == 0) {
+        if (k >= 1) {
+          for (int i = tid; i < k; i += GC_THREADS)
+            Hm[i + (int64_t)(k - 1) * ldh] = Km[i + (int64_t)(k - 1) * ldk] + sC[i];
+          if (tid == 0) Hm[k + (int64_t)(k - 1) * ldh] = alpha;
+          __syncthreads();
+          if (warp == 0) {
+            double cn = 0.0;
+            for (int i = lane; i <= k; i += 32) {
+              const double h = Hm[i + (int64_t)(k - 1) * ldh];
+              cn += h * h;
+            }
+            cn = gc_warp_sum(cn);
+            if (lane == 0 && alpha <= 1e-13 * sqrt(cn)) gc_set_status(&s_status, KC_ERR_BREAKDOWN);
+          }
+          if (tid == 32) {                  // Givens rotation of the finalised column k-1
+            s_est = givens_rotate(s_gc, s_gs, s_g, Hm, ldh, k - 1, Rm, ldr);
+            s_ncols = k;
+            if (!(s_est > target)) s_stop = 1;
+          }
+        } else if (tid == 0) {
+          s_g[0] = alpha;
+        }
+        for (int i = tid; i <= k; i += GC_THREADS) {
+          double hc = 0.0;
+          for (int j = 0; j < k; j++) hc += Hm[i + (int64_t)j * ldh] * sC[j];
+          Km[i + (int64_t)k * ldk] = sT[i] - hc * inv_alpha;
+        }
+      }
+      // w and CTA 0's stop flag become visible to every CTA
+      __threadfence();
+      cl.sync();
+      if (*stop0) { stopped = true; break; }
+    }
+    if (!stopped) {
+      // CGS2 finish of the last column: C1 = Q^T w, w -= Q C1, C2 = Q^T w, w -= Q C2,
+      // alpha = ||w||; H(:, n-1) = K(:, n-1) + C1 + C2, H(n, n-1) = alpha
+      for (int pass = 0; pass < 3; pass++) {
+        const int ntask = pass < 2 ? n : 0;      // pass 2: the norm alone
+        for (int t = warp; t <= ntask; t += GC_WARPS) {
+          const double* q = t < ntask ? Qb + (int64_t)t * qs : wb;
+          double s0 = 0.0;
+          for (int i = lane; i < nrow; i += 32) s0 += q[i] * wb[i];
+          s0 = gc_warp_sum(s0);
+          if (lane == 0) part[pb][t] = s0;
+        }
+        gc_cluster_sum(cl, part[pb], tot, ntask + 1);
+        pb ^= 1;
+        if (pass == 2) break;
+        double* cdst = pass == 0 ? sC : sC2;
+        for (int i = tid; i < n; i += GC_THREADS) cdst[i] = tot[i];
+        __syncthreads();
+        for (int i = tid; i < nrow; i += GC_THREADS) {
+          double qc = 0.0;
+          for (int j = 0; j < n; j++) qc += Qb[(int64_t)j * qs + i] * cdst[j];
+          wb[i] -= qc;
+        }
+        __syncthreads();
+      }
+      const double alpha = sqrt(tot[0]);
+      if (rank == 0) {
+        for (int i = tid; i < n; i += GC_THREADS)
+          Hm[i + (int64_t)(n - 1) * ldh] = Km[i + (int64_t)(n - 1) * ldk] + sC[i] + sC2[i];
+        if (tid == 0) Hm[n + (int64_t)(n - 1) * ldh] = alpha;
+        __syncthreads();
+        if (warp == 0) {
+          double cn = 0.0;
+          for (int i = lane; i <= n; i += 32) {
+            const double h = Hm[i + (int64_t)(n - 1) * ldh];
+            cn += h * h;
+          }
+          cn = gc_warp_sum(cn);
+          if (lane == 0 && alpha <= 1e-13 * sqrt(cn)) gc_set_status(&s_status, KC_ERR_BREAKDOWN);
+        }
+        if (tid == 32) {
+          s_est = givens_rotate(s_gc, s_gs, s_g, Hm, ldh, n - 1, Rm, ldr);
+          s_ncols = n;
+          if (!(s_est > target)) s_stop = 1;
+        }
+      }
+    }
+    // y = R^{-1} g in CTA 0 (column-oriented back substitution), then x += Q y everywhere
+    if (rank == 0) {
+      __syncthreads();
+      const int nc = s_ncols;
+      for (int i = tid; i < nc; i += GC_THREADS) sy[i] = s_g[i];
+      for (int j = nc - 1; j >= 0; j--) {
+        __syncthreads();
+        if (tid == 0) sy[j] = sy[j] / Rm[j + (int64_t)j * ldr];
+        __syncthreads();
+        const double yj = sy[j];
+        for (int i = tid; i < j; i += GC_THREADS) sy[i] -= Rm[i + (int64_t)j * ldr] * yj;
+      }
+    }
+    __threadfence();
+    cl.sync();
+    const int nc = *ncols0;                 // columns finalised in this cycle
+    const double* y0 = cl.map_shared_rank(sy, 0);
+    double* yl = sT;                        // local copy of y (T is not needed any more)
+    for (int i = tid; i < nc; i += GC_THREADS) yl[i] = y0[i];
+    __syncthreads();
+    for (int i = tid; i < nrow; i += GC_THREADS) {
+      double s = 0.0;
+      for (int j = 0; j < nc; j++) s += Qb[(int64_t)j * qs + i] * yl[j];
+      a.x[r0 + i] += s;
+    }
+    const int stop_flag = *stop0;
+    matvecs += (stop_flag && nc < n) ? nc + 1 : n;
+    cycles++;
+    est = *est0;
+    if (rank == 0 && s_status != KC_OK && s_status != KC_ERR_BREAKDOWN) last_status = s_status;
+  }
+  cl.sync();                                // no CTA exits while its shared memory may be read
+  if (rank == 0 && tid == 0) {
+    a.out[0] = matvecs;
+    a.out[1] = cycles;
+    a.out[2] = est;
+    a.out[3] = rn;
+    a.out[4] = bnorm;
+    a.out[5] = result;
+    a.out[6] = last_status;
+  }
+}
+
+// cluster size the device can schedule for the kernel with `smem` bytes of dynamic shared
+// memory (16, else 8; 0 if neither)
+static int gmres_cluster_size(int smem) {
+  for (int cs = 16; cs >= 8; cs /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(GC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_gmres_cluster, &cfg) == cudaSuccess &&
+        nclusters >= 1)
+      return cs;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+static void gmres_cluster_probe(kc_ctx* ctx) {
+  static std::atomic<unsigned long long> attr_done{0};
+  const unsigned long long bit = 1ull << (ctx->device & 63);
+  if (!(attr_done.load(std::memory_order_acquire) & bit)) {
+    cudaFuncSetAttribute(k_gmres_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_gmres_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         GC_DYN_SMEM_MAX);
+    cudaGetLastError();
+    attr_done.fetch_or(bit, std::memory_order_release);
+  }
+  if (ctx->gmres_cluster == 0) {
+    const int probed = gmres_cluster_size(GC_DYN_SMEM_MAX);
+    ctx->gmres_cluster = probed > 0 ? probed : -1;
+  }
+}
+
+// shared-memory bytes of a CTA's rows of Q (n+1 columns), v and w
+static int64_t gmres_cluster_row_bytes(int64_t m, int n, int cs) {
+  return (int64_t)(n + 3) * ((m + cs - 1) / cs) * 8;
+}
+
+bool gmres_cluster_preferred(kc_ctx* ctx, int64_t m, int n) {
+  gmres_cluster_probe(ctx);
+  return ctx->gmres_cluster > 0 &&
+         gmres_cluster_row_bytes(m, n, ctx->gmres_cluster) <= GC_DYN_SMEM_MAX;
+}
+
+kc_status gmres_cluster_solve(kc_ctx* ctx, const kc_csr* A, const double* b, double* x,
+                              double* Q, int64_t ldq, double* w, double* v, double* H,
+                              double* K, double* R, int n, int maxit, double rtol,
+                              double* out_dev, double* out_host) {
+  gmres_cluster_probe(ctx);
+  const int cs = ctx->gmres_cluster;
+  if (cs < 0) return fail(ctx, KC_ERR_CUDA, "gmres: no thread-block cluster can be scheduled");
+  GcArgs a = {};
+  if (is_stencil(A)) {
+    a.stencil = 1;
+    a.nx = A->grid[0];
+    a.ny = A->grid[1];
+    a.nz = A->grid[2];
+    for (int i = 0; i < 7; i++) a.c7[i] = A->stencil[i];
+  } else {
+    a.rp = A->row_ptr;
+    a.ci = A->col_idx;
+    a.val = (const double*)A->val;
+  }
+  a.b = b; a.x = x; a.Q = Q; a.ldq = ldq; a.w = w; a.v = v; a.H = H; a.K = K; a.R = R;
+  a.n = n; a.maxit = maxit; a.m = A->m; a.rtol = rtol; a.out = out_dev;
+  // shared-memory residency: rows of Q, v and w per CTA, then CTA 0's H, K, R
+  const int64_t rc = (A->m + cs - 1) / cs;
+  const int64_t bq = gmres_cluster_row_bytes(A->m, n, cs);
+  const int64_t bh = (int64_t)(2 * (n + 1) * n + n * n) * 8;
+  a.rc = (int)rc;
+  a.smem_q = bq <= GC_DYN_SMEM_MAX;
+  a.smem_h = (a.smem_q ? bq : 0) + bh <= GC_DYN_SMEM_MAX;
+  const int64_t dyn = (a.smem_q ? bq : 0) + (a.smem_h ? bh : 0);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, 1, 1);
+  cfg.blockDim = dim3(GC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)dyn;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  timing_begin(ctx, KID_OTHER);
+  KC_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_gmres_cluster, a));
+  KC_LAUNCHED(ctx);
+  KC_CUDA(ctx, cudaMemcpyAsync(out_host, out_dev, 7 * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  KC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return KC_OK;
+}
+
+}  // namespace kc

@@ -46,6 +46,37 @@ struct Scalars {
   double zscale[NMAX];  // flexible GMRES: 1/alpha_k, the scale of the stored M(w_k)
 };
 
+// GMRES: rotate the just-finalised Hessenberg column j (rows 0..j+1) with the previous
+// Givens rotations (gc, gs), make a new one, update g; R (ld ldr) receives the rotated
+// column.  Returns |g_{j+1}|, the residual estimate.  Serial (one thread), O(j).
+__device__ inline double givens_rotate(double* gc, double* gs, double* g, const double* H,
+                                       int ldh, int j, double* R, int ldr) {
+  double h[NMAX + 1];
+  for (int i = 0; i <= j + 1; i++) h[i] = H[i + (int64_t)j * ldh];
+  for (int i = 0; i < j; i++) {
+    double t = gc[i] * h[i] + gs[i] * h[i + 1];
+    h[i + 1] = -gs[i] * h[i] + gc[i] * h[i + 1];
+    h[i] = t;
+  }
+  double r = hypot(h[j], h[j + 1]);
+  double c = h[j] / r, s = h[j + 1] / r;
+  gc[j] = c;
+  gs[j] = s;
+  h[j] = r;
+  for (int i = 0; i <= j; i++) R[i + (int64_t)j * ldr] = h[i];
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  return fabs(g[j + 1]);
+}
+
+// givens_rotate on the state in sc, raising `stop` when |g_{j+1}| <= rtol_abs
+__device__ inline void givens_column(Scalars* sc, const double* H, int ldh, int j, double* R,
+                                     int ldr) {
+  sc->resid_est = givens_rotate(sc->gc, sc->gs, sc->g, H, ldh, j, R, ldr);
+  sc->ncols = j + 1;
+  if (!(sc->resid_est > sc->rtol_abs)) sc->stop = 1;
+}
+
 enum Epilogue : int {
   EPI_DCGS2 = 0,        // full DCGS2 scalar step (flexible variant: see flags)
   EPI_STORE_C = 1,      // store Q^T x into C (finish first pass, CGS2 second projection)
@@ -111,6 +142,8 @@ struct kc_ctx {
   int fp64_mode;           // 0: every product in FP64; 1: FP64 with float-float offload
   int staged;              // bit 0: staged FP64 update; bit 1: tensor-copy staged reduction
   int conv_tc;             // 32 -> 32 convolutions: 0 mma.sync, 1 tcgen05 (tensor memory)
+  int gmres_path;          // FP64 gmres_solve: 0 auto, 1 multi-kernel, 2 one-cluster kernel
+  int gmres_cluster;       // its cluster size once probed (0: not yet, -1: none schedulable)
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
   kc::TimingRec* trec;
@@ -210,6 +243,16 @@ kc_status cnn_adam(kc_ctx* ctx, float* w, const float* g, float* m, float* v, in
 int64_t cnn_nparam();
 // the operator is the matrix-free 7-point stencil rather than a CSR matrix
 inline bool is_stencil(const kc_csr* A) { return A->grid[0] > 0; }
+// restarted FP64 DCGS2-GMRES in one thread-block cluster (kc_gmres_cluster.cu); writes
+// out_host[0..6] = matvecs, cycles, |g| estimate, ||b - A x||, ||b||, result, last status
+kc_status gmres_cluster_solve(kc_ctx* ctx, const kc_csr* A, const double* b, double* x,
+                              double* Q, int64_t ldq, double* w, double* v, double* H,
+                              double* K, double* R, int n, int maxit, double rtol,
+                              double* out_dev, double* out_host);
+// gmres_path 0 takes the one-cluster kernel when each CTA's rows of the basis, v and w fit
+// in its shared memory (about 12k rows at GMRES(30)): beyond that its 16 SMs of FP64 lose
+// to the whole GPU
+bool gmres_cluster_preferred(kc_ctx* ctx, int64_t m, int n);
 kc_status validate_csr(kc_ctx* ctx, const kc_csr* A);
 // validate_csr, and A must be a CSR matrix (for callers that read its entries)
 kc_status validate_csr_entries(kc_ctx* ctx, const kc_csr* A);

@@ -138,31 +138,6 @@ __device__ __forceinline__ void set_status(Scalars* sc, int st) {
   if (sc->status == KC_OK) sc->status = st;
 }
 
-// GMRES: rotate the just-finalised Hessenberg column j (rows 0..j+1) with the previous
-// Givens rotations, make a new one, update g, and raise `stop` when |g_{j+1}| <= rtol_abs.
-// R (ld ldr) receives the rotated column.  Serial (one thread), O(j).
-__device__ void givens_column(Scalars* sc, const double* H, int ldh, int j, double* R,
-                              int ldr) {
-  double h[NMAX + 1];
-  for (int i = 0; i <= j + 1; i++) h[i] = H[i + (int64_t)j * ldh];
-  for (int i = 0; i < j; i++) {
-    double t = sc->gc[i] * h[i] + sc->gs[i] * h[i + 1];
-    h[i + 1] = -sc->gs[i] * h[i] + sc->gc[i] * h[i + 1];
-    h[i] = t;
-  }
-  double r = hypot(h[j], h[j + 1]);
-  double c = h[j] / r, s = h[j + 1] / r;
-  sc->gc[j] = c;
-  sc->gs[j] = s;
-  h[j] = r;
-  for (int i = 0; i <= j; i++) R[i + (int64_t)j * ldr] = h[i];
-  sc->g[j + 1] = -s * sc->g[j];
-  sc->g[j] = c * sc->g[j];
-  sc->resid_est = fabs(sc->g[j + 1]);
-  sc->ncols = j + 1;
-  if (!(sc->resid_est > sc->rtol_abs)) sc->stop = 1;
-}
-
 // The scalar step of Algorithm 4 after alpha is known (all threads of one CTA).
 // Inputs in sc: C (C_{0:k-1}), S (raw S_{0:k-1} = Q_k^T v), s (= w^T v), cs (= C^T S).
 //   T_{0:k-1} = S/alpha (line 6), T_k = (s - C^T S)/alpha^2 (line 5, eq. 30);

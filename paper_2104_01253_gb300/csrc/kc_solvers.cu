@@ -232,6 +232,7 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   const size_t ov64 = off; off = align256(off + (size_t)ldq * 8);
   const size_t od = off; off = align256(off + (size_t)ldq * 4);
   const size_t orhs = off; off = align256(off + (size_t)ldq * 4);
+  const size_t oout = off; off = align256(off + 8 * sizeof(double));
   if ((s = ensure_workspace(ctx, off)) != KC_OK) return s;
   char* ws = (char*)ctx->ws;
   Cycle c;
@@ -244,6 +245,29 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   float* rhs32 = (float*)(ws + orhs);
   KC_CUDA(ctx, cudaMemsetAsync(c.H, 0, (size_t)(n + 1) * n * 8, ctx->stream));
   KC_CUDA(ctx, cudaMemsetAsync(c.K, 0, (size_t)(n + 1) * n * 8, ctx->stream));
+
+  // small FP64 problems: the whole solve in one thread-block cluster (one launch)
+  const bool cluster = prec == 0 && (ctx->gmres_path == 2 ||
+                                     (ctx->gmres_path == 0 && gmres_cluster_preferred(ctx, m, n)));
+  if (cluster) {
+    double out[7];
+    if ((s = gmres_cluster_solve(ctx, A, b, x, (double*)c.Q, ldq, (double*)c.w, (double*)c.v,
+                                 c.H, c.K, c.R, n, opts->maxit, opts->rtol,
+                                 (double*)(ws + oout), out)) != KC_OK)
+      return s;
+    const double bn = out[4];
+    info->iters = (int)out[0];
+    info->restarts = (int)out[1];
+    info->outer = 0;
+    info->rel_resid_est = bn > 0.0 ? out[2] / bn : 0.0;
+    info->rel_resid_true = bn > 0.0 ? out[3] / bn : 0.0;
+    const kc_status result = (kc_status)(int)out[5], last = (kc_status)(int)out[6];
+    info->status = result == KC_OK ? last : result;
+    if (result != KC_OK)
+      fail(ctx, result, "gmres_solve: %d matvecs, relative residual %.3e", info->iters,
+           info->rel_resid_true);
+    return result;
+  }
 
   double bnorm;
   if ((s = host_norm(ctx, b, m, KC_F64, &bnorm)) != KC_OK) return s;

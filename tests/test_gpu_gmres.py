@@ -27,7 +27,18 @@ def ctx(kc):
     return kc.Context(0)
 
 
-def test_one_cycle_solution_matches_oracle(kc, ctx):
+PATHS = [1, 2]     # Context.GMRES_MULTI_KERNEL, Context.GMRES_CLUSTER
+
+
+@pytest.fixture
+def path(ctx, request):
+    ctx.set_gmres_path(request.param)
+    yield request.param
+    ctx.set_gmres_path(0)
+
+
+@pytest.mark.parametrize("path", PATHS, indirect=True)
+def test_one_cycle_solution_matches_oracle(kc, ctx, path):
     Ah = config1_operator()
     b = gaussian_vector(Ah.m, 1001)
     A = kc.DeviceCSR(Ah)
@@ -41,7 +52,8 @@ def test_one_cycle_solution_matches_oracle(kc, ctx):
     assert abs(info["rel_resid_true"] - io["rel_resid_true"]) <= 1e-8 * io["rel_resid_true"]
 
 
-def test_config1_converges_to_1e10(kc, ctx):
+@pytest.mark.parametrize("path", PATHS, indirect=True)
+def test_config1_converges_to_1e10(kc, ctx, path):
     Ah = config1_operator()
     b = gaussian_vector(Ah.m, 1001)
     A = kc.DeviceCSR(Ah)
@@ -57,7 +69,8 @@ def test_config1_converges_to_1e10(kc, ctx):
     assert abs(info["iters"] - io["iters"]) <= 2
 
 
-def test_early_convergence_inside_a_cycle(kc, ctx):
+@pytest.mark.parametrize("path", PATHS, indirect=True)
+def test_early_convergence_inside_a_cycle(kc, ctx, path):
     """A well-conditioned operator converges before the basis fills: the device stop flag
     skips the remaining kernels of the cycle."""
     Ah = convdiff_csr(20, 2, [1.0, 1.0])
@@ -93,3 +106,68 @@ def test_iterative_refinement_reaches_fp64_accuracy(kc, ctx, precision, basis):
     assert abs(info["outer"] - io["outer"]) <= 1
     xs = xo
     assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) <= 1e-8
+
+
+@pytest.mark.parametrize("make", [lambda: convdiff_csr(31, 2, [7.0, 7.0]),       # m = 961
+                                  lambda: convdiff_csr(10, 3, [3.0, 1.0, 0.5]),   # m = 1000
+                                  lambda: convdiff_csr(50, 3, [50.0, 25.0, 12.5])])  # m = 125000
+def test_cluster_path_matches_multi_kernel_path(kc, ctx, make):
+    """The one-cluster solve (ragged row blocks, up to the auto threshold's size) takes the
+    same iterations as the multi-kernel path, and both reach a true residual of 1e-10."""
+    Ah = make()
+    b = gaussian_vector(Ah.m, 77)
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(b, device="cuda")
+    out = {}
+    try:
+        for p in (1, 2):
+            ctx.set_gmres_path(p)
+            x = torch.zeros_like(bd)
+            info = kc.gmres_solve(ctx, A, bd, x, restart=30, rtol=1e-10)
+            xg = x.cpu().numpy()
+            true = np.linalg.norm(b - Ah.to_scipy() @ xg) / np.linalg.norm(b)
+            assert info["status"] == 0 and true <= 1e-10
+            assert abs(true - info["rel_resid_true"]) <= 1e-3 * true
+            out[p] = (info, xg)
+    finally:
+        ctx.set_gmres_path(0)
+    assert abs(out[1][0]["iters"] - out[2][0]["iters"]) <= 1
+    assert out[1][0]["restarts"] == out[2][0]["restarts"]
+    x1, x2 = out[1][1], out[2][1]
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) <= 1e-6
+
+
+def test_cluster_path_on_stencil_operator(kc, ctx):
+    import synth
+    st = synth.config1_stencil()
+    Ah = config1_operator()
+    b = gaussian_vector(st.m, 1001)
+    bd = torch.as_tensor(b, device="cuda")
+    x = torch.zeros_like(bd)
+    ctx.set_gmres_path(2)
+    try:
+        info = kc.gmres_solve(ctx, kc.DeviceStencil7(st), bd, x, restart=30, rtol=1e-10)
+    finally:
+        ctx.set_gmres_path(0)
+    _, io = orc_gmres(Ah.to_scipy(), b, restart=30, rtol=1e-10)
+    xg = x.cpu().numpy()
+    assert info["status"] == 0
+    assert np.linalg.norm(b - Ah.to_scipy() @ xg) / np.linalg.norm(b) <= 1e-10
+    assert abs(info["iters"] - io["iters"]) <= 2
+
+
+@pytest.mark.parametrize("path", PATHS, indirect=True)
+def test_iteration_cap_and_zero_rhs(kc, ctx, path):
+    """maxit below one cycle: the cycle runs, the solve stops unconverged with the same
+    count on both paths; b = 0 returns x = 0 at once."""
+    Ah = config1_operator()
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(gaussian_vector(Ah.m, 1001), device="cuda")
+    x = torch.zeros_like(bd)
+    info = kc.gmres_solve(ctx, A, bd, x, restart=30, rtol=1e-10, maxit=10)
+    assert info["status"] == 5 and info["iters"] == 30 and info["restarts"] == 1
+    z = torch.zeros_like(bd)
+    x = torch.ones_like(bd)
+    info = kc.gmres_solve(ctx, A, z, x, restart=30, rtol=1e-10)
+    assert info["status"] == 0 and info["iters"] == 0
+    assert torch.count_nonzero(x).item() == 0
