@@ -228,13 +228,14 @@ def solver_suite(kc, ctx, A, m, stream):
     x1.zero_()
     out["config1_fp64_gmres30"] = timed_solve(
         lambda: kc.gmres_solve(ctx, A1, b1, x1, restart=30, rtol=1e-10))
-    out["config1_fp64_gmres30"]["path"] = "one thread-block cluster, one launch"
-    ctx.set_gmres_path(ctx.GMRES_MULTI_KERNEL)
-    x1.zero_()
-    kc.gmres_solve(ctx, A1, b1, x1, restart=30, rtol=1e-10)           # warm-up
-    x1.zero_()
-    out["config1_fp64_gmres30_multi_kernel"] = timed_solve(
-        lambda: kc.gmres_solve(ctx, A1, b1, x1, restart=30, rtol=1e-10))
+    out["config1_fp64_gmres30"]["path"] = "one launch, one CTA per SM (grid barrier)"
+    for name, path in (("config1_fp64_gmres30_cluster", ctx.GMRES_CLUSTER),
+                       ("config1_fp64_gmres30_multi_kernel", ctx.GMRES_MULTI_KERNEL)):
+        ctx.set_gmres_path(path)
+        x1.zero_()
+        kc.gmres_solve(ctx, A1, b1, x1, restart=30, rtol=1e-10)       # warm-up
+        x1.zero_()
+        out[name] = timed_solve(lambda: kc.gmres_solve(ctx, A1, b1, x1, restart=30, rtol=1e-10))
     ctx.set_gmres_path(ctx.GMRES_AUTO)
     A32 = kc.DeviceCSR.__new__(kc.DeviceCSR)
     A32.m, A32.nnz = A.m, A.nnz

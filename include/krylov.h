@@ -136,13 +136,20 @@ kc_status kc_set_staged(kc_ctx* ctx, int flags);
 kc_status kc_set_conv_kernel(kc_ctx* ctx, int kind);
 /* Execution path of an FP64 gmres_solve (precision 0): 0 (default) chooses by size, 1 the
  * multi-kernel path (three launches per Arnoldi step, the host reads the Givens state once
- * per cycle), 2 the one-cluster path: the whole restarted solve in ONE launch of a
- * thread-block cluster (16 CTAs, or 8) that owns the rows in blocks and replaces kernel
- * boundaries by cluster barriers and the cross-CTA sums by distributed-shared-memory reads;
- * it is latency-optimal for small m and limited to the cluster's SMs for large m, so 0
- * takes it when each CTA's rows of the basis fit in its shared memory (about 12,000 rows
- * at GMRES(30)).  Both give the same iterates up to rounding. */
+ * per cycle), 2 and 3 the whole restarted solve in ONE launch whose CTAs own the rows in
+ * blocks and meet at barriers instead of kernel boundaries: 2 on one thread-block cluster
+ * (16 CTAs, or 8; hardware barriers, partial sums read from the other CTAs' shared memory),
+ * 3 on one CTA per SM of the whole GPU (cooperative launch; partial sums through global
+ * memory; a software barrier whose wait is bounded: KC_ERR_TIMEOUT if a CTA waits longer
+ * than about a second).  0 takes 3 when each SM's rows of the basis fit in its shared
+ * memory (about 115,000 rows at GMRES(30)), else 1.  All give the same iterates up to
+ * rounding. */
 kc_status kc_set_gmres_path(kc_ctx* ctx, int path);
+/* Test hook for the bounded grid barrier of gmres_path 3: when on, the next such solve
+ * expects one arrival more than it has CTAs, so its first barrier cannot complete; every
+ * CTA gives up after about a second and the solve returns KC_ERR_TIMEOUT (no fault, the
+ * context stays usable).  The hook clears itself after that one solve. */
+kc_status kc_set_barrier_test(kc_ctx* ctx, int on);
 /* Number of SMs and the persistent grid size used for reductions. */
 kc_status kc_device_info(const kc_ctx* ctx, int* num_sms, int* reduce_grid);
 /* Number of kernels this context has launched since creation (host-side counter). */

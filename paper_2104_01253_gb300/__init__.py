@@ -58,11 +58,12 @@ class Context:
         """Kernel of the network's 32 -> 32 convolutions (CONV_MMA_SYNC or CONV_TCGEN05)."""
         self.check(self.lib.kc_set_conv_kernel(self.handle, int(kind)))
 
-    GMRES_AUTO, GMRES_MULTI_KERNEL, GMRES_CLUSTER = 0, 1, 2
+    GMRES_AUTO, GMRES_MULTI_KERNEL, GMRES_CLUSTER, GMRES_GRID = 0, 1, 2, 3
 
     def set_gmres_path(self, path: int):
-        """FP64 gmres_solve path: GMRES_AUTO (by size), GMRES_MULTI_KERNEL, or GMRES_CLUSTER
-        (the whole solve in one thread-block-cluster launch)."""
+        """FP64 gmres_solve path: GMRES_AUTO (by size), GMRES_MULTI_KERNEL, GMRES_CLUSTER
+        (the whole solve in one thread-block-cluster launch) or GMRES_GRID (one launch over
+        every SM with a bounded grid barrier)."""
         self.check(self.lib.kc_set_gmres_path(self.handle, int(path)))
 
     STAGED_UPDATE, STAGED_REDUCE = 1, 2

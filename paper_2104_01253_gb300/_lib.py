@@ -79,6 +79,7 @@ _SIGS = {
                      C.POINTER(kc_gmres_opts), C.POINTER(kc_gmres_info)], C.c_int),
     "kc_set_conv_kernel": ([_P, C.c_int], C.c_int),
     "kc_set_gmres_path": ([_P, C.c_int], C.c_int),
+    "kc_set_barrier_test": ([_P, C.c_int], C.c_int),
     "kc_cnn_param_count": ([], C.c_int64),
     "kc_cnn_forward": ([_P, _P, _P, _P, C.c_int, C.c_int, C.c_int], C.c_int),
     "kc_cnn_train_step": ([_P, _P, _P, _P, C.c_int64, C.c_float, _P, _P, C.c_int, C.c_int,

@@ -179,8 +179,14 @@ kc_status kc_set_conv_kernel(kc_ctx* ctx, int kind) {
 }
 
 kc_status kc_set_gmres_path(kc_ctx* ctx, int path) {
-  if (!ctx || path < 0 || path > 2) return KC_ERR_INVALID_ARG;
+  if (!ctx || path < 0 || path > 3) return KC_ERR_INVALID_ARG;
   ctx->gmres_path = path;
+  return KC_OK;
+}
+
+kc_status kc_set_barrier_test(kc_ctx* ctx, int on) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  ctx->barrier_test = on ? 1 : 0;
   return KC_OK;
 }
 

@@ -1,32 +1,37 @@
-// Restarted FP64 DCGS2-GMRES(n) for small problems in ONE thread-block cluster and ONE
-// launch per solve.
+// Restarted FP64 DCGS2-GMRES(n) for small problems in ONE launch per solve.
 //
 // At m = 10^4 (the 2D convection-diffusion problem of the GMRES benchmark) a DCGS2 step of
 // the multi-kernel path is three launches whose cost is latency, not bytes: the fused
 // reduction alone takes 12-30 us of partial sums, last-CTA ticket and serial scalar work
-// for 2.5 MB of basis.  Here the CTAs of one cluster (16, or 8 where 16 cannot be
-// scheduled) own contiguous row blocks of Q, w, v and x and run every phase of the solve
-// in place:
+// for 2.5 MB of basis.  Here one persistent kernel runs the whole solve; its CTAs own
+// contiguous row blocks of Q, v, w and x and run every phase in place:
 //   per Arnoldi step (Algorithm 4): v = A w on the CTA's rows; the partial sums of
-//   [Q_k, w]^T [w, v]; one cluster barrier; every CTA adds the partials of all CTAs in the
-//   same rank order (distributed shared memory), so every CTA holds bitwise the same C, S,
-//   beta, s and takes the same decisions; alpha by Pythagoras, T by Stephen's trick; the
-//   row-local update of q_k and w; CTA 0 alone forms the lagged H and K columns and
-//   rotates the finalised column (Givens, stop test); a second cluster barrier makes w
-//   (read across row blocks by the next matvec) and CTA 0's stop flag visible;
+//   [Q_k, w]^T [w, v]; one exchange; every CTA adds the partials of all CTAs in the same
+//   rank order, so every CTA holds bitwise the same C, S, beta, s and takes the same
+//   decisions; alpha by Pythagoras, T by Stephen's trick; the row-local update of q_k and
+//   w; CTA 0 alone forms the lagged H and K columns and rotates the finalised column
+//   (Givens, stop test); a barrier makes w (read across row blocks by the next matvec) and
+//   CTA 0's stop flag visible;
 //   per cycle: the CGS2 finish of the last column (two projections and a norm), the
 //   triangular solve y = R^{-1} g in CTA 0 (column-parallel back substitution), x += Q y,
 //   and the FP64 residual b - A x with its norm for the restart test.
-// Where they fit, a CTA keeps its rows of the basis, of v and of w in shared memory
-// (config 1: 625 rows x 31 columns, 155 KB; w is also written to global memory for the
-// other CTAs' matvecs) and CTA 0 keeps H, K, R there, so the step's dependent chains run at
-// shared-memory latency; otherwise the same code addresses them in global memory.  The
-// partial-sum buffers alternate between reductions, so one barrier per reduction is enough:
-// a CTA writes a buffer again only after the next reduction's barrier, which every CTA
-// reaches after it has read that buffer.  Vectors other CTAs write (w, x)
-// are read through L2 (ld.global.cg), never from a stale L1 line; a last barrier keeps
-// every CTA (and its shared memory) alive until all remote reads are done.  There are no
-// spin-waits: the cluster barriers are the hardware's.
+// Two ways to exchange, one kernel body (a policy template):
+//   cluster: one thread-block cluster of 16 CTAs (8 where 16 cannot be scheduled); the
+//     partials and CTA 0's published state are read from the other CTAs' shared memory
+//     (distributed shared memory) after a hardware cluster barrier;
+//   grid: one CTA per SM on the whole GPU, launched cooperatively (all CTAs resident); the
+//     partials go through global memory and the barrier is a counter and generation word
+//     in global memory whose spin is bounded (about a second), after which the kernel
+//     sets an error word, every CTA leaves the solve, and the call reports KC_ERR_TIMEOUT.
+// A CTA keeps its rows of the basis, of v and of w in shared memory where they fit (w is
+// also written to global memory for the other CTAs' matvecs) and CTA 0 keeps H, K, R
+// there, so the step's dependent chains run at shared-memory latency; otherwise the same
+// code addresses them in global memory.  The partial-sum buffers alternate between
+// reductions, so one barrier per reduction is enough: a CTA writes a buffer again only
+// after the next reduction's barrier, which every CTA reaches after it has read that
+// buffer.  Vectors other CTAs write (w, x) are read through L2 (ld.global.cg), never from a
+// stale L1 line; in the cluster form a last barrier keeps every CTA (and its shared memory)
+// alive until all remote reads are done.
 #include "kc_internal.cuh"
 
 #include <cooperative_groups.h>
@@ -39,6 +44,20 @@ constexpr int GC_THREADS = 1024;       // one thread per row at config 1 (625 ro
 constexpr int GC_WARPS = GC_THREADS / 32;
 constexpr int GC_PART = 2 * NMAX + 2;
 constexpr int GC_DYN_SMEM_MAX = 200 * 1024;   // dynamic shared memory the kernel may use
+constexpr long long GRID_WAIT_LIMIT = 2000000000LL;   // cycles (about 1 s) per barrier
+
+// CTA 0's state that every CTA reads after a barrier
+struct GcPub {
+  int stop, ncols;
+  double est;
+  double y[NMAX];
+};
+
+// grid barrier: arrivals, generation, error word (zeroed before the launch)
+struct GridBar {
+  unsigned int count, gen;
+  int err, pad;
+};
 
 struct GcArgs {
   // operator: CSR (stencil == 0) or the 7-point stencil
@@ -64,6 +83,11 @@ struct GcArgs {
   int smem_h;       // CTA 0 keeps H, K, R in shared memory
   double rtol;
   double* out;      // matvecs, cycles, est, rn, bnorm, result, last status
+  // grid form only
+  double* gpart;    // [2][grid][GC_PART] partial sums
+  GcPub* pub;       // CTA 0's published state
+  GridBar* bar;
+  int bar_extra;    // arrivals expected beyond the CTAs (test hook: > 0 makes a wait run out)
 };
 
 __device__ __forceinline__ double gc_warp_sum(double v) {
@@ -92,20 +116,6 @@ __device__ __forceinline__ double gc_apply_row(const GcArgs& a, const double* y,
   return s;
 }
 
-// Sum over the cluster of the nval partials each CTA left in `mine`, in rank order, into
-// `tot` (identical in every CTA).  Includes the cluster barrier; ends with __syncthreads.
-__device__ void gc_cluster_sum(cg::cluster_group& cl, double* mine, double* tot, int nval) {
-  __threadfence();
-  cl.sync();
-  const int nb = (int)cl.num_blocks();
-  for (int i = threadIdx.x; i < nval; i += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nb; c++) s += cl.map_shared_rank(mine, c)[i];
-    tot[i] = s;
-  }
-  __syncthreads();
-}
-
 // this thread's partial of a scalar sum -> part[0] of the CTA (fixed order)
 __device__ void gc_block_sum(double val, double* part, double* scratch) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -123,21 +133,123 @@ __device__ __forceinline__ void gc_set_status(int* st, int v) {
   if (*st == KC_OK) *st = v;
 }
 
-__global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t r0 = a.m * rank / nb, r1 = a.m * (rank + 1) / nb;
-  const int nrow = (int)(r1 - r0);
-  const int n = a.n, ldh = n + 1, ldk = n + 1, ldr = n;
+// ---- exchange policies ---------------------------------------------------------------------
+
+struct ClusterComm {
+  cg::cluster_group cl;
+  int rank, nb;
+  GcPub* pub_w;          // where CTA 0 writes its state (its shared memory)
+  const GcPub* pub_r;    // where every CTA reads it (CTA 0's shared memory, mapped)
+  __device__ ClusterComm(const GcArgs&, GcPub* s_pub) : cl(cg::this_cluster()) {
+    rank = (int)cl.block_rank();
+    nb = (int)cl.num_blocks();
+    pub_w = s_pub;
+    pub_r = cl.map_shared_rank(s_pub, 0);
+  }
+  __device__ bool sync() {
+    __threadfence();
+    cl.sync();
+    return true;
+  }
+  // every CTA: tot[i] = sum over ranks (in rank order) of their `mine`[i]
+  __device__ bool sum(double* mine, int, double* tot, int nval) {
+    sync();
+    for (int i = threadIdx.x; i < nval; i += blockDim.x) {
+      double s = 0.0;
+      for (int c = 0; c < nb; c++) s += cl.map_shared_rank(mine, c)[i];
+      tot[i] = s;
+    }
+    __syncthreads();
+    return true;
+  }
+  __device__ int ld(const int* p) const { return *(volatile const int*)p; }
+  __device__ double ld(const double* p) const { return *(volatile const double*)p; }
+  __device__ void finish() { cl.sync(); }   // no CTA exits while its shared memory may be read
+};
+
+struct GridComm {
+  int rank, nb;
+  GridBar* bar;
+  double* gpart;
+  GcPub* pub_w;
+  const GcPub* pub_r;
+  unsigned int arrivals;
+  __device__ GridComm(const GcArgs& a, GcPub*) {
+    rank = (int)blockIdx.x;
+    nb = (int)gridDim.x;
+    arrivals = (unsigned int)(nb + a.bar_extra);
+    bar = a.bar;
+    gpart = a.gpart;
+    pub_w = a.pub;
+    pub_r = a.pub;
+  }
+  // bounded barrier over the grid: false once any CTA has given up waiting.  Every thread
+  // fences its global writes before the CTA's arrival.
+  __device__ bool sync() {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int g = *(volatile unsigned int*)&bar->gen;
+      if (atomicAdd(&bar->count, 1u) == arrivals - 1u) {
+        atomicExch(&bar->count, 0u);
+        __threadfence();
+        atomicAdd(&bar->gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*(volatile unsigned int*)&bar->gen == g) {
+          if (clock64() - t0 > GRID_WAIT_LIMIT) {
+            atomicExch(&bar->err, 1);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)&bar->err == 0;
+  }
+  __device__ bool sum(double* mine, int buf, double* tot, int nval) {
+    double* my = gpart + ((int64_t)buf * nb + rank) * GC_PART;
+    __syncthreads();                         // every warp's partials are in `mine`
+    for (int i = threadIdx.x; i < nval; i += blockDim.x) my[i] = mine[i];
+    if (!sync()) return false;
+    // one warp per value: lanes add ranks lane, lane + 32, ... then a fixed shuffle tree,
+    // so the totals are bitwise the same in every CTA
+    const double* base = gpart + (int64_t)buf * nb * GC_PART;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < nval; i += (int)(blockDim.x >> 5)) {
+      double s = 0.0;
+      for (int c = lane; c < nb; c += 32) s += __ldcg(base + (int64_t)c * GC_PART + i);
+      s = gc_warp_sum(s);
+      if (lane == 0) tot[i] = s;
+    }
+    __syncthreads();
+    return true;
+  }
+  __device__ int ld(const int* p) const { return __ldcg(p); }
+  __device__ double ld(const double* p) const { return __ldcg(p); }
+  __device__ void finish() {}
+};
+
+// ---- the solve -----------------------------------------------------------------------------
+
+template <class Comm>
+__global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_fused(const GcArgs a) {
   extern __shared__ __align__(16) double gc_dyn[];
   __shared__ double part[2][GC_PART];
   __shared__ double tot[GC_PART];
   __shared__ double sC[NMAX], sC2[NMAX], sT[NMAX + 1], sy[NMAX];
   __shared__ double s_g[NMAX + 1], s_gc[NMAX], s_gs[NMAX];   // CTA 0: Givens state
   __shared__ double scratch[GC_WARPS];
-  __shared__ double s_alpha, s_inv_alpha, s_est;
-  __shared__ int s_status, s_stop, s_ncols;                   // CTA 0: cycle state
+  __shared__ double s_alpha, s_inv_alpha;
+  __shared__ int s_status;                                   // CTA 0: first failure of a cycle
+  __shared__ GcPub s_pub;                                    // cluster form: CTA 0's state
+  Comm comm(a, &s_pub);
+  const int rank = comm.rank, nb = comm.nb;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t r0 = a.m * rank / nb, r1 = a.m * (rank + 1) / nb;
+  const int nrow = (int)(r1 - r0);
+  const int n = a.n, ldh = n + 1, ldk = n + 1, ldr = n;
   // this CTA's rows of the basis (column j at Qb + j * qs, row r at index r - r0), of v
   // and of w, and CTA 0's H, K, R: in shared memory where they fit, else in global memory.
   // w is also kept in global memory (wg), where the other CTAs' matvecs read it.
@@ -151,37 +263,31 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
   double* const Hm = a.smem_h ? hb : a.H;
   double* const Km = a.smem_h ? hb + (n + 1) * n : a.K;
   double* const Rm = a.smem_h ? hb + 2 * (n + 1) * n : a.R;
+  GcPub* const pw = comm.pub_w;
+  const GcPub* const pr = comm.pub_r;
   int pb = 0;                             // partial-sum buffer of the next reduction
+  int matvecs = 0, cycles = 0, last_status = KC_OK, result = KC_ERR_NOT_CONVERGED;
+  double rn = 0.0, est = 0.0, bnorm = 0.0, target = 0.0;
 
   // ||b|| and the absolute tolerance
   {
     double acc = 0.0;
     for (int64_t r = r0 + tid; r < r1; r += GC_THREADS) acc += a.b[r] * a.b[r];
     gc_block_sum(acc, part[pb], scratch);
-    gc_cluster_sum(cl, part[pb], tot, 1);
+    if (!comm.sum(part[pb], pb, tot, 1)) goto failed;
     pb ^= 1;
   }
-  const double bnorm = sqrt(tot[0]);
+  bnorm = sqrt(tot[0]);
   if (!(bnorm > 0.0)) {
     for (int64_t r = r0 + tid; r < r1; r += GC_THREADS) a.x[r] = 0.0;
-    if (rank == 0 && tid == 0) {
-      a.out[0] = 0; a.out[1] = 0; a.out[2] = 0.0; a.out[3] = 0.0; a.out[4] = 0.0;
-      a.out[5] = KC_OK; a.out[6] = KC_OK;
-    }
-    cl.sync();                              // no CTA exits while its partials may be read
-    return;
+    result = KC_OK;
+    goto done;
   }
-  const double target = a.rtol * bnorm;
-  int matvecs = 0, cycles = 0, last_status = KC_OK, result = KC_ERR_NOT_CONVERGED;
-  double rn = 0.0, est = 0.0;
-  const int* stop0 = cl.map_shared_rank(&s_stop, 0);
-  const int* ncols0 = cl.map_shared_rank(&s_ncols, 0);
-  const double* est0 = cl.map_shared_rank(&s_est, 0);
+  target = a.rtol * bnorm;
 
   for (;;) {
     // ---- FP64 residual w = r = b - A x and its norm (x is written by every CTA) ----
-    __threadfence();
-    cl.sync();
+    if (!comm.sync()) goto failed;
     {
       double acc = 0.0;
       for (int i = tid; i < nrow; i += GC_THREADS) {
@@ -191,7 +297,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
         acc += rr * rr;
       }
       gc_block_sum(acc, part[pb], scratch);
-      gc_cluster_sum(cl, part[pb], tot, 1);
+      if (!comm.sum(part[pb], pb, tot, 1)) goto failed;
       pb ^= 1;
     }
     rn = sqrt(tot[0]);
@@ -200,9 +306,9 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
 
     // ---- one GMRES(n) cycle ----
     if (rank == 0 && tid == 0) {
-      s_stop = 0;
-      s_ncols = 0;
-      s_est = 0.0;
+      pw->stop = 0;
+      pw->ncols = 0;
+      pw->est = 0.0;
       s_status = KC_OK;
     }
     bool stopped = false;
@@ -226,7 +332,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
           part[pb][2 * t + 1] = s1;
         }
       }
-      gc_cluster_sum(cl, part[pb], tot, 2 * k + 2);
+      if (!comm.sum(part[pb], pb, tot, 2 * k + 2)) goto failed;
       pb ^= 1;
       // scalar step (every CTA): Pythagoras (Alg. 4 line 4), T (lines 5-6, eq. 30)
       if (warp == 0) {
@@ -291,9 +397,10 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
             if (lane == 0 && alpha <= 1e-13 * sqrt(cn)) gc_set_status(&s_status, KC_ERR_BREAKDOWN);
           }
           if (tid == 32) {                  // Givens rotation of the finalised column k-1
-            s_est = givens_rotate(s_gc, s_gs, s_g, Hm, ldh, k - 1, Rm, ldr);
-            s_ncols = k;
-            if (!(s_est > target)) s_stop = 1;
+            const double e = givens_rotate(s_gc, s_gs, s_g, Hm, ldh, k - 1, Rm, ldr);
+            pw->est = e;
+            pw->ncols = k;
+            if (!(e > target)) pw->stop = 1;
           }
         } else if (tid == 0) {
           s_g[0] = alpha;
@@ -305,9 +412,8 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
         }
       }
       // w and CTA 0's stop flag become visible to every CTA
-      __threadfence();
-      cl.sync();
-      if (*stop0) { stopped = true; break; }
+      if (!comm.sync()) goto failed;
+      if (comm.ld(&pr->stop)) { stopped = true; break; }
     }
     if (!stopped) {
       // CGS2 finish of the last column: C1 = Q^T w, w -= Q C1, C2 = Q^T w, w -= Q C2,
@@ -321,7 +427,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
           s0 = gc_warp_sum(s0);
           if (lane == 0) part[pb][t] = s0;
         }
-        gc_cluster_sum(cl, part[pb], tot, ntask + 1);
+        if (!comm.sum(part[pb], pb, tot, ntask + 1)) goto failed;
         pb ^= 1;
         if (pass == 2) break;
         double* cdst = pass == 0 ? sC : sC2;
@@ -350,16 +456,18 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
           if (lane == 0 && alpha <= 1e-13 * sqrt(cn)) gc_set_status(&s_status, KC_ERR_BREAKDOWN);
         }
         if (tid == 32) {
-          s_est = givens_rotate(s_gc, s_gs, s_g, Hm, ldh, n - 1, Rm, ldr);
-          s_ncols = n;
-          if (!(s_est > target)) s_stop = 1;
+          const double e = givens_rotate(s_gc, s_gs, s_g, Hm, ldh, n - 1, Rm, ldr);
+          pw->est = e;
+          pw->ncols = n;
+          if (!(e > target)) pw->stop = 1;
         }
       }
     }
-    // y = R^{-1} g in CTA 0 (column-oriented back substitution), then x += Q y everywhere
+    // y = R^{-1} g in CTA 0 (column-oriented back substitution), published with the
+    // column count; then x += Q y everywhere
     if (rank == 0) {
       __syncthreads();
-      const int nc = s_ncols;
+      const int nc = pw->ncols;
       for (int i = tid; i < nc; i += GC_THREADS) sy[i] = s_g[i];
       for (int j = nc - 1; j >= 0; j--) {
         __syncthreads();
@@ -368,26 +476,32 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
         const double yj = sy[j];
         for (int i = tid; i < j; i += GC_THREADS) sy[i] -= Rm[i + (int64_t)j * ldr] * yj;
       }
+      __syncthreads();
+      for (int i = tid; i < nc; i += GC_THREADS) pw->y[i] = sy[i];
     }
-    __threadfence();
-    cl.sync();
-    const int nc = *ncols0;                 // columns finalised in this cycle
-    const double* y0 = cl.map_shared_rank(sy, 0);
-    double* yl = sT;                        // local copy of y (T is not needed any more)
-    for (int i = tid; i < nc; i += GC_THREADS) yl[i] = y0[i];
-    __syncthreads();
-    for (int i = tid; i < nrow; i += GC_THREADS) {
-      double s = 0.0;
-      for (int j = 0; j < nc; j++) s += Qb[(int64_t)j * qs + i] * yl[j];
-      a.x[r0 + i] += s;
+    if (!comm.sync()) goto failed;
+    {
+      const int nc = comm.ld(&pr->ncols);   // columns finalised in this cycle
+      double* yl = sT;                      // local copy of y (T is not needed any more)
+      for (int i = tid; i < nc; i += GC_THREADS) yl[i] = comm.ld(&pr->y[i]);
+      __syncthreads();
+      for (int i = tid; i < nrow; i += GC_THREADS) {
+        double s = 0.0;
+        for (int j = 0; j < nc; j++) s += Qb[(int64_t)j * qs + i] * yl[j];
+        a.x[r0 + i] += s;
+      }
+      const int stop_flag = comm.ld(&pr->stop);
+      matvecs += (stop_flag && nc < n) ? nc + 1 : n;
+      cycles++;
+      est = comm.ld(&pr->est);
+      if (rank == 0 && s_status != KC_OK && s_status != KC_ERR_BREAKDOWN) last_status = s_status;
     }
-    const int stop_flag = *stop0;
-    matvecs += (stop_flag && nc < n) ? nc + 1 : n;
-    cycles++;
-    est = *est0;
-    if (rank == 0 && s_status != KC_OK && s_status != KC_ERR_BREAKDOWN) last_status = s_status;
   }
-  cl.sync();                                // no CTA exits while its shared memory may be read
+  goto done;
+failed:
+  result = KC_ERR_TIMEOUT;
+done:
+  comm.finish();
   if (rank == 0 && tid == 0) {
     a.out[0] = matvecs;
     a.out[1] = cycles;
@@ -398,6 +512,8 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_cluster(const GcArgs a)
     a.out[6] = last_status;
   }
 }
+
+// ---- launch --------------------------------------------------------------------------------
 
 // cluster size the device can schedule for the kernel with `smem` bytes of dynamic shared
 // memory (16, else 8; 0 if neither)
@@ -415,7 +531,8 @@ static int gmres_cluster_size(int smem) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_gmres_cluster, &cfg) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_gmres_fused<ClusterComm>, &cfg) ==
+            cudaSuccess &&
         nclusters >= 1)
       return cs;
     cudaGetLastError();
@@ -423,13 +540,16 @@ static int gmres_cluster_size(int smem) {
   return 0;
 }
 
-static void gmres_cluster_probe(kc_ctx* ctx) {
+static void gmres_fused_setup(kc_ctx* ctx) {
   static std::atomic<unsigned long long> attr_done{0};
   const unsigned long long bit = 1ull << (ctx->device & 63);
   if (!(attr_done.load(std::memory_order_acquire) & bit)) {
-    cudaFuncSetAttribute(k_gmres_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(k_gmres_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         GC_DYN_SMEM_MAX);
+    cudaFuncSetAttribute(k_gmres_fused<ClusterComm>,
+                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_gmres_fused<ClusterComm>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, GC_DYN_SMEM_MAX);
+    cudaFuncSetAttribute(k_gmres_fused<GridComm>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, GC_DYN_SMEM_MAX);
     cudaGetLastError();
     attr_done.fetch_or(bit, std::memory_order_release);
   }
@@ -440,23 +560,44 @@ static void gmres_cluster_probe(kc_ctx* ctx) {
 }
 
 // shared-memory bytes of a CTA's rows of Q (n+1 columns), v and w
-static int64_t gmres_cluster_row_bytes(int64_t m, int n, int cs) {
-  return (int64_t)(n + 3) * ((m + cs - 1) / cs) * 8;
+static int64_t gmres_fused_row_bytes(int64_t m, int n, int ctas) {
+  return (int64_t)(n + 3) * ((m + ctas - 1) / ctas) * 8;
 }
 
-bool gmres_cluster_preferred(kc_ctx* ctx, int64_t m, int n) {
-  gmres_cluster_probe(ctx);
-  return ctx->gmres_cluster > 0 &&
-         gmres_cluster_row_bytes(m, n, ctx->gmres_cluster) <= GC_DYN_SMEM_MAX;
+bool gmres_grid_preferred(kc_ctx* ctx, int64_t m, int n) {
+  gmres_fused_setup(ctx);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_fused<GridComm>, GC_THREADS,
+                                                    GC_DYN_SMEM_MAX) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return occ >= 1 && gmres_fused_row_bytes(m, n, ctx->num_sms) <= GC_DYN_SMEM_MAX;
 }
 
-kc_status gmres_cluster_solve(kc_ctx* ctx, const kc_csr* A, const double* b, double* x,
-                              double* Q, int64_t ldq, double* w, double* v, double* H,
-                              double* K, double* R, int n, int maxit, double rtol,
-                              double* out_dev, double* out_host) {
-  gmres_cluster_probe(ctx);
-  const int cs = ctx->gmres_cluster;
-  if (cs < 0) return fail(ctx, KC_ERR_CUDA, "gmres: no thread-block cluster can be scheduled");
+size_t gmres_grid_workspace(const kc_ctx* ctx) {
+  return (size_t)2 * ctx->num_sms * GC_PART * sizeof(double) + sizeof(GcPub) + sizeof(GridBar);
+}
+
+kc_status gmres_fused_solve(kc_ctx* ctx, int grid_form, const kc_csr* A, const double* b,
+                            double* x, double* Q, int64_t ldq, double* w, double* v, double* H,
+                            double* K, double* R, int n, int maxit, double rtol,
+                            void* grid_ws, double* out_dev, double* out_host) {
+  gmres_fused_setup(ctx);
+  int ctas;
+  if (grid_form) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gmres_fused<GridComm>,
+                                                      GC_THREADS, GC_DYN_SMEM_MAX) !=
+            cudaSuccess ||
+        occ < 1)
+      return fail(ctx, KC_ERR_CUDA, "gmres: the grid-wide kernel cannot be resident");
+    ctas = ctx->num_sms;
+  } else {
+    if (ctx->gmres_cluster < 0)
+      return fail(ctx, KC_ERR_CUDA, "gmres: no thread-block cluster can be scheduled");
+    ctas = ctx->gmres_cluster;
+  }
   GcArgs a = {};
   if (is_stencil(A)) {
     a.stencil = 1;
@@ -472,27 +613,39 @@ kc_status gmres_cluster_solve(kc_ctx* ctx, const kc_csr* A, const double* b, dou
   a.b = b; a.x = x; a.Q = Q; a.ldq = ldq; a.w = w; a.v = v; a.H = H; a.K = K; a.R = R;
   a.n = n; a.maxit = maxit; a.m = A->m; a.rtol = rtol; a.out = out_dev;
   // shared-memory residency: rows of Q, v and w per CTA, then CTA 0's H, K, R
-  const int64_t rc = (A->m + cs - 1) / cs;
-  const int64_t bq = gmres_cluster_row_bytes(A->m, n, cs);
+  const int64_t bq = gmres_fused_row_bytes(A->m, n, ctas);
   const int64_t bh = (int64_t)(2 * (n + 1) * n + n * n) * 8;
-  a.rc = (int)rc;
+  a.rc = (int)((A->m + ctas - 1) / ctas);
   a.smem_q = bq <= GC_DYN_SMEM_MAX;
   a.smem_h = (a.smem_q ? bq : 0) + bh <= GC_DYN_SMEM_MAX;
   const int64_t dyn = (a.smem_q ? bq : 0) + (a.smem_h ? bh : 0);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cs, 1, 1);
-  cfg.blockDim = dim3(GC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = (size_t)dyn;
-  cfg.stream = ctx->stream;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cs;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
+  a.bar_extra = ctx->barrier_test ? 1 : 0;
+  ctx->barrier_test = 0;
   timing_begin(ctx, KID_OTHER);
-  KC_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_gmres_cluster, a));
+  if (grid_form) {
+    char* g = (char*)grid_ws;
+    a.gpart = (double*)g;
+    a.pub = (GcPub*)(g + (size_t)2 * ctas * GC_PART * sizeof(double));
+    a.bar = (GridBar*)((char*)a.pub + sizeof(GcPub));
+    KC_CUDA(ctx, cudaMemsetAsync(a.bar, 0, sizeof(GridBar), ctx->stream));
+    void* args[] = {(void*)&a};
+    KC_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_gmres_fused<GridComm>, dim3(ctas),
+                                             dim3(GC_THREADS), args, (size_t)dyn, ctx->stream));
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas, 1, 1);
+    cfg.blockDim = dim3(GC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)dyn;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ctas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    KC_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_gmres_fused<ClusterComm>, a));
+  }
   KC_LAUNCHED(ctx);
   KC_CUDA(ctx, cudaMemcpyAsync(out_host, out_dev, 7 * sizeof(double), cudaMemcpyDeviceToHost,
                                ctx->stream));

@@ -142,8 +142,9 @@ struct kc_ctx {
   int fp64_mode;           // 0: every product in FP64; 1: FP64 with float-float offload
   int staged;              // bit 0: staged FP64 update; bit 1: tensor-copy staged reduction
   int conv_tc;             // 32 -> 32 convolutions: 0 mma.sync, 1 tcgen05 (tensor memory)
-  int gmres_path;          // FP64 gmres_solve: 0 auto, 1 multi-kernel, 2 one-cluster kernel
+  int gmres_path;          // FP64 gmres_solve: 0 auto, 1 multi-kernel, 2 cluster, 3 grid
   int gmres_cluster;       // its cluster size once probed (0: not yet, -1: none schedulable)
+  int barrier_test;        // test hook: the next grid-form solve's first barrier times out
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
   kc::TimingRec* trec;
@@ -243,16 +244,18 @@ kc_status cnn_adam(kc_ctx* ctx, float* w, const float* g, float* m, float* v, in
 int64_t cnn_nparam();
 // the operator is the matrix-free 7-point stencil rather than a CSR matrix
 inline bool is_stencil(const kc_csr* A) { return A->grid[0] > 0; }
-// restarted FP64 DCGS2-GMRES in one thread-block cluster (kc_gmres_cluster.cu); writes
-// out_host[0..6] = matvecs, cycles, |g| estimate, ||b - A x||, ||b||, result, last status
-kc_status gmres_cluster_solve(kc_ctx* ctx, const kc_csr* A, const double* b, double* x,
-                              double* Q, int64_t ldq, double* w, double* v, double* H,
-                              double* K, double* R, int n, int maxit, double rtol,
-                              double* out_dev, double* out_host);
-// gmres_path 0 takes the one-cluster kernel when each CTA's rows of the basis, v and w fit
-// in its shared memory (about 12k rows at GMRES(30)): beyond that its 16 SMs of FP64 lose
-// to the whole GPU
-bool gmres_cluster_preferred(kc_ctx* ctx, int64_t m, int n);
+// restarted FP64 DCGS2-GMRES in one launch (kc_gmres_cluster.cu): one thread-block
+// cluster (grid_form 0) or one CTA per SM with a bounded grid barrier (grid_form 1, needs
+// gmres_grid_workspace bytes at grid_ws); writes out_host[0..6] = matvecs, cycles, |g|
+// estimate, ||b - A x||, ||b||, result, last status
+kc_status gmres_fused_solve(kc_ctx* ctx, int grid_form, const kc_csr* A, const double* b,
+                            double* x, double* Q, int64_t ldq, double* w, double* v, double* H,
+                            double* K, double* R, int n, int maxit, double rtol,
+                            void* grid_ws, double* out_dev, double* out_host);
+size_t gmres_grid_workspace(const kc_ctx* ctx);
+// gmres_path 0 takes the one-launch grid kernel when each SM's rows of the basis, v and w
+// fit in its shared memory (about 115k rows at GMRES(30)); the multi-kernel path otherwise
+bool gmres_grid_preferred(kc_ctx* ctx, int64_t m, int n);
 kc_status validate_csr(kc_ctx* ctx, const kc_csr* A);
 // validate_csr, and A must be a CSR matrix (for callers that read its entries)
 kc_status validate_csr_entries(kc_ctx* ctx, const kc_csr* A);

@@ -233,6 +233,7 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   const size_t od = off; off = align256(off + (size_t)ldq * 4);
   const size_t orhs = off; off = align256(off + (size_t)ldq * 4);
   const size_t oout = off; off = align256(off + 8 * sizeof(double));
+  const size_t ogrid = off; off = align256(off + gmres_grid_workspace(ctx));
   if ((s = ensure_workspace(ctx, off)) != KC_OK) return s;
   char* ws = (char*)ctx->ws;
   Cycle c;
@@ -246,14 +247,14 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   KC_CUDA(ctx, cudaMemsetAsync(c.H, 0, (size_t)(n + 1) * n * 8, ctx->stream));
   KC_CUDA(ctx, cudaMemsetAsync(c.K, 0, (size_t)(n + 1) * n * 8, ctx->stream));
 
-  // small FP64 problems: the whole solve in one thread-block cluster (one launch)
-  const bool cluster = prec == 0 && (ctx->gmres_path == 2 ||
-                                     (ctx->gmres_path == 0 && gmres_cluster_preferred(ctx, m, n)));
-  if (cluster) {
+  // small FP64 problems: the whole solve in one launch (one cluster, or the whole grid)
+  const int path = prec != 0 ? 1 : (ctx->gmres_path != 0 ? ctx->gmres_path
+                                    : (gmres_grid_preferred(ctx, m, n) ? 3 : 1));
+  if (path >= 2) {
     double out[7];
-    if ((s = gmres_cluster_solve(ctx, A, b, x, (double*)c.Q, ldq, (double*)c.w, (double*)c.v,
-                                 c.H, c.K, c.R, n, opts->maxit, opts->rtol,
-                                 (double*)(ws + oout), out)) != KC_OK)
+    if ((s = gmres_fused_solve(ctx, path == 3, A, b, x, (double*)c.Q, ldq, (double*)c.w,
+                               (double*)c.v, c.H, c.K, c.R, n, opts->maxit, opts->rtol,
+                               ws + ogrid, (double*)(ws + oout), out)) != KC_OK)
       return s;
     const double bn = out[4];
     info->iters = (int)out[0];

@@ -27,7 +27,7 @@ def ctx(kc):
     return kc.Context(0)
 
 
-PATHS = [1, 2]     # Context.GMRES_MULTI_KERNEL, Context.GMRES_CLUSTER
+PATHS = [1, 2, 3]  # Context.GMRES_MULTI_KERNEL, GMRES_CLUSTER, GMRES_GRID
 
 
 @pytest.fixture
@@ -112,15 +112,16 @@ def test_iterative_refinement_reaches_fp64_accuracy(kc, ctx, precision, basis):
                                   lambda: convdiff_csr(10, 3, [3.0, 1.0, 0.5]),   # m = 1000
                                   lambda: convdiff_csr(50, 3, [50.0, 25.0, 12.5])])  # m = 125000
 def test_cluster_path_matches_multi_kernel_path(kc, ctx, make):
-    """The one-cluster solve (ragged row blocks, up to the auto threshold's size) takes the
-    same iterations as the multi-kernel path, and both reach a true residual of 1e-10."""
+    """The one-launch solves (one cluster, one CTA per SM; ragged row blocks, the basis in
+    shared or global memory) take the same iterations as the multi-kernel path, and all
+    reach a true residual of 1e-10."""
     Ah = make()
     b = gaussian_vector(Ah.m, 77)
     A = kc.DeviceCSR(Ah)
     bd = torch.as_tensor(b, device="cuda")
     out = {}
     try:
-        for p in (1, 2):
+        for p in (1, 2, 3):
             ctx.set_gmres_path(p)
             x = torch.zeros_like(bd)
             info = kc.gmres_solve(ctx, A, bd, x, restart=30, rtol=1e-10)
@@ -131,10 +132,11 @@ def test_cluster_path_matches_multi_kernel_path(kc, ctx, make):
             out[p] = (info, xg)
     finally:
         ctx.set_gmres_path(0)
-    assert abs(out[1][0]["iters"] - out[2][0]["iters"]) <= 1
-    assert out[1][0]["restarts"] == out[2][0]["restarts"]
-    x1, x2 = out[1][1], out[2][1]
-    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) <= 1e-6
+    for p in (2, 3):
+        assert abs(out[1][0]["iters"] - out[p][0]["iters"]) <= 1
+        assert out[1][0]["restarts"] == out[p][0]["restarts"]
+        x1, xp = out[1][1], out[p][1]
+        assert np.linalg.norm(x1 - xp) / np.linalg.norm(x1) <= 1e-6
 
 
 def test_cluster_path_on_stencil_operator(kc, ctx):
@@ -171,3 +173,24 @@ def test_iteration_cap_and_zero_rhs(kc, ctx, path):
     info = kc.gmres_solve(ctx, A, z, x, restart=30, rtol=1e-10)
     assert info["status"] == 0 and info["iters"] == 0
     assert torch.count_nonzero(x).item() == 0
+
+
+def test_grid_barrier_wait_is_bounded(kc, ctx):
+    """Failure detection without a GPU fault: the test hook makes the grid form's first
+    barrier wait for an arrival that never comes; every CTA gives up after about a second,
+    the solve reports KC_ERR_TIMEOUT (7), and the next solve on the context succeeds."""
+    Ah = config1_operator()
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(gaussian_vector(Ah.m, 1001), device="cuda")
+    x = torch.zeros_like(bd)
+    ctx.set_gmres_path(3)
+    try:
+        assert ctx.lib.kc_set_barrier_test(ctx.handle, 1) == 0
+        with pytest.raises(kc.KrylovError) as e:
+            kc.gmres_solve(ctx, A, bd, x, restart=30, rtol=1e-10)
+        assert e.value.status == 7
+        x.zero_()
+        info = kc.gmres_solve(ctx, A, bd, x, restart=30, rtol=1e-10)
+        assert info["status"] == 0 and info["rel_resid_true"] <= 1e-10
+    finally:
+        ctx.set_gmres_path(0)
