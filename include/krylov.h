@@ -141,9 +141,8 @@ kc_status kc_set_conv_kernel(kc_ctx* ctx, int kind);
  * (16 CTAs, or 8; hardware barriers, partial sums read from the other CTAs' shared memory),
  * 3 on one CTA per SM of the whole GPU (cooperative launch; partial sums through global
  * memory; a software barrier whose wait is bounded: KC_ERR_TIMEOUT if a CTA waits longer
- * than about a second).  0 takes 3 when each SM's rows of the basis fit in its shared
- * memory (about 115,000 rows at GMRES(30)), else 1.  All give the same iterates up to
- * rounding. */
+ * than about a second).  0 takes 3 up to m = 393,216 rows (where it was measured faster
+ * than 1), else 1.  All give the same iterates up to rounding. */
 kc_status kc_set_gmres_path(kc_ctx* ctx, int path);
 /* Test hook for the bounded grid barrier of gmres_path 3: when on, the next such solve
  * expects one arrival more than it has CTAs, so its first barrier cannot complete; every

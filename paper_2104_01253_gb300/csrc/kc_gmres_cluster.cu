@@ -45,6 +45,10 @@ constexpr int GC_WARPS = GC_THREADS / 32;
 constexpr int GC_PART = 2 * NMAX + 2;
 constexpr int GC_DYN_SMEM_MAX = 200 * 1024;   // dynamic shared memory the kernel may use
 constexpr long long GRID_WAIT_LIMIT = 2000000000LL;   // cycles (about 1 s) per barrier
+// rows up to which the default takes the grid form: GMRES(30) to 1e-10 on 2D problems took
+// 113.8 vs 176.7 ms (m = 65,536), 763 vs 945 ms (m = 262,144) against the multi-kernel
+// path, and 9.24 vs 7.50 s at m = 1,048,576, where the basis streams from HBM
+constexpr int64_t GMRES_GRID_MAX_ROWS = 393216;
 
 // CTA 0's state that every CTA reads after a barrier
 struct GcPub {
@@ -572,7 +576,8 @@ bool gmres_grid_preferred(kc_ctx* ctx, int64_t m, int n) {
     cudaGetLastError();
     return false;
   }
-  return occ >= 1 && gmres_fused_row_bytes(m, n, ctx->num_sms) <= GC_DYN_SMEM_MAX;
+  (void)n;
+  return occ >= 1 && m <= GMRES_GRID_MAX_ROWS;
 }
 
 size_t gmres_grid_workspace(const kc_ctx* ctx) {

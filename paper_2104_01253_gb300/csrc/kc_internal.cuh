@@ -253,8 +253,8 @@ kc_status gmres_fused_solve(kc_ctx* ctx, int grid_form, const kc_csr* A, const d
                             double* K, double* R, int n, int maxit, double rtol,
                             void* grid_ws, double* out_dev, double* out_host);
 size_t gmres_grid_workspace(const kc_ctx* ctx);
-// gmres_path 0 takes the one-launch grid kernel when each SM's rows of the basis, v and w
-// fit in its shared memory (about 115k rows at GMRES(30)); the multi-kernel path otherwise
+// gmres_path 0 takes the one-launch grid kernel up to 393,216 rows (measured crossover with
+// the multi-kernel path), the multi-kernel path beyond
 bool gmres_grid_preferred(kc_ctx* ctx, int64_t m, int n);
 kc_status validate_csr(kc_ctx* ctx, const kc_csr* A);
 // validate_csr, and A must be a CSR matrix (for callers that read its entries)
