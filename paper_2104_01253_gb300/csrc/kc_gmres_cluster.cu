@@ -92,6 +92,7 @@ struct GcArgs {
   GcPub* pub;       // CTA 0's published state
   GridBar* bar;
   int bar_extra;    // arrivals expected beyond the CTAs (test hook: > 0 makes a wait run out)
+  int skip0;        // CTA 0 owns no rows (grid form: its serial work overlaps the others')
 };
 
 __device__ __forceinline__ double gc_warp_sum(double v) {
@@ -160,6 +161,7 @@ struct ClusterComm {
     sync();
     for (int i = threadIdx.x; i < nval; i += blockDim.x) {
       double s = 0.0;
+#pragma unroll 16
       for (int c = 0; c < nb; c++) s += cl.map_shared_rank(mine, c)[i];
       tot[i] = s;
     }
@@ -223,6 +225,7 @@ struct GridComm {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = warp; i < nval; i += (int)(blockDim.x >> 5)) {
       double s = 0.0;
+#pragma unroll 8
       for (int c = lane; c < nb; c += 32) s += __ldcg(base + (int64_t)c * GC_PART + i);
       s = gc_warp_sum(s);
       if (lane == 0) tot[i] = s;
@@ -251,7 +254,10 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_fused(const GcArgs a) {
   Comm comm(a, &s_pub);
   const int rank = comm.rank, nb = comm.nb;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t r0 = a.m * rank / nb, r1 = a.m * (rank + 1) / nb;
+  // row block of this CTA: the CTAs that own rows split them evenly (with skip0, CTA 0
+  // owns none and its H, K, Givens work runs while the others compute)
+  const int nrb = a.skip0 ? nb - 1 : nb, rr = a.skip0 ? rank - 1 : rank;
+  const int64_t r0 = rr < 0 ? 0 : a.m * rr / nrb, r1 = rr < 0 ? 0 : a.m * (rr + 1) / nrb;
   const int nrow = (int)(r1 - r0);
   const int n = a.n, ldh = n + 1, ldk = n + 1, ldr = n;
   // this CTA's rows of the basis (column j at Qb + j * qs, row r at index r - r0), of v
@@ -618,9 +624,11 @@ kc_status gmres_fused_solve(kc_ctx* ctx, int grid_form, const kc_csr* A, const d
   a.b = b; a.x = x; a.Q = Q; a.ldq = ldq; a.w = w; a.v = v; a.H = H; a.K = K; a.R = R;
   a.n = n; a.maxit = maxit; a.m = A->m; a.rtol = rtol; a.out = out_dev;
   // shared-memory residency: rows of Q, v and w per CTA, then CTA 0's H, K, R
-  const int64_t bq = gmres_fused_row_bytes(A->m, n, ctas);
+  a.skip0 = grid_form && ctas >= 2 ? 1 : 0;
+  const int row_ctas = ctas - a.skip0;
+  const int64_t bq = gmres_fused_row_bytes(A->m, n, row_ctas);
   const int64_t bh = (int64_t)(2 * (n + 1) * n + n * n) * 8;
-  a.rc = (int)((A->m + ctas - 1) / ctas);
+  a.rc = (int)((A->m + row_ctas - 1) / row_ctas);
   a.smem_q = bq <= GC_DYN_SMEM_MAX;
   a.smem_h = (a.smem_q ? bq : 0) + bh <= GC_DYN_SMEM_MAX;
   const int64_t dyn = (a.smem_q ? bq : 0) + (a.smem_h ? bh : 0);
