@@ -253,8 +253,31 @@ def solver_suite(kc, ctx, A, m, stream):
             inner_max_cycles=3))
     del A32
     out.update(qr_suite(kc, ctx, m, stream))
+    out.update(ks_suite(kc, ctx, timed_solve))
     out.update(learned_suite(kc, ctx, timed_solve))
     return out
+
+
+def ks_suite(kc, ctx, timed_solve):
+    """Krylov-Schur on config 3 (2D, N = 1000, m = 10^6, kappa i.i.d. log-uniform on
+    [0.1, 10], seed 1003; start vector seed 1003): the 10 eigenvalues of largest real part
+    with 40-column expansions restarted to 20, to a relative Ritz residual of 1e-10 (the
+    eigenvalues themselves are checked against dense eigenvalues on the 40 x 40 copy by
+    the tests).  Time by CUDA events around the C-ABI call, after a one-restart warm-up."""
+    import torch
+    from synth import config3_operator
+    A3h = config3_operator()
+    A3 = kc.DeviceCSR(A3h)
+    v0 = torch.as_tensor(gaussian_vector(A3h.m, 1003), device="cuda")
+    del A3h
+    kc.krylov_schur_eigs(ctx, A3, v0, nev=10, ncv=40, nkeep=20, tol=1e-10, maxrestarts=1)
+    res = timed_solve(lambda: kc.krylov_schur_eigs(ctx, A3, v0, nev=10, ncv=40, nkeep=20,
+                                                   tol=1e-10, maxrestarts=2000))
+    eigs = res.pop("eigs")
+    resid = res.pop("resid")
+    res["max_rel_ritz_residual"] = float(np.max(resid / np.maximum(np.abs(eigs), 1e-300)))
+    res["eigs_largest_real"] = [[float(z.real), float(z.imag)] for z in eigs]
+    return {"config3_krylov_schur_nev10_ncv40": res}
 
 
 def qr_suite(kc, ctx, m, stream, n=50, reps=3):
