@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_fused(const GcArgs a) {
   int pb = 0;                             // partial-sum buffer of the next reduction
   int matvecs = 0, cycles = 0, last_status = KC_OK, result = KC_ERR_NOT_CONVERGED;
   double rn = 0.0, est = 0.0, bnorm = 0.0, target = 0.0;
+  // H below its subdiagonal is never written but is read by the K-column product
+  // (line 11 over the full H(0:k, 0:k-1)): zero it (the global copy is zeroed by the host)
+  if (rank == 0 && a.smem_h)
+    for (int i = tid; i < (n + 1) * n; i += GC_THREADS) Hm[i] = 0.0;
 
   // ||b|| and the absolute tolerance
   {
