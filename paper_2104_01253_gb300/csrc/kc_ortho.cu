@@ -514,9 +514,9 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // Offloaded reduction, task layout.  ntask = k + 2 tasks of equal FP64 cost (two FP64
 // FMAs per group of two rows): task t < k is column t (C_t = q_t^T w in FP64 and
 // S_t = q_t^T v in float-float), task k is beta = w^T w and task k + 1 is s = w^T v, both
-// in FP64.  The tasks are cut into nsplit subsets of at most 32 (nt each); the grid is
+// in FP64.  The tasks are cut into nsplit subsets of at most 48 (nt each); the grid is
 // nsplit CTAs per row block, CTA (row block r, subset h) has nw = ceil(nt / TPW) warps and
-// warp w takes the subset's tasks w, w + nw, ... (TPW slots, TPW <= 2), so at most TPW - 1
+// warp w takes the subset's tasks w, w + nw, ... (TPW slots, TPW <= 3), so at most TPW - 1
 // slots of a CTA are idle and every CTA has at most 16 warps (two or more CTAs per SM
 // with 64 registers).  All warps of a CTA walk the same rows; w and v come from L1 after
 // the first warp has loaded them (and from L2 for the other subsets of the row block).
@@ -1070,8 +1070,10 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     if (st != KC_OK) return st;
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
       ctx->fp64_mode == 1) {
-    // Task layout: nsplit = ceil(ntask / 32) subsets of nt tasks, CTAs of nw <= 16 warps
-    // with tpw <= 2 slots, tpw chosen (once per k) to maximise resident warps x used slots.
+    // Task layout: nsplit subsets of nt tasks (ceil(ntask / 48) <= nsplit <= ceil(ntask /
+    // 32)), CTAs of nw <= 16 warps with tpw <= 3 slots, chosen once per k to maximise
+    // resident warps x used slots; three slots (one row group per iteration, which fits 64
+    // registers) keep up to 48 tasks in one subset, so w and v are read once per row block.
     // (Three subsets and more, or more subsets than needed, measured slower.)
     const int ntask = k + 2;
     int nsplit, nt, tpw, nw, occ;
@@ -1080,17 +1082,18 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
       if (pick[0] == 0) {
         double best = -1.0;
         const int s0 = (ntask + 31) / 32;
-        for (int ns = s0; ns <= s0; ns++)
-          for (int tp = 1; tp <= 2; tp++) {
+        for (int ns = (ntask + 47) / 48; ns <= s0; ns++)
+          for (int tp = 1; tp <= 3; tp++) {
             const int ntt = (ntask + ns - 1) / ns;
             const int nww = (ntt + tp - 1) / tp;
             if (nww > 16) continue;
             int& o = ctx->red_occ[tp - 1][nww];
             if (o == 0) {
               int n = 0;
-              cudaError_t e = tp == 1
-                  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<1, 2>, 32 * nww, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<2, 2>, 32 * nww, 0);
+              cudaError_t e =
+                  tp == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<1, 2>, 32 * nww, 0)
+                  : tp == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<2, 2>, 32 * nww, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<3, 1>, 32 * nww, 0);
               if (e != cudaSuccess || n < 1) n = 1;
               o = n > PARTIAL_CTAS_PER_SM ? PARTIAL_CTAS_PER_SM : n;
             }
@@ -1115,7 +1118,8 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
                                            ctx->scal, sa, nsplit, nt);
     };
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
-    else go(k_reduce_f64x<2, 2>);
+    else if (tpw == 2) go(k_reduce_f64x<2, 2>);
+    else go(k_reduce_f64x<3, 1>);
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
     if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
     else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);
