@@ -127,7 +127,7 @@ struct kc_ctx {
   int num_sms;
   int reduce_grid;
   int red_occ[4][33];      // resident CTAs per SM of the offload reduction, by (TPW, warps)
-  int red_pick[kc::NMAX][5]; // its task layout per k: nsplit, tasks per subset, TPW, warps, CTAs/SM
+  int red_pick[2][kc::NMAX][5]; // its task layout per size class (m >= 2^22) and k: nsplit, tasks per subset, TPW, warps, CTAs/SM
   double* partials;        // PARTIAL_CTAS_PER_SM * num_sms * (2*NMAX + 4) doubles
   unsigned int* counters;  // ticket counters for last-CTA reductions
   kc::Scalars* scal;       // device scalars

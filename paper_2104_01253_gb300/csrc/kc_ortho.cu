@@ -115,6 +115,7 @@ __device__ void sum_partials(const double* __restrict__ partials, int nparts, in
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int vi = warp; vi < nval; vi += nw) {
     double s = 0.0;
+#pragma unroll 4
     for (int c = lane; c < nparts; c += 32) s += __ldcg(partials + (int64_t)c * PSTRIDE + vi);
     s = warp_sum(s);
     if (lane == 0) tot[vi] = s;
@@ -145,6 +146,12 @@ __device__ __forceinline__ void set_status(Scalars* sc, int st) {
 //   K(0:k, k) = T - H(0:k, 0:k-1) C / alpha (line 11; the flexible variant keeps K = T);
 //   GMRES: Givens rotation of the finalised column k-1.
 __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha) {
+  // The last CTA runs this once per step, so its dependent FP64 chains (about 70 cycles a
+  // link) are on the step's critical path: C, the finalised H column and the Givens state
+  // are staged in shared memory first, the column norm is a warp sum, and the K-column
+  // products unroll their loads.
+  __shared__ double s_c[NMAX], s_h[NMAX + 2], s_gc[NMAX], s_gs[NMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     sc->alpha = alpha;
     sc->inv_alpha = 1.0 / alpha;
@@ -154,28 +161,42 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
     if ((sa.flags & SF_GIVENS) && k == 0) { sc->g[0] = alpha; sc->ncols = 0; }
     if (sa.flags & SF_FLEXIBLE) sc->zscale[k] = 1.0 / alpha;
     if (k >= 1 || qr) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;
+    s_h[k] = alpha;
   }
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double c = sc->C[i];
     sc->T[i] = (sa.flags & SF_QR) ? sc->S[i] : sc->S[i] / alpha;
-    sa.H[i + (int64_t)(k - 1) * sa.ldh] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + sc->C[i];
+    const double h = sa.K[i + (int64_t)(k - 1) * sa.ldk] + c;
+    sa.H[i + (int64_t)(k - 1) * sa.ldh] = h;
+    s_c[i] = c;
+    s_h[i] = h;
+    if (i < k - 1) { s_gc[i] = sc->gc[i]; s_gs[i] = sc->gs[i]; }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && k >= 1) {
+  if (warp == 0 && k >= 1) {
     double cn = 0.0;
-    for (int i = 0; i <= k; i++) {
-      double h = sa.H[i + (int64_t)(k - 1) * sa.ldh];
-      cn += h * h;
-    }
-    if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
+    for (int i = lane; i <= k; i += 32) cn += s_h[i] * s_h[i];
+    cn = warp_sum(cn);
+    if (lane == 0 && alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
   }
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
     double hc = 0.0;
-    if (!(sa.flags & (SF_FLEXIBLE | SF_QR)))
-      for (int j = 0; j < k; j++) hc += sa.H[i + (int64_t)j * sa.ldh] * sc->C[j];
+    if (!(sa.flags & (SF_FLEXIBLE | SF_QR))) {
+#pragma unroll 4
+      for (int j = 0; j < k; j++) hc += sa.H[i + (int64_t)j * sa.ldh] * s_c[j];
+    }
     sa.K[i + (int64_t)k * sa.ldk] = sc->T[i] - hc / alpha;
   }
-  if (threadIdx.x == 0 && (sa.flags & SF_GIVENS) && k >= 1)
-    givens_column(sc, sa.H, sa.ldh, k - 1, sa.R, sa.ldr);
+  if (threadIdx.x == 0 && (sa.flags & SF_GIVENS) && k >= 1) {
+    // Givens rotation of column k-1 on the staged copies (the column is s_h, stride 0)
+    const int j = k - 1;
+    const double e = givens_rotate(s_gc, s_gs, sc->g, s_h, 0, j, sa.R, sa.ldr);
+    sc->gc[j] = s_gc[j];
+    sc->gs[j] = s_gs[j];
+    sc->resid_est = e;
+    sc->ncols = j + 1;
+    if (!(e > sc->rtol_abs)) sc->stop = 1;
+  }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -259,30 +280,34 @@ __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int 
     sc->C[i] = tot[2 * i];
     sc->S[i] = tot[2 * i + 1];
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {                                   // C^T C and C^T S: warp 0
     double cc = 0.0, cs = 0.0;
-    for (int i = 0; i < k; i++) {
+    for (int i = threadIdx.x; i < k; i += 32) {
       cc += tot[2 * i] * tot[2 * i];
       cs += tot[2 * i] * tot[2 * i + 1];
     }
-    const double beta = tot[2 * k], s = tot[2 * k + 1];
-    double a2 = beta - cc;                                   // Pythagoras, line 4
-    sc->beta = beta;
-    sc->s = s;
-    sc->cs = cs;
-    s_ok = 1;
-    if (!isfinite(a2) || !isfinite(s)) {
-      set_status(sc, KC_ERR_NONFINITE);
-    } else if (!(a2 > sa.pyth_tol * beta)) {
-      if (sa.flags & SF_FALLBACK) {
-        sc->fallback = 1;                                    // explicit norm pass follows
-        s_ok = 0;
-      } else {
-        set_status(sc, KC_ERR_PYTHAGORAS_NEG);
-        a2 = fmax(a2, 1e-300);
+    cc = warp_sum(cc);
+    cs = warp_sum(cs);
+    if (threadIdx.x == 0) {
+      const double beta = tot[2 * k], s = tot[2 * k + 1];
+      double a2 = beta - cc;                                 // Pythagoras, line 4
+      sc->beta = beta;
+      sc->s = s;
+      sc->cs = cs;
+      s_ok = 1;
+      if (!isfinite(a2) || !isfinite(s)) {
+        set_status(sc, KC_ERR_NONFINITE);
+      } else if (!(a2 > sa.pyth_tol * beta)) {
+        if (sa.flags & SF_FALLBACK) {
+          sc->fallback = 1;                                  // explicit norm pass follows
+          s_ok = 0;
+        } else {
+          set_status(sc, KC_ERR_PYTHAGORAS_NEG);
+          a2 = fmax(a2, 1e-300);
+        }
       }
+      s_alpha = sqrt(a2);
     }
-    s_alpha = sqrt(a2);
   }
   __syncthreads();
   if (s_ok) scalar_step(sc, sa, k, s_alpha);
@@ -1071,19 +1096,25 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
       ctx->fp64_mode == 1) {
     // Task layout: nsplit subsets of nt tasks (ceil(ntask / 48) <= nsplit <= ceil(ntask /
-    // 32)), CTAs of nw <= 16 warps with tpw <= 3 slots, chosen once per k to maximise
-    // resident warps x used slots; three slots (one row group per iteration, which fits 64
-    // registers) keep up to 48 tasks in one subset, so w and v are read once per row block.
-    // (Three subsets and more, or more subsets than needed, measured slower.)
+    // 32)), CTAs of nw <= 16 warps with tpw slots, chosen once per k and size class to
+    // maximise resident warps x used slots.  Three slots (one row group per iteration,
+    // which fits 64 registers) keep 33-48 tasks in one subset, so that w and v are read
+    // once per row block.  Below 33 tasks their small CTAs pay off only on long vectors:
+    // at m = 16 M, 8 warps x 3 slots beat 12 x 2 for 21-24 tasks (753-822 us against
+    // 833-872), while at m = 10^6 the larger CTAs won (83-86 us against 90-97) and below 21
+    // tasks they won at both sizes.  (Three subsets and more, or more subsets than needed,
+    // measured slower.)
     const int ntask = k + 2;
+    const int big = m >= ((int64_t)1 << 22);
     int nsplit, nt, tpw, nw, occ;
     {
-      int* pick = ctx->red_pick[k];
+      int* pick = ctx->red_pick[big][k];
       if (pick[0] == 0) {
         double best = -1.0;
         const int s0 = (ntask + 31) / 32;
+        const int tpmax = (ntask > 32 || (big && ntask > 20)) ? 3 : 2;
         for (int ns = (ntask + 47) / 48; ns <= s0; ns++)
-          for (int tp = 1; tp <= 3; tp++) {
+          for (int tp = 1; tp <= tpmax; tp++) {
             const int ntt = (ntask + ns - 1) / ns;
             const int nww = (ntt + tp - 1) / tp;
             if (nww > 16) continue;
