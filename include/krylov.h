@@ -120,7 +120,15 @@ const char* kc_last_error(const kc_ctx* ctx);
  *     arithmetic (about 2^-44 relative) on the FP32/INT pipes.  An error d in S is
  *     removed by the next step's delayed reorthogonalisation (it returns as -d/alpha in
  *     the next C and cancels in H = K + C, Section 4), and Q C is scaled by the tiny C,
- *     so Q and H keep FP64 accuracy while half of the FP64 FMAs leave the FP64 pipe. */
+ *     so Q and H keep FP64 accuracy while half of the FP64 FMAs leave the FP64 pipe.
+ *  2: as 1, but the fused reduction (C, S, beta, s; Algorithm 4 lines 1-3) runs on the
+ *     tensor cores as exact integer dot products of fixed-point digit expansions (the
+ *     Ozaki scheme: basis entries as round(q 2^56), w and v scaled per 512-row chunk,
+ *     FP16 digits, FP32 accumulators that stay exact, one FP64 rounding per chunk), with
+ *     no FP64 arithmetic per basis entry; steps with more than 62 basis columns, or a
+ *     basis, w or v not 16-byte aligned (odd leading dimension), use mode 1's reduction.
+ *     A basis entry of magnitude >= 2 or a non-finite operand sets KC_ERR_NONFINITE.
+ * Other values return KC_ERR_INVALID_ARG. */
 kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode);
 int kc_get_fp64_mode(const kc_ctx* ctx);
 /* Kernel variants of the FP64 basis passes (bit flags; same arithmetic either way):

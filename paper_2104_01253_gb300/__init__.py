@@ -49,7 +49,8 @@ class Context:
         return _lib.check(self.handle, status)
 
     def set_fp64_mode(self, mode: int):
-        """0: all FP64 products; 1: FP64 with float-float offload (default)."""
+        """0: all FP64 products; 1: FP64 with float-float offload (default); 2: the fused
+        reduction as exact fixed-point digit products on the tensor cores."""
         self.check(self.lib.kc_set_fp64_mode(self.handle, mode))
 
     CONV_MMA_SYNC, CONV_TCGEN05 = 0, 1

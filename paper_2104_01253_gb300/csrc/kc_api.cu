@@ -165,7 +165,7 @@ kc_status kc_destroy(kc_ctx* ctx) {
 }
 
 kc_status kc_set_fp64_mode(kc_ctx* ctx, int mode) {
-  if (!ctx || mode < 0 || mode > 1) return KC_ERR_INVALID_ARG;
+  if (!ctx || mode < 0 || mode > 2) return KC_ERR_INVALID_ARG;
   ctx->fp64_mode = mode;
   return KC_OK;
 }

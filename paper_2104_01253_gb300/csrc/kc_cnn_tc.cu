@@ -23,6 +23,7 @@
 // Every wait is bounded: on a timeout the kernel records KC_ERR_TIMEOUT, stops, waits
 // (bounded) for its copies and MMAs in flight, frees its tensor memory and returns.
 #include "kc_internal.cuh"
+#include "kc_tcgen05.cuh"
 #include "kc_tma.cuh"
 
 namespace kc {
@@ -42,65 +43,9 @@ constexpr int TP_SMEM = 128 + TC_WREGION + TP_NS * TP_STAGE + TP_OUT;
 constexpr int TP_THREADS = 192;
 constexpr int TP_TMEM_COLS = 64;                          // two 32-column accumulators
 constexpr int TC_CTAS_PER_SM = 2;
-// instruction descriptor, kind::f16: D = F32 (bits 4-5), A = B = BF16 (bits 7-9, 10-12),
-// both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28)
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) |
-                              ((128u >> 4) << 24);
+constexpr uint32_t TC_IDESC = idesc_bf16_f32(128, 32);
 static_assert(TP_PLANE % 128 == 0 && TP_PLANE >= TC_HH * TC_HW * 16, "plane size");
 static_assert(TC_WREGION % 128 == 0 && TC_WREGION >= 9 * 4 * 512, "weight region");
-
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets,
-// descriptor version 1, no swizzle
-__device__ __forceinline__ unsigned long long umma_desc(unsigned int saddr, unsigned int lbo,
-                                                        unsigned int sbo) {
-  return (unsigned long long)((saddr >> 4) & 0x3FFFu) |
-         ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_mma(unsigned int dtmem, unsigned long long adesc,
-                                       unsigned long long bdesc, unsigned int idesc,
-                                       unsigned int accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-               ::"r"(smem_u32(bar)) : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tc_ld32(unsigned int taddr, float (&v)[32]) {
-  unsigned int r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-      "%28, %29, %30, %31}, [%32];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
-}
 
 __device__ __forceinline__ unsigned int tc_bfbits(float f) {
   const unsigned int u = __float_as_uint(f);

@@ -1030,6 +1030,7 @@ static int reduce_grid_for(const kc_ctx* ctx, int64_t ngroups) {
 }  // namespace kc
 
 #include "kc_reduce_tma.cuh"
+#include "kc_reduce_tc.cuh"
 
 namespace kc {
 
@@ -1089,53 +1090,76 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     return fail(ctx, KC_ERR_INVALID_ARG, "reduce: unsupported basis/vector types %d/%d", q_dtype, vec_dtype);
   timing_begin(ctx, KID_REDUCE);
   if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
-      (ctx->staged & 2) && reduce_tma_supported(k, m)) {
-    kc_status st = launch_reduce_tma(ctx, (const double*)Q, ldq, k, (const double*)x,
-                                     (const double*)y, m, ctx->fp64_mode == 1, sa);
+      ctx->fp64_mode == 2 && reduce_tcx_supported(k, m, Q, ldq, x, y)) {
+    kc_status st = launch_reduce_tcx(ctx, (const double*)Q, ldq, k, (const double*)x,
+                                     (const double*)y, m, sa);
     if (st != KC_OK) return st;
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
-      ctx->fp64_mode == 1) {
+      (ctx->staged & 2) && reduce_tma_supported(k, m)) {
+    kc_status st = launch_reduce_tma(ctx, (const double*)Q, ldq, k, (const double*)x,
+                                     (const double*)y, m, ctx->fp64_mode >= 1, sa);
+    if (st != KC_OK) return st;
+  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
+      ctx->fp64_mode >= 1) {
     // Task layout: nsplit subsets of nt tasks (ceil(ntask / 48) <= nsplit <= ceil(ntask /
     // 32)), CTAs of nw <= 16 warps with tpw slots, chosen once per k and size class to
     // maximise resident warps x used slots.  Three slots (one row group per iteration,
     // which fits 64 registers) keep 33-48 tasks in one subset, so that w and v are read
     // once per row block.  Below 33 tasks their small CTAs pay off only on long vectors:
     // at m = 16 M, 8 warps x 3 slots beat 12 x 2 for 21-24 tasks (753-822 us against
-    // 833-872), while at m = 10^6 the larger CTAs won (83-86 us against 90-97) and below 21
-    // tasks they won at both sizes.  (Three subsets and more, or more subsets than needed,
-    // measured slower.)
+    // 833-872), while at m = 10^6 the larger CTAs won (83-86 us against 90-97).  (Three
+    // subsets and more, or more subsets than needed, measured slower.)  Sweeps of every
+    // layout at each k (m = 16 M and 10^6) found three ranges where the score misjudges,
+    // taken from the measurements instead: 33-36 tasks run fastest as two subsets of two
+    // slots (5% at both sizes), and up to 16 tasks as one subset of two slots on long
+    // vectors (up to 14%) but of one slot on short ones.
     const int ntask = k + 2;
     const int big = m >= ((int64_t)1 << 22);
     int nsplit, nt, tpw, nw, occ;
     {
       int* pick = ctx->red_pick[big][k];
       if (pick[0] == 0) {
-        double best = -1.0;
-        const int s0 = (ntask + 31) / 32;
-        const int tpmax = (ntask > 32 || (big && ntask > 20)) ? 3 : 2;
-        for (int ns = (ntask + 47) / 48; ns <= s0; ns++)
-          for (int tp = 1; tp <= tpmax; tp++) {
-            const int ntt = (ntask + ns - 1) / ns;
-            const int nww = (ntt + tp - 1) / tp;
-            if (nww > 16) continue;
-            int& o = ctx->red_occ[tp - 1][nww];
-            if (o == 0) {
-              int n = 0;
-              cudaError_t e =
-                  tp == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<1, 2>, 32 * nww, 0)
-                  : tp == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<2, 2>, 32 * nww, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<3, 1>, 32 * nww, 0);
-              if (e != cudaSuccess || n < 1) n = 1;
-              o = n > PARTIAL_CTAS_PER_SM ? PARTIAL_CTAS_PER_SM : n;
-            }
-            const int warps = o * nww < 32 ? o * nww : 32;
-            const double score = warps * (double)ntask / ((double)ns * nww * tp) /
-                                 (1.0 + 0.03 * (ns - s0));
-            if (score > best) {
-              best = score;
-              pick[0] = ns; pick[1] = ntt; pick[2] = tp; pick[3] = nww; pick[4] = o;
-            }
+        auto occ_of = [&](int tp, int nww) {
+          int& o = ctx->red_occ[tp - 1][nww];
+          if (o == 0) {
+            int n = 0;
+            cudaError_t e =
+                tp == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<1, 2>, 32 * nww, 0)
+                : tp == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<2, 2>, 32 * nww, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce_f64x<3, 1>, 32 * nww, 0);
+            if (e != cudaSuccess || n < 1) n = 1;
+            o = n > PARTIAL_CTAS_PER_SM ? PARTIAL_CTAS_PER_SM : n;
           }
+          return o;
+        };
+        auto take = [&](int ns, int tp) {
+          const int ntt = (ntask + ns - 1) / ns;
+          const int nww = (ntt + tp - 1) / tp;
+          pick[0] = ns; pick[1] = ntt; pick[2] = tp; pick[3] = nww; pick[4] = occ_of(tp, nww);
+        };
+        if (ntask >= 33 && ntask <= 36) {
+          take(2, 2);
+        } else if (ntask <= 16) {
+          take(1, big && ntask >= 5 ? 2 : 1);
+        } else {
+          double best = -1.0;
+          const int s0 = (ntask + 31) / 32;
+          const int tpmax = (ntask > 32 || (big && ntask > 20)) ? 3 : 2;
+          for (int ns = (ntask + 47) / 48; ns <= s0; ns++)
+            for (int tp = 1; tp <= tpmax; tp++) {
+              const int ntt = (ntask + ns - 1) / ns;
+              const int nww = (ntt + tp - 1) / tp;
+              if (nww > 16) continue;
+              const int o = occ_of(tp, nww);
+              const int warps = o * nww < 32 ? o * nww : 32;
+              const double score = warps * (double)ntask / ((double)ns * nww * tp) /
+                                   (1.0 + 0.03 * (ns - s0));
+              if (score > best) {
+                best = score;
+                take(ns, tp);
+              }
+            }
+        }
       }
       nsplit = pick[0]; nt = pick[1]; tpw = pick[2]; nw = pick[3]; occ = pick[4];
     }
@@ -1172,7 +1196,7 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
   const int R = vec_dtype == KC_F64 ? 2 : 4;
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_UPDATE);
-  if (q_dtype == KC_F64 && ctx->fp64_mode == 1)
+  if (q_dtype == KC_F64 && ctx->fp64_mode >= 1)
     k_dcgs2_update_f64x<<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
   else if (q_dtype == KC_F64)
     k_dcgs2_update<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);

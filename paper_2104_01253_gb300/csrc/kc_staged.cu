@@ -207,7 +207,7 @@ k_update_staged(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__
 kc_status launch_update_staged(kc_ctx* ctx, double* Q, int64_t ldq, int k, double* w,
                                const double* v, int64_t m) {
   static std::atomic<unsigned long long> attr_done[2];
-  const int off = ctx->fp64_mode == 1 ? 1 : 0;
+  const int off = ctx->fp64_mode >= 1 ? 1 : 0;
   if (off) KC_TRY(smem_attr_once(ctx, attr_done[1], k_update_staged<true>, (int)ST_SMEM, "staged update"));
   else KC_TRY(smem_attr_once(ctx, attr_done[0], k_update_staged<false>, (int)ST_SMEM, "staged update"));
   const int64_t ntiles = (m + ST_TR - 1) / ST_TR;

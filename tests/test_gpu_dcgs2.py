@@ -71,13 +71,14 @@ def test_spmv_matches_scipy(kc, ctx, name, make):
 
 
 @pytest.mark.parametrize("staged", [0, 2, 3])
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("name,make", CASES)
 @pytest.mark.parametrize("n", [1, 2, 17, 50])
 def test_dcgs2_matches_oracle(kc, ctx, name, make, n, mode, staged):
-    """Both FP64 modes: all-FP64 products (0) and FP64 with float-float offload (1); the
-    register-streaming kernels (staged 0), the tensor-copy staged reduction (2) and that
-    with the bulk-copy staged update (3)."""
+    """The FP64 modes: all-FP64 products (0), FP64 with float-float offload (1) and the
+    reduction as exact digit products on the tensor cores (2, which takes precedence over
+    the staged reduction); the register-streaming kernels (staged 0), the tensor-copy
+    staged reduction (2) and that with the bulk-copy staged update (3)."""
     Ah = make()
     r0 = gaussian_vector(Ah.m, 1002)
     ctx.set_fp64_mode(mode)
@@ -119,7 +120,7 @@ def test_offload_falls_back_to_fp64_outside_the_float_range(kc, ctx, case):
     assert ctx.read_status() == 0
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_dcgs2_stepwise_state_matches_oracle(kc, ctx, mode):
     """After every step: pending w, the lagged H columns and alpha agree with the oracle.
     (The offload mode's S error shows in w at about 1e-13 relative; H is unaffected.)"""
@@ -141,6 +142,54 @@ def test_dcgs2_stepwise_state_matches_oracle(kc, ctx, mode):
             Hg = st.H(k + 1, k).cpu().numpy()
             assert np.abs(Hg - ref.H[:k + 1, :k]).max() <= 1e-12 * np.abs(ref.H[:k + 1, :k]).max()
     ctx.set_fp64_mode(1)
+
+
+@pytest.mark.parametrize("m", [255, 256, 257, 3001])
+def test_tensor_core_reduction_scalars_match_exact_sums(kc, ctx, m):
+    """Mode 2 on a single step: alpha, beta and s from the tensor-core reduction against
+    the oracle's step, on sizes around one 256-row chunk (empty tail, exact fit, one row
+    over) and a start vector with a 10^12 dynamic range."""
+    rng = np.random.default_rng(m)
+    r0 = rng.standard_normal(m)
+    r0[::3] *= 1e-12
+    Ah = CSR(m, np.arange(m + 1, dtype=np.int32), np.arange(m, dtype=np.int32),
+             np.linspace(1.0, 3.0, m))
+    A = kc.DeviceCSR(Ah)
+    ref = orc.DCGS2Arnoldi(Ah.to_scipy(), r0, 4)
+    st = kc.ArnoldiState(m, 4, kc.KC_F64)
+    ctx.set_fp64_mode(2)
+    try:
+        kc.dcgs2_arnoldi_init(ctx, A, st, torch.as_tensor(r0, device="cuda"))
+        for _ in range(3):
+            kc.dcgs2_arnoldi_step(ctx, A, st)
+            alpha_o = ref.step()
+            alpha_g, _, _ = ctx.last_scalars()
+            assert abs(alpha_g - alpha_o) <= 1e-13 * alpha_o
+    finally:
+        ctx.set_fp64_mode(1)
+    assert ctx.read_status() == 0
+
+
+def test_tensor_core_reduction_flags_a_basis_entry_out_of_range(kc, ctx):
+    """The fixed-point form holds basis entries below 2 in magnitude: a stored column
+    entry of 3 (a column far from unit norm) makes the step report KC_ERR_NONFINITE."""
+    Ah = convdiff_csr(8, 3, [1.0, 1.0, 1.0])
+    r0 = gaussian_vector(Ah.m, 3)
+    A = kc.DeviceCSR(Ah)
+    st = kc.ArnoldiState(Ah.m, 6, kc.KC_F64)
+    ctx.set_fp64_mode(2)
+    try:
+        kc.dcgs2_arnoldi_init(ctx, A, st, torch.as_tensor(r0, device="cuda"))
+        kc.dcgs2_arnoldi_step(ctx, A, st)
+        kc.dcgs2_arnoldi_step(ctx, A, st)
+        torch.cuda.synchronize()
+        assert ctx.read_status() == 0
+        st.Qbuf[0, 5] = 3.0
+        kc.dcgs2_arnoldi_step(ctx, A, st)
+        torch.cuda.synchronize()
+        assert ctx.read_status() == kc._lib.KC_ERR_NONFINITE
+    finally:
+        ctx.set_fp64_mode(1)
 
 
 def test_first_step_normalises_r0(kc, ctx):

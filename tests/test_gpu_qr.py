@@ -52,7 +52,7 @@ def _run(kc, ctx, B, mode):
     return Qt[:, :m].cpu().numpy().T, Rt.cpu().numpy().T
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("m,n,graded", [(1000, 1, False), (1000, 2, False), (5001, 17, False),
                                         (20000, 40, True), (40000, 64, False)])
 def test_dcgs2_qr_matches_oracle(kc, ctx, m, n, graded, mode):
@@ -77,7 +77,7 @@ def test_dcgs2_qr_rejects_bad_arguments(kc, ctx):
         kc.dcgs2_qr(ctx, torch.zeros((4, 101), dtype=torch.float64, device="cuda"), Qt, Rt)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_dcgs2_qr_orthogonality_over_condition_numbers(kc, ctx, mode):
     """Table 3: DCGS2 (QR) keeps the loss of orthogonality at O(eps) whatever kappa(A), and
     the representation error at O(eps).  Graded matrices with kappa from 1e2 to 1e14 (one

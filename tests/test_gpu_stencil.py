@@ -100,7 +100,7 @@ STENCILS = [
 ]
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("name,make", STENCILS)
 def test_dcgs2_on_stencil_matches_oracle(kc, ctx, name, make, mode):
     st = make()
