@@ -26,7 +26,8 @@
 //
 // Layout: per chunk of TX_R rows, B (N = 32: twelve w digits, twelve v digits, zero rows)
 // in shared memory; per stage of TX_KS rows, A tiles of 128 rows = 21 columns x 6 digits
-// (+ 2 zero rows), at most TX_MT tiles (k + 1 <= 63 columns).  Both are K-major core
+// and two more rows, at most TX_MT tiles (k + 1 <= 63 columns).  Row 126 of tile 0 holds
+// FP16 ones, so its accumulator row is sum_i d_t,i of w and v (the bias to remove).  Both are K-major core
 // matrices of 8 rows x 16 bytes without swizzle; the K-adjacent slabs are padded by 16
 // bytes so that the 4-byte digit-pair stores of a warp hit 32 distinct banks.  One CTA
 // per SM, 16 warps: warp w converts columns w, w + 16, ... (lane l: rows 2l, 2l + 1 of
