@@ -341,7 +341,43 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
   const int64_t ngroups = m / R;
   const int64_t g0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
   const int64_t g1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
-  for (int64_t g = g0 + lane; g < g1; g += 32) {
+  int64_t g = g0 + lane;
+  // FP32 / BF16 vectors (HBM-bound): two row groups per iteration, every load issued
+  // before the arithmetic, so twice the bytes are in flight per warp
+  if (sizeof(TV) == 4 && TPW <= 4) {
+    for (; g + 32 < g1; g += 64) {
+      TV xa[R], ya[R], xb[R], yb[R];
+      ldv(x, g, xa);
+      ldv(x, g + 32, xb);
+      if (NRHS == 2) { ldv(y, g, ya); ldv(y, g + 32, yb); }
+      TA qa[TPW][R], qb[TPW][R];
+#pragma unroll
+      for (int i = 0; i < TPW; i++) {
+        const int t = warp + RED_WARPS * i;
+        if (t < k) {
+          load_q(Q + (int64_t)t * ldq, g, qa[i]);
+          load_q(Q + (int64_t)t * ldq, g + 32, qb[i]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; r++) { qa[i][r] = xa[r]; qb[i][r] = xb[r]; }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < TPW; i++) {
+        if (warp + RED_WARPS * i >= ntask) continue;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          acc[i][0] += qa[i][r] * (TA)xa[r];
+          acc[i][0] += qb[i][r] * (TA)xb[r];
+          if (NRHS == 2) {
+            acc[i][1] += qa[i][r] * (TA)ya[r];
+            acc[i][1] += qb[i][r] * (TA)yb[r];
+          }
+        }
+      }
+    }
+  }
+  for (; g < g1; g += 32) {
     TV xv[R], yv[R];
     ldv(x, g, xv);
     if (NRHS == 2) ldv(y, g, yv);

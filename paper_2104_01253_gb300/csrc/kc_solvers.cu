@@ -60,11 +60,14 @@ __global__ void __launch_bounds__(256) k_x_update(const TQ* __restrict__ Q, int6
   const int n = sc->ncols;
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = sc->y[i];
   __syncthreads();
+  // an FP32 solution (the inner solve of iterative refinement, tolerance 1e-4) is
+  // accumulated in FP32: the FP64 pipe would bound this HBM pass at n FMAs per row
+  using TS = typename std::conditional<sizeof(TX) == 4, float, double>::type;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
        r += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < n; j++) s += qval(Q + (int64_t)j * ldq, r) * y[j];
-    x[r] = (TX)((double)x[r] + s);
+    TS s = 0;
+    for (int j = 0; j < n; j++) s += (TS)qval(Q + (int64_t)j * ldq, r) * (TS)y[j];
+    x[r] = (TX)((TS)x[r] + s);
   }
 }
 

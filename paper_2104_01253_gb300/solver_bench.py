@@ -1,7 +1,8 @@
 """Time one restarted DCGS2-GMRES solve and break it down by kernel kind.
 
     python -m paper_2104_01253_gb300.solver_bench [--config 1|2] [--restart 30]
-                                                  [--stencil] [--reps 3] [--path 0|1|2]
+                                                  [--stencil] [--reps 3] [--path 0|1|2|3]
+                                                  [--precision 0|1|2]
 
 config 1: the 2D convection-diffusion operator on a 100 x 100 grid (m = 10,000), b ~ N(0,1)
 seed 1001, GMRES(30); config 2: the 252^3 operator (m = 16,003,008), b seed 1004,
@@ -12,7 +13,9 @@ resident on the GPU), iterations, launches per solve, and the summed device time
 kernel kind from a separate solve timed with per-launch CUDA events (kc_timing_enable),
 whose gap to the wall time is host launch overhead and idle device time.  --path selects
 the FP64 solve path (0 by size, 1 multi-kernel, 2 one thread-block cluster, 3 one CTA per
-SM over the whole GPU).
+SM over the whole GPU).  --precision 1 / 2: FP32 / BF16-basis inner solves in FP64
+iterative refinement (inner tolerance 1e-4, at most 3 inner cycles, as bench.py), with
+an FP32 copy of the operator.
 """
 from __future__ import annotations
 
@@ -33,6 +36,7 @@ def main():
     p.add_argument("--stencil", action="store_true", help="matrix-free operator")
     p.add_argument("--reps", type=int, default=3)
     p.add_argument("--path", type=int, default=0, choices=[0, 1, 2, 3])
+    p.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
     a = p.parse_args()
     import synth
     if a.grid2d:
@@ -50,30 +54,38 @@ def main():
     ctx = Context(0)
     ctx.set_gmres_path(a.path)
     A = DeviceStencil7(op) if a.stencil else DeviceCSR(op)
+    A32 = None
+    if a.precision:
+        A32 = (DeviceStencil7(op, dtype=torch.float32) if a.stencil
+               else DeviceCSR(op, dtype=torch.float32))
     m = A.m
+    solve = lambda: gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10,
+                                precision=a.precision, A32=A32, inner_rtol=1e-4,
+                                inner_max_cycles=3)
     b = torch.as_tensor(synth.gaussian_vector(m, seed), device="cuda")
     x = torch.zeros_like(b)
-    gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10)            # warm-up
+    solve()                                                           # warm-up
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     launches0 = ctx.launch_count()
     t0.record()
     for _ in range(a.reps):
         x.zero_()
-        info = gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10)
+        info = solve()
     t1.record()
     torch.cuda.synchronize()
     launches = (ctx.launch_count() - launches0) // a.reps
     ms = t0.elapsed_time(t1) / a.reps
     x.zero_()
     ctx.timing_enable(True)
-    gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10)
+    solve()
     torch.cuda.synchronize()
     kinds = ctx.timing_read()
     ctx.timing_enable(False)
     print(json.dumps({"config": ("2d N=%d" % a.grid2d) if a.grid2d else a.config,
                       "operator": "stencil" if a.stencil else "csr",
                       "path": ["auto", "multi-kernel", "cluster", "grid"][a.path],
+                      "precision": ["fp64", "fp32-inner-ir", "bf16-basis-ir"][a.precision],
                       "m": m, "restart": restart, "ms_per_solve": ms, "iters": info["iters"],
                       "status": info["status"], "rel_resid_true": info["rel_resid_true"],
                       "launches_per_solve": launches,
