@@ -115,7 +115,7 @@ __device__ void sum_partials(const double* __restrict__ partials, int nparts, in
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int vi = warp; vi < nval; vi += nw) {
     double s = 0.0;
-#pragma unroll 4
+#pragma unroll 8
     for (int c = lane; c < nparts; c += 32) s += __ldcg(partials + (int64_t)c * PSTRIDE + vi);
     s = warp_sum(s);
     if (lane == 0) tot[vi] = s;
@@ -330,7 +330,10 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
   using TA = typename Acc<TV>::T;
   constexpr int R = Grp<TV>::R;
   if (sc->stop) return;
+  // (only one-slot launches run with fewer than RED_WARPS warps; a compile-time warp count
+  // keeps the multi-slot variants within 64 registers)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = TPW == 1 ? (int)(blockDim.x >> 5) : RED_WARPS;
   const int ntask = k + 1;
   TA acc[TPW][NRHS];
 #pragma unroll
@@ -353,7 +356,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
       TA qa[TPW][R], qb[TPW][R];
 #pragma unroll
       for (int i = 0; i < TPW; i++) {
-        const int t = warp + RED_WARPS * i;
+        const int t = warp + nw * i;
         if (t < k) {
           load_q(Q + (int64_t)t * ldq, g, qa[i]);
           load_q(Q + (int64_t)t * ldq, g + 32, qb[i]);
@@ -364,7 +367,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
       }
 #pragma unroll
       for (int i = 0; i < TPW; i++) {
-        if (warp + RED_WARPS * i >= ntask) continue;
+        if (warp + nw * i >= ntask) continue;
 #pragma unroll
         for (int r = 0; r < R; r++) {
           acc[i][0] += qa[i][r] * (TA)xa[r];
@@ -383,7 +386,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
     if (NRHS == 2) ldv(y, g, yv);
 #pragma unroll
     for (int i = 0; i < TPW; i++) {
-      const int t = warp + RED_WARPS * i;
+      const int t = warp + nw * i;
       if (t < ntask) {
         TA qv[R];
         if (t < k) {
@@ -407,7 +410,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
       TA ys = NRHS == 2 ? (TA)__ldcg(y + row) : (TA)0;
 #pragma unroll
       for (int i = 0; i < TPW; i++) {
-        const int t = warp + RED_WARPS * i;
+        const int t = warp + nw * i;
         if (t < ntask) {
           TA q = t < k ? (TA)ld1(Q + (int64_t)t * ldq, row) : xs;
           acc[i][0] += q * xs;
@@ -418,7 +421,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
   }
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
-    const int t = warp + RED_WARPS * i;
+    const int t = warp + nw * i;
 #pragma unroll
     for (int r = 0; r < NRHS; r++) {
       double v = (double)warp_sum(acc[i][r]);
@@ -1103,9 +1106,31 @@ template <typename TQ, typename TV, int NRHS>
 static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int k,
                             const TV* x, const TV* y, int64_t m, int epi, const StepArgs& sa) {
   const int ntask = k + 1;
+  // Few tasks: one warp per task and as many CTAs per SM as fit, so that every SM streams
+  // many row ranges at once (16 warps sharing one row range left most of them idle with one
+  // memory round trip per iteration: 159 us for w and v of an FP32 basis at m = 16 M, 63 us
+  // this way).  Measured faster up to 10 tasks; from 13 the 2 x 16-warp layout is ahead.
+  int nw = RED_WARPS;
+  if (ntask <= 10) {
+    nw = ntask;
+    static int occ[11];                           // resident CTAs per SM, by warps
+    if (occ[nw] == 0) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 1, NRHS>, 32 * nw,
+                                                        0) != cudaSuccess || n < 1)
+        n = 1;
+      occ[nw] = n;
+    }
+    const int cps = occ[nw] < PARTIAL_CTAS_PER_SM ? occ[nw] : PARTIAL_CTAS_PER_SM;
+    const int64_t ngroups = m / Grp<TV>::R;
+    int64_t b = (ngroups + 32 * 4 - 1) / (32 * 4);
+    const int64_t cap = (int64_t)ctx->num_sms * cps;
+    if (b > cap) b = cap;
+    grid = (int)(b < 1 ? 1 : b);
+  }
   auto args = [&](auto kern) {
-    kern<<<grid, RED_THREADS, 0, ctx->stream>>>(Q, ldq, k, x, y, m, ctx->partials,
-                                                ctx->counters, ctx->scal, epi, sa);
+    kern<<<grid, 32 * nw, 0, ctx->stream>>>(Q, ldq, k, x, y, m, ctx->partials,
+                                            ctx->counters, ctx->scal, epi, sa);
   };
   if (ntask <= RED_WARPS) args(k_reduce<TQ, TV, 1, NRHS>);
   else if (ntask <= 2 * RED_WARPS) args(k_reduce<TQ, TV, 2, NRHS>);
