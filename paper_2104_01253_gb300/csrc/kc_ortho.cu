@@ -330,10 +330,10 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
   using TA = typename Acc<TV>::T;
   constexpr int R = Grp<TV>::R;
   if (sc->stop) return;
-  // (only one-slot launches run with fewer than RED_WARPS warps; a compile-time warp count
-  // keeps the multi-slot variants within 64 registers)
+  // (one- and two-slot launches size their CTAs to the task count; a compile-time warp
+  // count keeps the four- and eight-slot variants within 64 registers)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = TPW == 1 ? (int)(blockDim.x >> 5) : RED_WARPS;
+  const int nw = TPW <= 2 ? (int)(blockDim.x >> 5) : RED_WARPS;
   const int ntask = k + 1;
   TA acc[TPW][NRHS];
 #pragma unroll
@@ -1109,19 +1109,24 @@ static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int
   // Few tasks: one warp per task and as many CTAs per SM as fit, so that every SM streams
   // many row ranges at once (16 warps sharing one row range left most of them idle with one
   // memory round trip per iteration: 159 us for w and v of an FP32 basis at m = 16 M, 63 us
-  // this way).  Measured faster up to 10 tasks; from 13 the 2 x 16-warp layout is ahead.
+  // this way); measured faster up to 10 tasks, while from 13 to 16 the 2 x 16-warp layout
+  // is ahead.  17-32 tasks: two slots per warp in ceil(ntask / 2) warps, so that no warp
+  // carries twice the columns of the others (17 tasks on 16 warps ran at half pace).
   int nw = RED_WARPS;
-  if (ntask <= 10) {
-    nw = ntask;
-    static int occ[11];                           // resident CTAs per SM, by warps
-    if (occ[nw] == 0) {
+  if (ntask <= 10 || (ntask > RED_WARPS && ntask <= 2 * RED_WARPS)) {
+    nw = ntask <= 10 ? ntask : (ntask + 1) / 2;
+    static int occ[2][RED_WARPS + 1];             // resident CTAs per SM, by slots and warps
+    int& o = occ[ntask > 10][nw];
+    if (o == 0) {
       int n = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 1, NRHS>, 32 * nw,
-                                                        0) != cudaSuccess || n < 1)
-        n = 1;
-      occ[nw] = n;
+      const cudaError_t e =
+          ntask <= 10
+              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 1, NRHS>, 32 * nw, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 2, NRHS>, 32 * nw, 0);
+      if (e != cudaSuccess || n < 1) n = 1;
+      o = n;
     }
-    const int cps = occ[nw] < PARTIAL_CTAS_PER_SM ? occ[nw] : PARTIAL_CTAS_PER_SM;
+    const int cps = o < PARTIAL_CTAS_PER_SM ? o : PARTIAL_CTAS_PER_SM;
     const int64_t ngroups = m / Grp<TV>::R;
     int64_t b = (ngroups + 32 * 4 - 1) / (32 * 4);
     const int64_t cap = (int64_t)ctx->num_sms * cps;
