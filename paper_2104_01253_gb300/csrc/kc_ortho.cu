@@ -330,10 +330,10 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
   using TA = typename Acc<TV>::T;
   constexpr int R = Grp<TV>::R;
   if (sc->stop) return;
-  // (one- and two-slot launches size their CTAs to the task count; a compile-time warp
+  // (one- to three-slot launches size their CTAs to the task count; a compile-time warp
   // count keeps the four- and eight-slot variants within 64 registers)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = TPW <= 2 ? (int)(blockDim.x >> 5) : RED_WARPS;
+  const int nw = TPW <= 3 ? (int)(blockDim.x >> 5) : RED_WARPS;
   const int ntask = k + 1;
   TA acc[TPW][NRHS];
 #pragma unroll
@@ -1110,19 +1110,21 @@ static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int
   // many row ranges at once (16 warps sharing one row range left most of them idle with one
   // memory round trip per iteration: 159 us for w and v of an FP32 basis at m = 16 M, 63 us
   // this way); measured faster up to 10 tasks, while from 13 to 16 the 2 x 16-warp layout
-  // is ahead.  17-32 tasks: two slots per warp in ceil(ntask / 2) warps, so that no warp
-  // carries twice the columns of the others (17 tasks on 16 warps ran at half pace).
+  // is ahead.  17-32 and 33-48 tasks: two or three slots per warp in ceil(ntask / slots)
+  // warps, so that no warp carries more columns than the others (17 tasks on 16 warps ran
+  // at half pace).
   int nw = RED_WARPS;
-  if (ntask <= 10 || (ntask > RED_WARPS && ntask <= 2 * RED_WARPS)) {
-    nw = ntask <= 10 ? ntask : (ntask + 1) / 2;
-    static int occ[2][RED_WARPS + 1];             // resident CTAs per SM, by slots and warps
-    int& o = occ[ntask > 10][nw];
+  const int slots = ntask <= 10 ? 1 : (ntask <= RED_WARPS ? 0 : (ntask <= 2 * RED_WARPS ? 2 : (ntask <= 3 * RED_WARPS ? 3 : 0)));
+  if (slots) {
+    nw = (ntask + slots - 1) / slots;
+    static int occ[4][RED_WARPS + 1];             // resident CTAs per SM, by slots and warps
+    int& o = occ[slots][nw];
     if (o == 0) {
       int n = 0;
       const cudaError_t e =
-          ntask <= 10
-              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 1, NRHS>, 32 * nw, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 2, NRHS>, 32 * nw, 0);
+          slots == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 1, NRHS>, 32 * nw, 0)
+          : slots == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 2, NRHS>, 32 * nw, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 3, NRHS>, 32 * nw, 0);
       if (e != cudaSuccess || n < 1) n = 1;
       o = n;
     }
@@ -1139,6 +1141,7 @@ static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int
   };
   if (ntask <= RED_WARPS) args(k_reduce<TQ, TV, 1, NRHS>);
   else if (ntask <= 2 * RED_WARPS) args(k_reduce<TQ, TV, 2, NRHS>);
+  else if (ntask <= 3 * RED_WARPS) args(k_reduce<TQ, TV, 3, NRHS>);
   else if (ntask <= 4 * RED_WARPS) args(k_reduce<TQ, TV, 4, NRHS>);
   else args(k_reduce<TQ, TV, 8, NRHS>);
 }
