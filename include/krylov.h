@@ -87,7 +87,7 @@ typedef struct {
  *        pending vector, v the matvec workspace.
  *  H     FP64, column-major, ldh >= ncap, at least ldh*(ncap-1) entries.
  *  K     FP64 workspace, ncap*(ncap-1) entries, column-major with ld ncap: column j holds
- *        the partial Hessenberg column that the next step completes (Alg. 4 line 11).
+ *        the partial Hessenberg column that the next step completes (Algorithm 4).
  *  k     number of final basis columns; written by the library (read-only for callers).
  *  nsteps_since_init  written by the library. */
 typedef struct {
@@ -121,7 +121,7 @@ const char* kc_last_error(const kc_ctx* ctx);
  *     removed by the next step's delayed reorthogonalisation (it returns as -d/alpha in
  *     the next C and cancels in H = K + C, Section 4), and Q C is scaled by the tiny C,
  *     so Q and H keep FP64 accuracy while half of the FP64 FMAs leave the FP64 pipe.
- *  2: as 1, but the fused reduction (C, S, beta, s; Algorithm 4 lines 1-3) runs on the
+ *  2: as 1, but the fused reduction (C, S, beta, s: the single reduction of Algorithm 4) runs on the
  *     tensor cores as exact integer dot products of fixed-point digit expansions (the
  *     Ozaki scheme: basis entries as round(q 2^56), w and v scaled per 512-row chunk,
  *     FP16 digits, FP32 accumulators that stay exact, one FP64 rounding per chunk), with
@@ -188,12 +188,11 @@ kc_status kc_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y);
 kc_status dcgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0);
 
 /* One DCGS2 step (Algorithm 4): v = A w; the single fused reduction
- * C = Q_k^T w, S = Q_k^T v, beta = w^T w, s = w^T v (Alg. 4 line 1); in the same launch
- * alpha = sqrt(beta - C^T C) (line 4), H(0:k, k-1) = K(0:k, k-1) + C and H(k, k-1) = alpha
- * (lines 10, 12), T = S/alpha, T_k = (s - C^T S)/alpha^2 (lines 5-6, eq. 30),
- * K(0:k+1, k) = T - H(0:k+1, 0:k) C / alpha (line 11, after line 12 since it reads
- * H(k, k-1)); then the fused update q_k = (w - Q_k C)/alpha -> Q(:,k) and
- * w <- v/alpha - Q_k T(0:k) - q_k T_k (lines 7-9).  Requires k+1 < ncap.
+ * C = Q_k^T w, S = Q_k^T v, beta = w^T w, s = w^T v; in the same launch
+ * alpha = sqrt(beta - C^T C), H(0:k, k-1) = K(0:k, k-1) + C and H(k, k-1) = alpha,
+ * T = S/alpha, T_k = (s - C^T S)/alpha^2 (eq. 30), K(0:k+1, k) =
+ * T - H(0:k+1, 0:k) C / alpha (after H(k, k-1), which it reads); then the fused update q_k = (w - Q_k C)/alpha -> Q(:,k) and
+ * w <- v/alpha - Q_k T(0:k) - q_k T_k.  Requires k+1 < ncap.
  * Three kernel launches; no host synchronisation.  Numerical failures are reported
  * through kc_read_status (the step still completes with a guarded alpha). */
 kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);

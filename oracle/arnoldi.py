@@ -27,10 +27,9 @@ class DCGS2Arnoldi:
 
     init(r0): w = r0 unnormalised (the factorised matrix is B = [r0, A Q], Section 1).
     step():   one matvec on the pending w, one fused reduction, the delayed normalisation
-              (Pythagorean trick, Alg. 4 line 4), Stephen's trick for T_k (eq. 30), the
-              projection (Alg. 4 lines 7-9) and the lagged representation update
-              (Alg. 4 lines 10-12, with line 12 executed before line 11 since line 11 reads
-              H_{j-1,j-2}; eq. 52 shows the term belongs).
+              (Pythagorean trick), Stephen's trick for T_k (eq. 30), the projection and
+              the lagged representation update (the new subdiagonal entry is set before
+              the K column that reads it, H_{j-1,j-2}; eq. 52 shows the term belongs).
     finish(): the last column by CGS2 with an explicit norm (end of Section 3: the n-th
               iteration applies CGS2 with two additional reductions).
     """
@@ -56,28 +55,28 @@ class DCGS2Arnoldi:
         Qk = self.Q[:, :k]
         w = self.w
         v = _matvec(self.A, w)                      # v = A w_{j-1} (Section 4, matvec on w)
-        # the single global reduction [Q_{1:j-2}, w_{j-1}]^T [w_{j-1}, A w_{j-1}] (Alg. 4 line 1)
+        # the single global reduction [Q_{1:j-2}, w_{j-1}]^T [w_{j-1}, A w_{j-1}] (Algorithm 4)
         C = Qk.T @ w                                # C_{1:j-2,j-1}
         S = Qk.T @ v                                # S_{1:j-2,j}
         beta = w @ w                                # beta_{j-1}
         s = w @ v                                   # S_{j-1,j}
-        alpha2 = beta - C @ C                       # Alg. 4 line 4 (Pythagoras)
+        alpha2 = beta - C @ C                       # Pythagoras (Algorithm 4)
         if not alpha2 > 0.0:
             raise FloatingPointError("Pythagorean norm is not positive")
         alpha = np.sqrt(alpha2)
-        if k >= 1:                                  # Alg. 4 lines 10 and 12: H column k-1
+        if k >= 1:                                  # H column k-1: K + C, subdiagonal alpha
             self.H[:k, k - 1] = self.K[:k, k - 1] + C
             self.H[k, k - 1] = alpha
             # happy breakdown: A q_{k-1} (nearly) lies in span(Q_k)
             if alpha <= 1e-13 * np.linalg.norm(self.H[:k + 1, k - 1]):
                 self.breakdown = True
         T = np.empty(k + 1)
-        T[:k] = S / alpha                           # Alg. 4 line 6
-        T[k] = (s - C @ S) / alpha ** 2             # Alg. 4 line 5 (Stephen's trick, eq. 30)
-        q = (w - Qk @ C) / alpha                    # Alg. 4 lines 7-8
+        T[:k] = S / alpha                           # first-projection coefficients
+        T[k] = (s - C @ S) / alpha ** 2             # Stephen's trick (eq. 30)
+        q = (w - Qk @ C) / alpha                    # reorthogonalise and normalise
         self.Q[:, k] = q
-        self.w = v / alpha - Qk @ T[:k] - q * T[k]  # Alg. 4 line 9
-        # Alg. 4 line 11: K_{1:j-1,j-1} = T - (1/alpha) H_{1:j-1,1:j-2} C
+        self.w = v / alpha - Qk @ T[:k] - q * T[k]  # projection
+        # K_{1:j-1,j-1} = T - (1/alpha) H_{1:j-1,1:j-2} C (Algorithm 4)
         self.K[:k + 1, k] = T - (self.H[:k + 1, :k] @ C) / alpha
         self.alphas.append(alpha)
         self.k = k + 1

@@ -43,18 +43,18 @@ def dcgs2_arnoldi_rows(A, r0, n, rank, P, allreduce_sum, allgather):
         part = np.concatenate([Qk.T @ w, Qk.T @ v, [w @ w, w @ v]])
         tot = allreduce_sum(part)                            # the one reduction of step k
         C, S, beta, s = tot[:k], tot[k:2 * k], tot[2 * k], tot[2 * k + 1]
-        a2 = beta - C @ C                                    # Pythagoras (Alg. 4 line 4)
+        a2 = beta - C @ C                                    # Pythagoras (Algorithm 4)
         if not a2 > 0.0:
             raise FloatingPointError("beta - C^T C <= 0 at step %d" % k)
         alpha = np.sqrt(a2)
         if k >= 1:
-            H[:k, k - 1] = K[:k, k - 1] + C                  # line 10
-            H[k, k - 1] = alpha                              # line 12
-        T = np.concatenate([S / alpha, [(s - C @ S) / alpha ** 2]])   # lines 5-6, eq. 30
-        q = (w - Qk @ C) / alpha                             # line 7
+            H[:k, k - 1] = K[:k, k - 1] + C                  # H column: K + C
+            H[k, k - 1] = alpha                              # subdiagonal
+        T = np.concatenate([S / alpha, [(s - C @ S) / alpha ** 2]])   # Stephen's trick, eq. 30
+        q = (w - Qk @ C) / alpha                             # reorthogonalise
         Q[:, k] = q
-        K[:k + 1, k] = T - H[:k + 1, :k] @ C / alpha         # line 11
-        w = v / alpha - Qk @ T[:k] - q * T[k]                # lines 8-9
+        K[:k + 1, k] = T - H[:k + 1, :k] @ C / alpha         # lagged correction
+        w = v / alpha - Qk @ T[:k] - q * T[k]                # projection
     # CGS2 finish of the last column (explicit norm)
     Qn = Q[:, :n]
     C1 = allreduce_sum(Qn.T @ w)

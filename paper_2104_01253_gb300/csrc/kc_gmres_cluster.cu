@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_fused(const GcArgs a) {
   int matvecs = 0, cycles = 0, last_status = KC_OK, result = KC_ERR_NOT_CONVERGED;
   double rn = 0.0, est = 0.0, bnorm = 0.0, target = 0.0;
   // H below its subdiagonal is never written but is read by the K-column product
-  // (line 11 over the full H(0:k, 0:k-1)): zero it (the global copy is zeroed by the host)
+  // (T - H(0:k, 0:k-1) C / alpha over the full block): zero it (the global copy is zeroed by the host)
   if (rank == 0 && a.smem_h)
     for (int i = tid; i < (n + 1) * n; i += GC_THREADS) Hm[i] = 0.0;
 
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_fused(const GcArgs a) {
       }
       if (!comm.sum(part[pb], pb, tot, 2 * k + 2)) goto failed;
       pb ^= 1;
-      // scalar step (every CTA): Pythagoras (Alg. 4 line 4), T (lines 5-6, eq. 30)
+      // scalar step (every CTA): Pythagoras, T (eq. 30)
       if (warp == 0) {
         double cc = 0.0, cs = 0.0;
         for (int i = lane; i < k; i += 32) {
@@ -393,8 +393,8 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_gmres_fused(const GcArgs a) {
         wb[i] = wn;
         if (a.smem_q) wg[i] = wn;
       }
-      // CTA 0: H(0:k, k-1) = K(0:k, k-1) + C, H(k, k-1) = alpha (lines 10, 12);
-      // K(0:k, k) = T - H(0:k, 0:k-1) C / alpha (line 11); Givens of column k-1
+      // CTA 0: H(0:k, k-1) = K(0:k, k-1) + C, H(k, k-1) = alpha;
+      // K(0:k, k) = T - H(0:k, 0:k-1) C / alpha; Givens of column k-1
       if (rank == 0) {
         if (k >= 1) {
           for (int i = tid; i < k; i += GC_THREADS)

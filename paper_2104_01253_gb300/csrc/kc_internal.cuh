@@ -28,7 +28,7 @@ constexpr int UPD_THREADS = 256;
 struct Scalars {
   double C[NMAX];       // delayed reorthogonalisation coefficients C_{0:k-1}
   double S[NMAX];       // projections of v (S_{0:k-1}), or a second coefficient set
-  double T[NMAX + 1];   // T_{0:k}: scaled projection (Alg. 4 lines 5-6)
+  double T[NMAX + 1];   // T_{0:k}: scaled projection (Algorithm 4, eq. 30)
   double C2[NMAX];      // second CGS2 pass coefficients (finish / CGS2 baseline)
   double alpha, inv_alpha, beta, s;
   double vscale;        // factor of v in the update: 1/alpha (Arnoldi), 1 (QR of given columns)

@@ -141,9 +141,9 @@ __device__ __forceinline__ void set_status(Scalars* sc, int st) {
 
 // The scalar step of Algorithm 4 after alpha is known (all threads of one CTA).
 // Inputs in sc: C (C_{0:k-1}), S (raw S_{0:k-1} = Q_k^T v), s (= w^T v), cs (= C^T S).
-//   T_{0:k-1} = S/alpha (line 6), T_k = (s - C^T S)/alpha^2 (line 5, eq. 30);
-//   H(0:k, k-1) = K(0:k, k-1) + C (line 10), H(k, k-1) = alpha (line 12);
-//   K(0:k, k) = T - H(0:k, 0:k-1) C / alpha (line 11; the flexible variant keeps K = T);
+//   T_{0:k-1} = S/alpha, T_k = (s - C^T S)/alpha^2 (eq. 30);
+//   H(0:k, k-1) = K(0:k, k-1) + C, H(k, k-1) = alpha;
+//   K(0:k, k) = T - H(0:k, 0:k-1) C / alpha (the flexible variant keeps K = T);
 //   GMRES: Givens rotation of the finalised column k-1.
 __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha) {
   // The last CTA runs this once per step, so its dependent FP64 chains (about 70 cycles a
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __
 }
 
 // Last CTA of a reduction: deterministic sum of the per-CTA partials, then either a plain
-// store of Q^T x or the scalar step of Algorithm 4 (lines 4-6, 10-12).
+// store of Q^T x or the scalar step of Algorithm 4.
 __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int NRHS,
                                 Scalars* __restrict__ sc, int epilogue, const StepArgs& sa,
                                 int nparts = -1) {
@@ -273,7 +273,7 @@ __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int 
     return;
   }
 
-  // ---- scalar step of Algorithm 4 (lines 4-6 and 10-12), FP64 -------------------------
+  // ---- scalar step of Algorithm 4, FP64 --------------------------------------------------
   // tot[2i] = C_i, tot[2i+1] = S_i (i < k); tot[2k] = beta, tot[2k+1] = s
   __shared__ int s_ok;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
@@ -290,7 +290,7 @@ __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int 
     cs = warp_sum(cs);
     if (threadIdx.x == 0) {
       const double beta = tot[2 * k], s = tot[2 * k + 1];
-      double a2 = beta - cc;                                 // Pythagoras, line 4
+      double a2 = beta - cc;                                 // Pythagoras
       sc->beta = beta;
       sc->s = s;
       sc->cs = cs;
@@ -433,7 +433,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
 }
 
 // ----------------------------------------------------------------------------------------
-// K2': fused update of Algorithm 4 lines 7-9.
+// K2': fused update of Algorithm 4 (normalisation and projection).
 //   u = w - Q_k C;  q_k = u / alpha -> Q(:,k);  w <- v/alpha - Q_k T(0:k) - q_k T_k
 // One pass over Q_k; C and T are staged in shared memory.
 // ----------------------------------------------------------------------------------------
@@ -562,12 +562,12 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // FP64 with offload.  This GPU executes about 2 FP64 FMAs per SM per clock against
 // ~128 FP32 operations, so the two FP64 passes of a DCGS2 step are FP64-pipe bound.
 // Only half of their products need FP64: the reorthogonalisation coefficients
-// C = Q^T w (Alg. 4 line 3: a tiny result of heavy cancellation that enters H and q
-// directly) and the projection w <- v/alpha - Q T (line 9: its rounding error is the
-// Arnoldi representation error).  The first-projection coefficients S = Q^T v (line 2)
+// C = Q^T w (a tiny result of heavy cancellation that enters H and q
+// directly) and the projection w <- v/alpha - Q T (its rounding error is the
+// Arnoldi representation error).  The first-projection coefficients S = Q^T v
 // only need to be accurate enough for the next step's delayed reorthogonalisation to
 // remove what they leave behind (any error d in S reappears as -d/alpha in the next C and
-// cancels in H = K + C), and the product Q C in q = (w - Q C)/alpha (line 7) is
+// cancels in H = K + C), and the product Q C in q = (w - Q C)/alpha is
 // multiplied by the tiny C.  Both are evaluated here in float-float arithmetic
 // (operands split into two floats by integer operations, exact TwoProd products,
 // TwoSum accumulation; about 2^-44 relative), on the FP32/INT pipes, concurrently with

@@ -1,5 +1,5 @@
 // Fused DCGS2 reduction on the tensor cores (FP64 mode 2): C = Q^T w, S = Q^T v,
-// beta = w^T w and s = w^T v (Algorithm 4 lines 1-3) as exact integer dot products of
+// beta = w^T w and s = w^T v (the single reduction of Algorithm 4) as exact integer dot products of
 // fixed-point digit expansions, then the scalar step in the last CTA.
 //
 // Arithmetic (the Ozaki scheme on integer digits: Ozaki, Ogita, Oishi and Rump, Numer.

@@ -1,4 +1,4 @@
-// TMA-staged fused DCGS2 reduction (Algorithm 4 lines 1-3: C = Q^T w, S = Q^T v,
+// TMA-staged fused DCGS2 reduction (the single reduction of Algorithm 4: C = Q^T w, S = Q^T v,
 // beta = w^T w, s = w^T v, then the scalar step in the last CTA).
 //
 // One producer thread streams tiles of RT_TR rows: for every chunk of RT_CH basis columns

@@ -27,7 +27,7 @@ struct StagedCtl {
   int abort;
 };
 
-// DCGS2 update (Algorithm 4 lines 7-9), FP64; OFF: Q C in float-float (offload mode).
+// DCGS2 update (Algorithm 4: normalisation and projection), FP64; OFF: Q C in float-float (offload mode).
 template <bool OFF>
 __global__ void __launch_bounds__(ST_THREADS, 1)
 k_update_staged(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__ w,

@@ -165,7 +165,7 @@ def _crafted_step_errors(cls):
     pending vector w = alpha_3 q_3 + Q_3 c (c random, O(1)) and K[:, 2] = H[:3, 2] - c, so
     the delayed reorthogonalisation must remove c.  One step plus the CGS2 finish must
     reproduce alpha_3 (Pythagoras), q_3, column 2 of H, and column 3 of H (which needs
-    the correction H C / alpha of Algorithm 4 line 11); after the step, the new pending
+    the correction H C / alpha of Algorithm 4); after the step, the new pending
     vector is orthogonal to q_0..q_3 (Stephen's trick, eq. 30, for the q_3 component).
     Returns the worst relative deviation."""
     rng = np.random.default_rng(12)
