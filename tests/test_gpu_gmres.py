@@ -69,6 +69,34 @@ def test_config1_converges_to_1e10(kc, ctx, path):
     assert abs(info["iters"] - io["iters"]) <= 2
 
 
+def test_tensor_core_reduction_mode_in_gmres(kc, ctx):
+    """FP64 mode 2 (the reduction as exact digit products on the tensor cores) inside the
+    multi-kernel GMRES path, whose reduction epilogue also runs the Givens update: one
+    cycle matches the oracle to 1e-10 and the full solve converges like the oracle."""
+    Ah = config1_operator()
+    b = gaussian_vector(Ah.m, 1001)
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(b, device="cuda")
+    ctx.set_gmres_path(1)
+    ctx.set_fp64_mode(2)
+    try:
+        x = torch.zeros_like(bd)
+        info = kc.gmres_solve(ctx, A, bd, x, restart=30, rtol=1e-10, maxit=30)
+        xo, io = orc_gmres(Ah.to_scipy(), b, restart=30, rtol=1e-10, maxit=30)
+        assert info["iters"] == io["iters"] == 30
+        assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-10
+        x.zero_()
+        info = kc.gmres_solve(ctx, A, bd, x, restart=30, rtol=1e-10)
+        assert info["status"] == 0
+        true = np.linalg.norm(b - Ah.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b)
+        assert true <= 1e-10
+        _, io = orc_gmres(Ah.to_scipy(), b, restart=30, rtol=1e-10)
+        assert abs(info["iters"] - io["iters"]) <= 2
+    finally:
+        ctx.set_fp64_mode(1)
+        ctx.set_gmres_path(0)
+
+
 @pytest.mark.parametrize("path", PATHS, indirect=True)
 def test_early_convergence_inside_a_cycle(kc, ctx, path):
     """A well-conditioned operator converges before the basis fills: the device stop flag
