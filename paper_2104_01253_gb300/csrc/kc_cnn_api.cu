@@ -102,11 +102,17 @@ k_fgm_jacobi(const double* __restrict__ w, const double* __restrict__ dinv,
     u[i] = w[i] * dinv[i];
 }
 
-// network input: w / rms(w) in FP32 (rms from the norm kernel's sum of squares)
+// network input: w / rms(w) in FP32 (rms from the norm kernel's sum of squares; the square
+// root and reciprocal once per CTA: per thread they cost more FP64 work than the pass)
 __global__ void k_fgm_prep(const double* __restrict__ w, float* __restrict__ x, int64_t m,
                            const Scalars* __restrict__ sc) {
-  const double rms = sqrt(sc->norm_sq / (double)m);
-  const double inv = rms > 0.0 ? 1.0 / rms : 0.0;
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    const double rms = sqrt(sc->norm_sq / (double)m);
+    s_inv = rms > 0.0 ? 1.0 / rms : 0.0;
+  }
+  __syncthreads();
+  const double inv = s_inv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = (float)(w[i] * inv);
@@ -116,7 +122,10 @@ __global__ void k_fgm_prep(const double* __restrict__ w, float* __restrict__ x, 
 // the learned correction
 __global__ void k_fgm_post(const float* __restrict__ y, const double* __restrict__ w,
                            double* __restrict__ z, int64_t m, const Scalars* __restrict__ sc) {
-  const double rms = sqrt(sc->norm_sq / (double)m);
+  __shared__ double s_rms;
+  if (threadIdx.x == 0) s_rms = sqrt(sc->norm_sq / (double)m);
+  __syncthreads();
+  const double rms = s_rms;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
     z[i] = w[i] + (double)y[i] * rms;
