@@ -102,6 +102,45 @@ k_fgm_jacobi(const double* __restrict__ w, const double* __restrict__ dinv,
     u[i] = w[i] * dinv[i];
 }
 
+// u = D^{-1} w and sc->norm_sq = u^T u in one pass (the input scale of the network): CTA
+// sums written in CTA order, added by the last CTA in a fixed order (lane-strided, then a
+// warp tree), so the result is deterministic; the ticket counter is reset for the next call
+__global__ void __launch_bounds__(256)
+k_fgm_jacobi_sq(const double* __restrict__ w, const double* __restrict__ dinv,
+                double* __restrict__ u, int64_t m, double* __restrict__ partials,
+                unsigned int* __restrict__ counter, Scalars* __restrict__ sc) {
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[i] * dinv[i];
+    u[i] = v;
+    a = fma(v, v, a);
+  }
+  __shared__ double red[8];
+  __shared__ unsigned int ticket;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if (lane == 0) red[warp] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    partials[blockIdx.x] = t;
+    __threadfence();
+    ticket = atomicAdd(counter, 1u);
+  }
+  __syncthreads();
+  if (ticket != gridDim.x - 1 || warp != 0) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = lane; i < (int)gridDim.x; i += 32) t += __ldcg(partials + i);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0) {
+    sc->norm_sq = t;
+    *counter = 0u;
+  }
+}
+
 // network input: w / rms(w) in FP32 (rms from the norm kernel's sum of squares; the square
 // root and reciprocal once per CTA: per thread they cost more FP64 work than the pass)
 __global__ void k_fgm_prep(const double* __restrict__ w, float* __restrict__ x, int64_t m,
@@ -370,10 +409,9 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
       sa.k = k;
       if (use_net) {   // zhat = u + rms(u) net(u / rms(u)), u = D^{-1} w
         timing_begin(ctx, KID_OTHER);
-        k_fgm_jacobi<<<g, 256, 0, ctx->stream>>>(w, dinv, u, m);
+        k_fgm_jacobi_sq<<<g, 256, 0, ctx->stream>>>(w, dinv, u, m, ctx->partials,
+                                                     ctx->counters + 3, ctx->scal);
         KC_LAUNCHED(ctx);
-        StepArgs sn = {};
-        if ((s = launch_norm(ctx, u, nullptr, m, KC_F64, NEPI_INIT, sn)) != KC_OK) return s;
         timing_begin(ctx, KID_OTHER);
         k_fgm_prep<<<g, 256, 0, ctx->stream>>>(u, xin, m, ctx->scal);
         KC_LAUNCHED(ctx);
