@@ -18,7 +18,12 @@ the Jacobi step plus the learned correction (D = diag(A)).
 Pins: tests/test_oracle_cnn.py (central finite differences of both losses for weight and
 input gradients; a 1x1-equivalent kernel against a hand-computed stencil; homogeneity;
 a network that computes c x exactly, giving closed-form losses and M(w) = (1 + c) D^{-1} w;
-zero weights giving the Jacobi preconditioner).
+zero weights giving the Jacobi preconditioner).  The BF16-storage variants
+(forward_bf16_storage, loss_and_grads_bf16_storage, backward(bf16=True), the residual loss
+with bf16=True): a 1 x 1-image chain of three layers whose output, loss and gradients are
+written in closed form on rationals with every rounding point changing its value, and
+dyadic weights and inputs for which nothing rounds, where they equal the FP64 functions
+bit for bit; the rounding itself is gmres.round_bf16 (golden values).
 
 This module is test infrastructure: only tests, the smoke check and the CPU baseline of
 the benchmark use it.
@@ -26,6 +31,8 @@ the benchmark use it.
 from __future__ import annotations
 
 import numpy as np
+
+from .gmres import round_bf16
 
 CHANNELS = (1, 32, 32, 32, 32, 32, 1)
 
@@ -94,11 +101,10 @@ def loss_and_grads(ws, r, e):
 
 
 def _round_bf16(x):
-    """Round float64 values to the nearest bfloat16 (ties to even), as float64."""
-    f = np.asarray(x, dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    """Round to the nearest bfloat16 (ties to even), as float64: the value is first taken to
+    float32 (the GPU's accumulator type) and then rounded by gmres.round_bf16, whose
+    results are pinned by golden values."""
+    return round_bf16(np.asarray(x, dtype=np.float64).astype(np.float32)).astype(np.float64)
 
 
 def forward_bf16_storage(ws, x):
@@ -118,20 +124,15 @@ def forward_bf16_storage(ws, x):
 
 def loss_and_grads_bf16_storage(ws, r, e):
     """loss_and_grads with the GPU's storage rounding: BF16 weights, BF16 hidden
-    activations and BF16 hidden-layer gradients dL/dz (the output gradient stays FP64)."""
+    activations and BF16 hidden-layer gradients dL/dz (the output gradient stays FP64).
+    Returns L, dL/dW per layer and the network output y."""
     B = r.shape[0]
-    wb = [_round_bf16(W) for W in ws]
     y, acts = forward_bf16_storage(ws, r)
     diff = y - e
     en = np.sum(e * e, axis=(1, 2, 3))
     L = float(np.mean(np.sum(diff * diff, axis=(1, 2, 3)) / en))
     g = (2.0 / B) * diff / en[:, None, None, None]
-    grads = [None] * len(ws)
-    for li in range(len(ws) - 1, -1, -1):
-        if li < len(ws) - 1:
-            g = _round_bf16(g * (acts[li + 1] > 0.0))
-        gW, g = conv3x3_backward(acts[li], wb[li], g)
-        grads[li] = gW
+    grads, _ = backward(ws, acts, g, bf16=True)
     return L, grads, y
 
 

@@ -2,8 +2,10 @@
 
 loo: loss of orthogonality ||I - Q^T Q||_F.
 rre: relative representation error ||A Q_{:,0:n} - Q H||_F / ||A||_F (Arnoldi relation).
-Both are plain definitions; they are pinned by exact orthonormal / exact Arnoldi inputs in
-tests/test_oracle_arnoldi.py.
+Both are plain definitions; tests/test_oracle_metrics.py pins them with closed-form values:
+two unit columns at a known angle, orthogonal columns off unit norm, an exact Arnoldi pair
+of a scaled cyclic shift (rre = 0) and planted perturbations of one entry of H or of the
+last basis column with known rre = |delta| / ||A||_F.
 """
 import numpy as np
 
