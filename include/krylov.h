@@ -203,6 +203,15 @@ kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
  * Afterwards Q has k+1 columns and H is (k+1) x k. */
 kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 
+/* Gram matrix of a basis, G = Q^T Q, for the loss of orthogonality ||I - Q^T Q||_F
+ * (Section 5.1).  Q: device, column-major with leading dimension ldq >= m, ncols columns
+ * (1 <= ncols <= 128) of type q_dtype (KC_F64, KC_F32 or KC_BF16); G: device FP64,
+ * ncols x ncols column-major, overwritten.  Products and sums in FP64; the per-block
+ * sums are combined with atomics, so the last bits of G may vary from call to call.
+ * Asynchronous on the context stream. */
+kc_status kc_basis_gram(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int64_t m,
+                        int ncols, double* G);
+
 /* One FP64 DCGS2 step, as dcgs2_arnoldi_step in its all-FP64 mode, that allocates
  * nothing and needs no context.  (The paper has no counterpart: this is a deployment
  * variant.)  It is meant for callers that cannot call cudaMalloc: code running inside
@@ -218,9 +227,20 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
  * first call before any stream capture.  All calls share the one array and it keeps the
  * last call's contents; the call clears what must start at zero (ticket, flags), and two
  * calls that overlap on the GPU (different streams, concurrent graphs) race on it.
+ * The looked-up address is kept for the rest of the process: a cudaDeviceReset, which
+ * unloads the library from the device, leaves this entry point unusable on that device
+ * until the process exits.
  * Enqueued on `cuda_stream` (a cudaStream_t, NULL for the legacy stream); returns
- * KC_ERR_CUDA if the set-up or a launch fails.  Numerical status is not reported. */
+ * KC_ERR_CUDA if the set-up or a launch fails.  Numerical failures of the step (a
+ * non-positive Pythagorean norm, a breakdown, a non-finite value) are kept in the shared
+ * array's status word until the next call clears it: dcgs2_noalloc_read_status reads it. */
 kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st, void* cuda_stream);
+
+/* The status word of the last dcgs2_arnoldi_step_noalloc call on the current device
+ * (KC_OK or the first numerical failure of that step), copied to the host int *status
+ * after waiting for `cuda_stream`.  Allocates nothing; the paper has no counterpart.
+ * Returns KC_ERR_INVALID_ARG for a NULL status and KC_ERR_CUDA if the copy fails. */
+kc_status dcgs2_noalloc_read_status(int* status, void* cuda_stream);
 
 /* ---- baselines ---------------------------------------------------------------------- */
 
@@ -253,6 +273,10 @@ typedef struct {
   double inner_rtol;      /* IR: inner solve tolerance (relative to its right-hand side) */
   int32_t inner_max_cycles; /* IR: cycles per inner solve */
   int32_t precond;        /* fgmres_solve only: a kc_precond_kind (gmres_solve ignores it) */
+  int32_t diag_loo;       /* gmres_solve diagnostics: 1 = after every (inner) cycle form the
+                             Gram matrix of its basis (kc_basis_gram) and report the largest
+                             ||I - Q^T Q||_F in kc_gmres_info.max_loo (one extra pass of
+                             O(m n^2) FP64 work per cycle, and the multi-kernel path) */
 } kc_gmres_opts;
 
 /* Right preconditioner of fgmres_solve. */
@@ -268,6 +292,8 @@ typedef struct {
   int32_t status;         /* kc_status of the solve */
   double rel_resid_est;   /* last Givens estimate |g_k| / ||b|| */
   double rel_resid_true;  /* FP64 ||b - A x|| / ||b|| recomputed on the device */
+  double max_loo;         /* largest ||I - Q^T Q||_F over the cycles' bases when
+                             kc_gmres_opts.diag_loo is set, else -1 (Section 5.1 metric) */
 } kc_gmres_info;
 
 /* Restarted DCGS2-GMRES(n) (FP64), or FP32/BF16-basis DCGS2-GMRES inside FP64 iterative

@@ -98,7 +98,7 @@ class Context:
         return n.value, g.value
 
     KERNEL_KINDS = ("spmv", "reduce", "dcgs2_update", "gemv_sub", "norm", "scale", "axpy",
-                    "small", "other")
+                    "small", "other", "finish_reduce")
 
     def timing_enable(self, on=True):
         self.check(self.lib.kc_timing_enable(self.handle, 1 if on else 0))
@@ -245,19 +245,34 @@ def mgs_arnoldi_step(ctx: Context, A: DeviceCSR, st: ArnoldiState):
 
 def gmres_solve(ctx: Context, A: DeviceCSR, b, x, restart=30, rtol=1e-10, maxit=100000,
                 precision=0, A32: DeviceCSR = None, max_outer=50, inner_rtol=1e-4,
-                inner_max_cycles=3):
+                inner_max_cycles=3, diag_loo=False):
     """Restarted DCGS2-GMRES (precision 0) or FP32 / BF16-basis inner solves in FP64
-    iterative refinement (precision 1 / 2).  x holds x0 and receives the solution."""
+    iterative refinement (precision 1 / 2).  x holds x0 and receives the solution.
+    diag_loo: also report the largest loss of orthogonality over the cycles' bases."""
     opts = kc_gmres_opts(restart, maxit, precision, max_outer, rtol, inner_rtol,
-                         inner_max_cycles, 0)
+                         inner_max_cycles, 0, 1 if diag_loo else 0)
     info = kc_gmres_info()
     a32 = C.byref(A32.c) if A32 is not None else None
     st = ctx.lib.gmres_solve(ctx.handle, C.byref(A.c), a32, _ptr(b), _ptr(x), C.byref(opts),
                              C.byref(info))
     if st not in (0, _lib.KC_ERR_NOT_CONVERGED):
         ctx.check(st)
-    return dict(iters=info.iters, restarts=info.restarts, outer=info.outer, status=st,
-                rel_resid_est=info.rel_resid_est, rel_resid_true=info.rel_resid_true)
+    out = dict(iters=info.iters, restarts=info.restarts, outer=info.outer, status=st,
+               rel_resid_est=info.rel_resid_est, rel_resid_true=info.rel_resid_true)
+    if diag_loo:
+        out["max_loo"] = info.max_loo
+    return out
+
+
+def basis_gram(ctx: Context, Q, m: int, ncols: int, q_dtype=None):
+    """G = Q^T Q (FP64, ncols x ncols) of the first ncols columns of a basis stored like
+    ArnoldiState.Qbuf (one column per row of the tensor, leading dimension Q.shape[1])."""
+    import torch
+    dt = {torch.float64: _lib.KC_F64, torch.float32: _lib.KC_F32,
+          torch.bfloat16: _lib.KC_BF16}[Q.dtype] if q_dtype is None else q_dtype
+    G = torch.empty((ncols, ncols), dtype=torch.float64, device=Q.device)
+    ctx.check(ctx.lib.kc_basis_gram(ctx.handle, _ptr(Q), Q.shape[1], dt, m, ncols, _ptr(G)))
+    return G
 
 
 def krylov_schur_eigs(ctx: Context, A: DeviceCSR, v0, nev=10, ncv=40, nkeep=20, tol=1e-10,

@@ -36,13 +36,14 @@ class kc_arnoldi(C.Structure):
 class kc_gmres_opts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("maxit", C.c_int32), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("rtol", C.c_double), ("inner_rtol", C.c_double),
-                ("inner_max_cycles", C.c_int32), ("precond", C.c_int32)]
+                ("inner_max_cycles", C.c_int32), ("precond", C.c_int32),
+                ("diag_loo", C.c_int32)]
 
 
 class kc_gmres_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("outer", C.c_int32),
                 ("status", C.c_int32), ("rel_resid_est", C.c_double),
-                ("rel_resid_true", C.c_double)]
+                ("rel_resid_true", C.c_double), ("max_loo", C.c_double)]
 
 
 class kc_ks_opts(C.Structure):
@@ -71,6 +72,8 @@ _SIGS = {
     "dcgs2_arnoldi_step": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),
     "dcgs2_arnoldi_finish": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),
     "dcgs2_arnoldi_step_noalloc": ([C.POINTER(kc_csr), C.POINTER(kc_arnoldi), _P], C.c_int),
+    "dcgs2_noalloc_read_status": ([C.POINTER(C.c_int), _P], C.c_int),
+    "kc_basis_gram": ([_P, _P, C.c_int64, C.c_int, C.c_int64, C.c_int, _P], C.c_int),
     "dcgs2_qr": ([_P, _P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int], C.c_int),
     "cgs2_arnoldi_init": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi), _P], C.c_int),
     "cgs2_arnoldi_step": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),

@@ -75,7 +75,7 @@ void timing_begin(kc_ctx* ctx, int kid) {
     ctx->trec_cap = ncap;
   }
   TimingRec& r = ctx->trec[ctx->trec_len];
-  r.kid = kid;
+  r.kid = (ctx->timing_phase == 1 && kid == KID_REDUCE) ? KID_FIN_REDUCE : kid;
   cudaEventRecord(r.a, ctx->stream);
 }
 
@@ -304,6 +304,11 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
   if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
   const int vec = vec_of(st);
   StepArgs sa = step_args(st, k, 0);
+  struct Phase {                       // the finish's reductions are timed on their own
+    kc_ctx* c;
+    explicit Phase(kc_ctx* cc) : c(cc) { c->timing_phase = 1; }
+    ~Phase() { c->timing_phase = 0; }
+  } phase(ctx);
   KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, nullptr, A->m, vec,
                        EPI_STORE_C, sa));                                // C1 = Q^T w
   KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec, 0));

@@ -334,6 +334,7 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
   if (((uintptr_t)b & 15) || ((uintptr_t)x & 15))
     return fail(ctx, KC_ERR_INVALID_ARG, "b and x must be 16-byte aligned");
   memset(info, 0, sizeof(*info));
+  info->max_loo = -1.0;
   const int64_t m = A->m;
   const int64_t ld = (m + 31) / 32 * 32;
   size_t off = 0;

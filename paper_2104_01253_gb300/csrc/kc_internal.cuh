@@ -118,7 +118,7 @@ enum StepFlags : int { SF_FLEXIBLE = 1, SF_GIVENS = 2, SF_FALLBACK = 4, SF_QR = 
 namespace kc {
 enum KernelId : int {
   KID_SPMV = 0, KID_REDUCE, KID_UPDATE, KID_GEMV_SUB, KID_NORM, KID_SCALE, KID_AXPY,
-  KID_SMALL, KID_OTHER, KID_COUNT
+  KID_SMALL, KID_OTHER, KID_FIN_REDUCE, KID_COUNT
 };
 struct TimingRec { cudaEvent_t a, b; int kid; };
 }  // namespace kc
@@ -149,6 +149,7 @@ struct kc_ctx {
   int barrier_test;        // test hook: the next grid-form solve's first barrier times out
   // optional per-kernel timing: events recorded around every launch on ctx->stream
   int timing_on;
+  int timing_phase;     // 1 inside dcgs2_arnoldi_finish: its reductions count as KID_FIN_REDUCE
   kc::TimingRec* trec;
   int trec_len, trec_cap;
   char err[512];
@@ -224,6 +225,11 @@ kc_status launch_scale_to(kc_ctx* ctx, const void* x, void* qcol, int q_dtype, i
 kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_t m,
                         int vec_dtype);
 kc_status ensure_workspace(kc_ctx* ctx, size_t bytes);
+// Gram matrix G = Q^T Q (FP64, ncols x ncols, column-major) and ||I - G||_F (kc_gram.cu):
+// out[0] = the value, out[1] = max(out[1], value)
+kc_status launch_gram(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int64_t m,
+                      int ncols, double* G);
+kc_status launch_loo_from_gram(kc_ctx* ctx, const double* G, int ncols, double* out);
 kc_status launch_update_staged(kc_ctx* ctx, double* Q, int64_t ldq, int k, double* w,
                                const double* v, int64_t m);
 // convolutional preconditioner (kc_cnn.cu)

@@ -1448,3 +1448,19 @@ extern "C" kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st,
   st->k = k + 1;
   return KC_OK;
 }
+
+extern "C" kc_status dcgs2_noalloc_read_status(int* status, void* cuda_stream) {
+  using namespace kc;
+  if (!status) return KC_ERR_INVALID_ARG;
+  NoAllocScratch* scr = nullptr;
+  kc_status s = noalloc_setup(&scr);
+  if (s != KC_OK) return s;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  int v = KC_OK;
+  if (cudaMemcpyAsync(&v, &scr->sc.status, sizeof(int), cudaMemcpyDeviceToHost, stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return KC_ERR_CUDA;
+  *status = v;
+  return KC_OK;
+}

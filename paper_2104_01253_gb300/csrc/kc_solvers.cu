@@ -133,6 +133,8 @@ struct Cycle {
   double* K;
   double* R;
   int n;
+  double* gram;     // diagnostics: (n+1)^2 Gram matrix and loo[2] (NULL: off)
+  double* loo;
 };
 
 // One GMRES(n) cycle: expansion with lagged Givens rotations, then x += Q y.
@@ -181,6 +183,15 @@ static kc_status gmres_cycle(kc_ctx* ctx, const kc_csr* A, const Cycle& c, void*
   KC_LAUNCHED(ctx);
   if ((s = read_scalars(ctx)) != KC_OK) return s;
   const Scalars* h = ctx->scal_host;
+  if (c.gram) {
+    // loss of orthogonality of this cycle's basis: n + 1 columns after the CGS2 finish, the
+    // ncols columns built before an early stop
+    const int cols = h->stop ? h->ncols : c.n + 1;
+    if (cols >= 1) {
+      if ((s = launch_gram(ctx, c.Q, c.ldq, c.qdt, m, cols, c.gram)) != KC_OK) return s;
+      if ((s = launch_loo_from_gram(ctx, c.gram, cols, c.loo)) != KC_OK) return s;
+    }
+  }
   *ncols_out = h->ncols;
   *est_out = h->resid_est;
   *matvecs += (h->stop && h->ncols < c.n) ? h->ncols + 1 : c.n;
@@ -218,6 +229,7 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   if (((uintptr_t)b & 15) || ((uintptr_t)x & 15))
     return fail(ctx, KC_ERR_INVALID_ARG, "b and x must be 16-byte aligned");
   memset(info, 0, sizeof(*info));
+  info->max_loo = -1.0;
   const int64_t m = A->m;
   const int64_t ldq = (m + 31) / 32 * 32;
   const int qdt = prec == 0 ? KC_F64 : (prec == 1 ? KC_F32 : KC_BF16);
@@ -236,6 +248,7 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   const size_t od = off; off = align256(off + (size_t)ldq * 4);
   const size_t orhs = off; off = align256(off + (size_t)ldq * 4);
   const size_t oout = off; off = align256(off + 8 * sizeof(double));
+  const size_t ogram = off; off = align256(off + (size_t)(n + 1) * (n + 1) * 8 + 2 * 8);
   const size_t ogrid = off; off = align256(off + gmres_grid_workspace(ctx));
   if ((s = ensure_workspace(ctx, off)) != KC_OK) return s;
   char* ws = (char*)ctx->ws;
@@ -243,6 +256,9 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   c.Q = ws + oQ; c.ldq = ldq; c.qdt = qdt; c.vec = prec == 0 ? KC_F64 : KC_F32;
   c.w = ws + ow; c.v = ws + ov; c.H = (double*)(ws + oH); c.K = (double*)(ws + oK);
   c.R = (double*)(ws + oR); c.n = n;
+  c.gram = opts->diag_loo ? (double*)(ws + ogram) : nullptr;
+  c.loo = opts->diag_loo ? (double*)(ws + ogram) + (size_t)(n + 1) * (n + 1) : nullptr;
+  if (c.loo) KC_CUDA(ctx, cudaMemsetAsync(c.loo, 0, 2 * sizeof(double), ctx->stream));
   double* r64 = (double*)(ws + or64);
   double* v64 = (double*)(ws + ov64);
   float* d32 = (float*)(ws + od);
@@ -251,7 +267,7 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   KC_CUDA(ctx, cudaMemsetAsync(c.K, 0, (size_t)(n + 1) * n * 8, ctx->stream));
 
   // small FP64 problems: the whole solve in one launch (one cluster, or the whole grid)
-  const int path = prec != 0 ? 1 : (ctx->gmres_path != 0 ? ctx->gmres_path
+  const int path = (prec != 0 || opts->diag_loo) ? 1 : (ctx->gmres_path != 0 ? ctx->gmres_path
                                     : (gmres_grid_preferred(ctx, m, n) ? 3 : 1));
   if (path >= 2) {
     double out[7];
@@ -327,6 +343,12 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
       KC_LAUNCHED(ctx);
       outer++;
     }
+  }
+  if (c.loo) {
+    double lv[2];
+    KC_CUDA(ctx, cudaMemcpyAsync(lv, c.loo, sizeof(lv), cudaMemcpyDeviceToHost, ctx->stream));
+    KC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    info->max_loo = lv[1];
   }
   info->iters = matvecs;
   info->restarts = cycles;

@@ -3,8 +3,11 @@
 The network stores BF16 weights, activations and hidden gradients and accumulates in
 FP32; the oracle counterpart applies the same BF16 rounding points in FP64
 (oracle.cnn.forward_bf16_storage / loss_and_grads_bf16_storage).  Remaining differences
-come from FP32 accumulation order, which can flip the rounding of a few BF16 values:
-tolerance 5e-3 relative (L2) for outputs and 2e-2 for weight gradients.
+come from the FP32 accumulation, which moves a sum across a BF16 rounding boundary for a
+small fraction of the hidden values; each such value then differs by one BF16 unit
+(2^-8 relative) and the difference travels through the later layers.  The comparison is
+element by element: max |y - y_o| <= TOL_Y max |y_o| over every output pixel and
+max |g - g_o| <= TOL_G max |g_o| over every entry of each layer's weight gradient.
 """
 import numpy as np
 import pytest
@@ -15,6 +18,14 @@ pytestmark = pytest.mark.gpu
 from oracle import cnn  # noqa: E402
 from oracle.gmres import gmres as orc_gmres  # noqa: E402
 from synth import convdiff_csr, gaussian_vector, varcoef_fields_2d  # noqa: E402
+
+TOL_Y = 2e-2       # outputs: max-abs error over max-abs value
+TOL_G = 3e-2       # weight gradients, per layer
+
+
+def elementwise(a, ref):
+    """max |a - ref| / max |ref| (element by element)."""
+    return float(np.abs(np.asarray(a, dtype=np.float64) - ref).max() / np.abs(ref).max())
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +69,7 @@ def test_tcgen05_conv_single_tile(kc, ctx):
     assert ctx.read_status() == 0
     yo, _ = cnn.forward_bf16_storage(unpack(w32, ws), x.astype(np.float64))
     y = yd.cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 5e-3
+    assert elementwise(y, yo) <= TOL_Y
 
 
 @pytest.mark.parametrize("conv", [0, 1])
@@ -78,7 +89,9 @@ def test_forward_matches_oracle(kc, ctx, B, H, W, conv):
         ctx.set_conv_kernel(ctx.CONV_TCGEN05)
     y = yd.cpu().numpy().astype(np.float64)
     yo, _ = cnn.forward_bf16_storage(unpack(w32, ws), x.astype(np.float64))
-    assert np.linalg.norm(y - yo) / np.linalg.norm(yo) <= 5e-3
+    err = elementwise(y, yo)
+    print("forward %s conv %d: %.2e" % ((B, H, W), conv, err))
+    assert err <= TOL_Y
 
 
 @pytest.mark.parametrize("conv", [0, 1])
@@ -103,12 +116,98 @@ def test_gradients_match_oracle(kc, ctx, conv, B, H, W):
     assert abs(loss - Lo) <= 1e-3 * Lo
     g = unpack(grad.cpu().numpy(), ws)
     for li in range(6):
-        rel = np.linalg.norm(g[li] - go[li]) / np.linalg.norm(go[li])
-        assert rel <= 2e-2, (li, rel)
+        rel = elementwise(g[li], go[li])
+        print("gradient %s conv %d layer %d: %.2e" % ((B, H, W), conv, li, rel))
+        assert rel <= TOL_G, (li, rel)
     # and the BF16-storage gradients are close to the exact FP64 gradients
     _, gx, _ = cnn.loss_and_grads(unpack(w32, ws), x.astype(np.float64), e.astype(np.float64))
     for li in range(6):
         assert np.linalg.norm(g[li] - gx[li]) / np.linalg.norm(gx[li]) <= 0.25
+
+
+@pytest.mark.parametrize("conv", [1, 0])
+@pytest.mark.parametrize("B,H,W", [(1, 256, 256), (1, 64, 1024)])
+def test_forward_matches_oracle_at_size(kc, ctx, conv, B, H, W):
+    """Whole images of many tiles: 256 x 256 (2048 tcgen05 tiles of 16 x 8, more than the
+    persistent CTAs, so each CTA walks several) and a 1024-wide strip (the row length of
+    the config-5 grid), every pixel compared."""
+    ws = cnn.init_weights(23)
+    w32 = pack(ws)
+    x = np.random.default_rng(24).standard_normal((B, 1, H, W)).astype(np.float32)
+    xd = torch.as_tensor(x, device="cuda")
+    yd = torch.zeros_like(xd)
+    ctx.set_conv_kernel(conv)
+    try:
+        kc.kc_cnn_forward(ctx, torch.as_tensor(w32, device="cuda"), xd, yd, B, H, W)
+    finally:
+        ctx.set_conv_kernel(ctx.CONV_TCGEN05)
+    torch.cuda.synchronize()
+    assert ctx.read_status() == 0
+    yo, _ = cnn.forward_bf16_storage(unpack(w32, ws), x.astype(np.float64))
+    err = elementwise(yd.cpu().numpy(), yo)
+    print("forward %s conv %d: %.2e" % ((B, H, W), conv, err))
+    assert err <= TOL_Y
+
+
+def test_forward_matches_oracle_on_the_1024_grid(kc, ctx):
+    """The config-5 size, 1024 x 1024, through the tcgen05 kernel: the oracle recomputes
+    sampled windows.  An output pixel depends only on the 13 x 13 input pixels around it
+    (six 3 x 3 layers), so the oracle run on a crop gives the exact full-image values at
+    the crop pixels that lie at least 6 pixels inside it (or at an image border, where the
+    crop's zero padding is the image's)."""
+    H = W = 1024
+    ws = cnn.init_weights(25)
+    w32 = pack(ws)
+    x = np.random.default_rng(26).standard_normal((1, 1, H, W)).astype(np.float32)
+    xd = torch.as_tensor(x, device="cuda")
+    yd = torch.zeros_like(xd)
+    kc.kc_cnn_forward(ctx, torch.as_tensor(w32, device="cuda"), xd, yd, 1, H, W)
+    torch.cuda.synchronize()
+    assert ctx.read_status() == 0
+    y = yd.cpu().numpy()[0, 0].astype(np.float64)
+    wo = unpack(w32, ws)
+    R = 6
+    # windows: two corners, an edge, the middle and one straddling tile boundaries
+    for (r0, c0, h, w) in [(0, 0, 40, 40), (984, 984, 40, 40), (0, 500, 30, 64),
+                           (496, 504, 48, 40), (251, 123, 37, 29)]:
+        lo_r, lo_c = max(r0 - R, 0), max(c0 - R, 0)
+        hi_r, hi_c = min(r0 + h + R, H), min(c0 + w + R, W)
+        crop = x[:, :, lo_r:hi_r, lo_c:hi_c].astype(np.float64)
+        yo, _ = cnn.forward_bf16_storage(wo, crop)
+        yo = yo[0, 0, r0 - lo_r:r0 - lo_r + h, c0 - lo_c:c0 - lo_c + w]
+        err = elementwise(y[r0:r0 + h, c0:c0 + w], yo)
+        print("1024^2 window %s: %.2e" % ((r0, c0, h, w), err))
+        assert err <= TOL_Y
+
+
+@pytest.mark.parametrize("conv", [1, 0])
+def test_gradients_match_oracle_at_size(kc, ctx, conv):
+    """Weight gradients of the regression loss on a 256 x 256 image, every entry."""
+    B, H, W = 1, 256, 256
+    ws = cnn.init_weights(27)
+    w32 = pack(ws)
+    rng = np.random.default_rng(28)
+    x = rng.standard_normal((B, 1, H, W)).astype(np.float32)
+    e = rng.standard_normal((B, 1, H, W)).astype(np.float32)
+    wd = torch.as_tensor(w32, device="cuda")
+    grad = torch.zeros_like(wd)
+    yd = torch.zeros((B, 1, H, W), dtype=torch.float32, device="cuda")
+    ctx.set_conv_kernel(conv)
+    try:
+        loss = kc.kc_cnn_train_step(ctx, wd, None, None, 0, 0.0,
+                                    torch.as_tensor(x, device="cuda"),
+                                    torch.as_tensor(e, device="cuda"), B, H, W, yd, grad)
+    finally:
+        ctx.set_conv_kernel(ctx.CONV_TCGEN05)
+    Lo, go, yo = cnn.loss_and_grads_bf16_storage(unpack(w32, ws), x.astype(np.float64),
+                                                 e.astype(np.float64))
+    assert abs(loss - Lo) <= 1e-3 * Lo
+    assert elementwise(yd.cpu().numpy(), yo) <= TOL_Y
+    g = unpack(grad.cpu().numpy(), ws)
+    for li in range(6):
+        rel = elementwise(g[li], go[li])
+        print("gradient 256^2 conv %d layer %d: %.2e" % (conv, li, rel))
+        assert rel <= TOL_G, (li, rel)
 
 
 def test_adam_steps_reduce_the_loss(kc, ctx):
@@ -147,11 +246,12 @@ def test_residual_loss_gradients_match_oracle(kc, ctx):
     Lo, go, _, yo = cnn.residual_loss_and_grads(unpack(w32, ws), x.astype(np.float64),
                                                 r.astype(np.float64), Ah.to_scipy(), bf16=True)
     assert abs(loss - Lo) <= 2e-3 * Lo
-    assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) <= 5e-3
+    assert elementwise(yd.cpu().numpy(), yo) <= TOL_Y
     g = unpack(grad.cpu().numpy(), ws)
     for li in range(6):
-        rel = np.linalg.norm(g[li] - go[li]) / np.linalg.norm(go[li])
-        assert rel <= 2e-2, (li, rel)
+        rel = elementwise(g[li], go[li])
+        print("residual-loss gradient layer %d: %.2e" % (li, rel))
+        assert rel <= TOL_G, (li, rel)
 
 
 def test_residual_training_reduces_the_loss(kc, ctx):

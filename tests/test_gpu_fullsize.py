@@ -1,0 +1,67 @@
+"""DCGS2 parity with the FP64 oracle on a long basis (m >= 2^22 rows), n = 50.
+
+The reduction picks its long-vector task layouts (two slots per warp from 5 tasks, three
+slots from 21, the two-subset splits) only for m >= 2^22, and the default FP64 mode (1:
+float-float S = Q^T v and Q C) is the one the benchmark times; this file runs all three
+FP64 modes there, on the config-2 operator family (3D upwind convection-diffusion, wind
+along (1, 0.5, 0.25), Peclet 50) at N = 162 (m = 4,251,528), start vector N(0,1) seed
+1002.  Tolerances as in the other DCGS2 parity tests: H to 1e-12 relative (Frobenius),
+basis entries to 1e-10 absolute, loss of orthogonality and representation error at
+O(eps) (Section 5.1).  The oracle run (about 20 s of host time) is shared by the modes.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import arnoldi as orc  # noqa: E402
+from oracle.metrics import loo, rre  # noqa: E402
+from synth import config2_operator, gaussian_vector  # noqa: E402
+
+N_GRID, N_STEPS = 162, 50
+
+
+@pytest.fixture(scope="module")
+def kc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2104_01253_gb300 as kc
+    return kc
+
+
+@pytest.fixture(scope="module")
+def problem():
+    Ah = config2_operator(N_GRID)
+    assert Ah.m >= 2 ** 22
+    r0 = gaussian_vector(Ah.m, 1002)
+    Qo, Ho = orc.dcgs2_arnoldi(Ah.to_scipy(), r0, N_STEPS)
+    return Ah, r0, Qo, Ho
+
+
+@pytest.mark.parametrize("mode", [1, 0, 2])
+def test_dcgs2_long_basis_matches_oracle(kc, problem, mode):
+    Ah, r0, Qo, Ho = problem
+    ctx = kc.Context(0)
+    n = N_STEPS
+    A = kc.DeviceCSR(Ah)
+    st = kc.ArnoldiState(Ah.m, n + 1, kc.KC_F64)
+    ctx.set_fp64_mode(mode)
+    try:
+        kc.dcgs2_arnoldi_init(ctx, A, st, torch.as_tensor(r0, device="cuda"))
+        for _ in range(n):
+            kc.dcgs2_arnoldi_step(ctx, A, st)
+        kc.dcgs2_arnoldi_finish(ctx, A, st)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_fp64_mode(1)
+    assert ctx.read_status() == 0
+    Hg = st.H(n + 1, n).cpu().numpy()
+    Qg = st.Q(n + 1).cpu().numpy()
+    herr = np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho)
+    qerr = np.abs(Qg - Qo).max()
+    print("mode %d: H rel %.2e, Q abs %.2e" % (mode, herr, qerr))
+    assert herr <= 1e-12
+    assert qerr <= 1e-10
+    assert loo(Qg) <= 1e-13
+    assert rre(Ah.to_scipy(), Qg, Hg) <= 1e-14
