@@ -135,8 +135,12 @@ int kc_get_fp64_mode(const kc_ctx* ctx);
  *  1: the DCGS2 update stages basis tiles in shared memory with bulk asynchronous copies
  *     (one producer thread and an mbarrier ring per SM);
  *  2: the fused DCGS2 reduction stages 2D tiles of the basis with tensor-memory copies
- *     (cp.async.bulk.tensor, one producer thread, sixteen consumer warps per SM).
- * 0 streams both passes through registers. */
+ *     (cp.async.bulk.tensor, one producer thread, sixteen consumer warps per SM);
+ *  4: FP64 mode 1 / 2 without the bounded FP32 products: Q C of the update and of the
+ *     CGS2 finish's projections then always take float-float (update) or FP64 (finish),
+ *     instead of FP32 products on the launches whose error bound,
+ *     (k + 3) 2^-24 ||C||_1 <= 2^-53 ||w - Q C||, holds.
+ * 0 streams both passes through registers, with the bounded FP32 products. */
 kc_status kc_set_staged(kc_ctx* ctx, int flags);
 /* Kernel of the network's 32 -> 32 convolutions: 0 mma.sync (m16n8k16, registers);
  * 1 tcgen05 (default: tensor-copy fed, accumulator in tensor memory, operands in shared
@@ -206,11 +210,45 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 /* Gram matrix of a basis, G = Q^T Q, for the loss of orthogonality ||I - Q^T Q||_F
  * (Section 5.1).  Q: device, column-major with leading dimension ldq >= m, ncols columns
  * (1 <= ncols <= 128) of type q_dtype (KC_F64, KC_F32 or KC_BF16); G: device FP64,
- * ncols x ncols column-major, overwritten.  Products and sums in FP64; the per-block
- * sums are combined with atomics, so the last bits of G may vary from call to call.
+ * ncols x ncols column-major, overwritten, exactly symmetric.  Products and sums in FP64;
+ * the per-block sums are combined with atomics, so the last bits of G may vary from call
+ * to call.
  * Asynchronous on the context stream. */
 kc_status kc_basis_gram(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int64_t m,
                         int ncols, double* G);
+
+/* ---- row-partitioned DCGS2 (Section 4; Tables 1-2: rows split across processes) ---------
+ * The distributed layout of the paper: rank p owns a contiguous block of m_p rows of A, Q,
+ * w and v, and every step makes ONE global sum of its 2k + 2 partial dot products (the
+ * MPI_Allreduce of Section 4); the small scalar step is replicated.  These calls are the
+ * per-rank work of one GPU; the caller sums the partials over the ranks (NCCL or any other
+ * collective: the library makes none) and supplies the halo of w for the matvec.
+ *   A_local: the rank's m_p rows in CSR form (FP64 values), its column indices pointing
+ *            into w_ext;
+ *   st:      the rank's state: Q, w, v with m_p rows (ldq >= m_p), H and K replicated
+ *            (identical on every rank), FP64 basis; start with dcgs2_arnoldi_init on the
+ *            rank's rows of r0;
+ *   partial, totals: device FP64 arrays.  All calls are asynchronous on the context stream.
+ *
+ * dcgs2_part_reduce: v = A_local w_ext (this rank's rows of A w; w_ext holds w's rows that
+ * A_local's columns reach, i.e. the rank's own rows and the halo), then this rank's partial
+ * sums of [Q_k, w]^T [w, v] into partial[0 : 2k+2] = [C_0, S_0, ..., C_{k-1}, S_{k-1},
+ * beta, s] (the single reduction of Algorithm 4, over the local rows).
+ * dcgs2_part_update: totals = the element-wise sum of every rank's partial; the scalar step
+ * of Algorithm 4 (Pythagoras, eq. 30, the H and K columns) from it and the row-local update
+ * of q_k and w; k += 1.  Numerical failures go to kc_read_status as for dcgs2_arnoldi_step.
+ * dcgs2_part_finish: the CGS2 finish (end of Section 3) as four phases with three global
+ * sums between them: phase 0 writes partial[0 : k+1] = [Q^T w, w^T w]; phase 1 takes their
+ * sums, forms u = w - Q C1 and writes partial[0 : k+1] = [Q^T u, u^T u]; phase 2 takes those
+ * sums, forms u -= Q C2 and writes partial[0] = u^T u; phase 3 takes that sum and writes
+ * H(:, k-1), alpha and q_k = u / alpha (totals unused in phase 0, partial in phase 3).
+ * FP64 modes 0 and 1 as for dcgs2_arnoldi_step (mode 2 takes mode 1's reduction here). */
+kc_status dcgs2_part_reduce(kc_ctx* ctx, const kc_csr* A_local, kc_arnoldi* st,
+                            const double* w_ext, double* partial);
+kc_status dcgs2_part_update(kc_ctx* ctx, const kc_csr* A_local, kc_arnoldi* st,
+                            const double* totals);
+kc_status dcgs2_part_finish(kc_ctx* ctx, const kc_csr* A_local, kc_arnoldi* st, int phase,
+                            const double* totals, double* partial);
 
 /* One FP64 DCGS2 step, as dcgs2_arnoldi_step in its all-FP64 mode, that allocates
  * nothing and needs no context.  (The paper has no counterpart: this is a deployment
@@ -274,7 +312,8 @@ typedef struct {
   int32_t inner_max_cycles; /* IR: cycles per inner solve */
   int32_t precond;        /* fgmres_solve only: a kc_precond_kind (gmres_solve ignores it) */
   int32_t diag_loo;       /* gmres_solve diagnostics: 1 = after every (inner) cycle form the
-                             Gram matrix of its basis (kc_basis_gram) and report the largest
+                             Gram matrix of the n (or, at an early stop, ncols) columns that
+                             formed its correction (kc_basis_gram) and report the largest
                              ||I - Q^T Q||_F in kc_gmres_info.max_loo (one extra pass of
                              O(m n^2) FP64 work per cycle, and the multi-kernel path) */
 } kc_gmres_opts;

@@ -231,6 +231,27 @@ def dcgs2_arnoldi_finish(ctx: Context, A: DeviceCSR, st: ArnoldiState):
     ctx.check(ctx.lib.dcgs2_arnoldi_finish(ctx.handle, C.byref(A.c), C.byref(st.c)))
 
 
+def dcgs2_part_reduce(ctx: Context, A_local: DeviceCSR, st: ArnoldiState, w_ext, partial):
+    """Row-partitioned step, first half: v = A_local w_ext and this rank's 2k + 2 partial
+    sums [C_0, S_0, ..., beta, s] into the device tensor `partial`."""
+    ctx.check(ctx.lib.dcgs2_part_reduce(ctx.handle, C.byref(A_local.c), C.byref(st.c),
+                                        _ptr(w_ext), _ptr(partial)))
+
+
+def dcgs2_part_update(ctx: Context, A_local: DeviceCSR, st: ArnoldiState, totals):
+    """Row-partitioned step, second half, from the partial sums summed over the ranks."""
+    ctx.check(ctx.lib.dcgs2_part_update(ctx.handle, C.byref(A_local.c), C.byref(st.c),
+                                        _ptr(totals)))
+
+
+def dcgs2_part_finish(ctx: Context, A_local: DeviceCSR, st: ArnoldiState, phase: int,
+                      totals=None, partial=None):
+    """Row-partitioned CGS2 finish, phase 0..3 (three global sums between the phases)."""
+    ctx.check(ctx.lib.dcgs2_part_finish(ctx.handle, C.byref(A_local.c), C.byref(st.c),
+                                        int(phase), _ptr(totals) if totals is not None else None,
+                                        _ptr(partial) if partial is not None else None))
+
+
 def cgs2_arnoldi_init(ctx: Context, A: DeviceCSR, st: ArnoldiState, r0):
     ctx.check(ctx.lib.cgs2_arnoldi_init(ctx.handle, C.byref(A.c), C.byref(st.c), _ptr(r0)))
 

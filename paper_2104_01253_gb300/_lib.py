@@ -73,6 +73,10 @@ _SIGS = {
     "dcgs2_arnoldi_finish": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),
     "dcgs2_arnoldi_step_noalloc": ([C.POINTER(kc_csr), C.POINTER(kc_arnoldi), _P], C.c_int),
     "dcgs2_noalloc_read_status": ([C.POINTER(C.c_int), _P], C.c_int),
+    "dcgs2_part_reduce": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi), _P, _P], C.c_int),
+    "dcgs2_part_update": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi), _P], C.c_int),
+    "dcgs2_part_finish": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi), C.c_int, _P, _P],
+                          C.c_int),
     "kc_basis_gram": ([_P, _P, C.c_int64, C.c_int, C.c_int64, C.c_int, _P], C.c_int),
     "dcgs2_qr": ([_P, _P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int], C.c_int),
     "cgs2_arnoldi_init": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi), _P], C.c_int),

@@ -191,7 +191,7 @@ kc_status kc_set_barrier_test(kc_ctx* ctx, int on) {
 }
 
 kc_status kc_set_staged(kc_ctx* ctx, int flags) {
-  if (!ctx || flags < 0 || flags > 3) return KC_ERR_INVALID_ARG;
+  if (!ctx || flags < 0 || flags > 7) return KC_ERR_INVALID_ARG;
   ctx->staged = flags;
   return KC_OK;
 }
@@ -317,6 +317,88 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
   KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec, 1));
   KC_TRY(launch_norm(ctx, st->w, nullptr, A->m, vec, NEPI_FINISH, sa));  // alpha = ||u||
   KC_TRY(launch_scale_to(ctx, st->w, qcol(st, k), st->q_dtype, A->m, vec));
+  st->finished = 1;
+  return KC_OK;
+}
+
+// ---- row-partitioned DCGS2 (Section 4: rows of Q, w, v and A split across ranks) -----
+
+static kc_status part_checks(kc_ctx* ctx, const kc_csr* A, const kc_arnoldi* st) {
+  if (st->q_dtype != KC_F64)
+    return fail(ctx, KC_ERR_INVALID_ARG, "row-partitioned step: FP64 basis only");
+  if (A && (A->val_dtype != KC_F64 || is_stencil(A)))
+    return fail(ctx, KC_ERR_INVALID_ARG, "row-partitioned step: FP64 CSR rows only");
+  return KC_OK;
+}
+
+kc_status dcgs2_part_reduce(kc_ctx* ctx, const kc_csr* A_local, kc_arnoldi* st,
+                            const double* w_ext, double* partial) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr_entries(ctx, A_local));
+  KC_TRY(validate_state(ctx, A_local, st));
+  KC_TRY(part_checks(ctx, A_local, st));
+  if (!w_ext || !partial) return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
+  const int k = st->k;
+  if (k + 2 > st->ncap)
+    return fail(ctx, KC_ERR_INVALID_ARG, "basis full: k = %d, ncap = %d", k, st->ncap);
+  if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
+  KC_TRY(launch_spmv(ctx, A_local, w_ext, st->v, KC_F64));          // this rank's rows of A w
+  StepArgs sa = step_args(st, k, 0);
+  sa.part = partial;
+  return launch_reduce(ctx, st->Q, st->ldq, KC_F64, k, st->w, st->v, A_local->m, KC_F64,
+                       EPI_PARTIAL, sa);
+}
+
+kc_status dcgs2_part_update(kc_ctx* ctx, const kc_csr* A_local, kc_arnoldi* st,
+                            const double* totals) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A_local));
+  KC_TRY(validate_state(ctx, A_local, st));
+  KC_TRY(part_checks(ctx, A_local, st));
+  if (!totals) return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
+  const int k = st->k;
+  if (k + 2 > st->ncap || st->finished)
+    return fail(ctx, KC_ERR_INVALID_ARG, "no step to complete at k = %d", k);
+  StepArgs sa = step_args(st, k, 0);
+  KC_TRY(launch_scalar_from_totals(ctx, totals, k, sa));
+  KC_TRY(launch_dcgs2_update(ctx, st->Q, st->ldq, KC_F64, k, st->w, st->v, A_local->m, KC_F64));
+  st->k = k + 1;
+  return KC_OK;
+}
+
+kc_status dcgs2_part_finish(kc_ctx* ctx, const kc_csr* A_local, kc_arnoldi* st, int phase,
+                            const double* totals, double* partial) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A_local));
+  KC_TRY(validate_state(ctx, A_local, st));
+  KC_TRY(part_checks(ctx, A_local, st));
+  const int k = st->k;
+  if (k < 1 || st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "nothing to finish");
+  if (phase < 0 || phase > 3) return fail(ctx, KC_ERR_INVALID_ARG, "phase must be 0..3");
+  if ((phase > 0 && !totals) || (phase < 3 && !partial))
+    return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
+  const int64_t m = A_local->m;
+  StepArgs sa = step_args(st, k, 0);
+  sa.part = partial;
+  struct Phase {
+    kc_ctx* c;
+    explicit Phase(kc_ctx* cc) : c(cc) { c->timing_phase = 1; }
+    ~Phase() { c->timing_phase = 0; }
+  } timing(ctx);
+  if (phase == 0)                  // partial = [Q^T w, w^T w]
+    return launch_reduce(ctx, st->Q, st->ldq, KC_F64, k, st->w, nullptr, m, KC_F64,
+                         EPI_PARTIAL, sa);
+  if (phase == 1 || phase == 2) {  // u -= Q c with the summed c; partial of the next sums
+    KC_TRY(launch_store_totals(ctx, totals, k, phase - 1));
+    KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, KC_F64, k, st->w, m, KC_F64, phase - 1));
+    if (phase == 1)                // partial = [Q^T u, u^T u]
+      return launch_reduce(ctx, st->Q, st->ldq, KC_F64, k, st->w, nullptr, m, KC_F64,
+                           EPI_PARTIAL, sa);
+    return launch_reduce(ctx, st->Q, st->ldq, KC_F64, 0, st->w, nullptr, m, KC_F64,
+                         EPI_PARTIAL, sa);        // partial = [u^T u]
+  }
+  KC_TRY(launch_finish_from_norm(ctx, totals, sa));   // H column, alpha = ||u||
+  KC_TRY(launch_scale_to(ctx, st->w, qcol(st, k), KC_F64, m, KC_F64));
   st->finished = 1;
   return KC_OK;
 }

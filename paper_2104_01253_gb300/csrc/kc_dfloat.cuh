@@ -53,4 +53,15 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)d);
 }
 
+// FP32 value of a double by truncation to 24 significant bits, by integer operations (no
+// FP64 instruction): 0 below the FP32 normal range, NaN from 2^128 (and for Inf / NaN).
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int H = (unsigned int)(b >> 32), L = (unsigned int)b;
+  const unsigned int ef = H & 0x7ff00000u;
+  const unsigned int f = __funnelshift_l(L, H - (896u << 20), 3) | (H & 0x80000000u);
+  return ef < (897u << 20) ? 0.0f
+                           : (ef < (1151u << 20) ? __uint_as_float(f) : __int_as_float(0x7fc00000));
+}
+
 }  // namespace kc

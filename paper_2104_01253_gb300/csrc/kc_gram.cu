@@ -6,8 +6,9 @@
 // One CTA per row tile group: a tile of GRAM_ROWS rows of every column is staged in shared
 // memory as FP64 (FP32 and BF16 entries convert exactly), then each thread accumulates up
 // to GRAM_PPT of the ncols (ncols + 1) / 2 column pairs over the tile; blockIdx.y picks
-// the chunk of pairs.  The per-CTA sums are added into G with FP64 atomics (the order of
-// those additions is not fixed: G is a measurement, not part of the method).
+// the chunk of pairs.  The per-CTA sums are added into the upper triangle of G with FP64
+// atomics (the order of those additions is not fixed: G is a measurement, not part of
+// the method), and a second launch mirrors it into the lower triangle.
 #include "kc_internal.cuh"
 
 namespace kc {
@@ -69,14 +70,19 @@ k_gram(const TQ* __restrict__ Q, int64_t ldq, int64_t m, int ncols, double* __re
     }
   }
 #pragma unroll
-  for (int s = 0; s < GRAM_PPT; s++) {
-    if (pi[s] < 0) continue;
-    atomicAdd(G + pi[s] + (int64_t)pj[s] * ncols, acc[s]);
-    if (pi[s] != pj[s]) atomicAdd(G + pj[s] + (int64_t)pi[s] * ncols, acc[s]);
+  for (int s = 0; s < GRAM_PPT; s++)
+    if (pi[s] >= 0) atomicAdd(G + pi[s] + (int64_t)pj[s] * ncols, acc[s]);   // upper triangle
+}
+
+// G(j, i) = G(i, j) for i < j: the lower triangle mirrors the accumulated upper one
+__global__ void k_gram_mirror(double* __restrict__ G, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e % n, j = e / n;
+    if (i > j) G[e] = G[j + (int64_t)i * n];
   }
 }
 
-// out[0] = ||I - G||_F; out[1] = max(out[1], out[0])
+// out[0] = ||I - G||_F; out[1] = max(out[1], out[0]) (NaN if either is NaN)
 __global__ void k_loo_from_gram(const double* __restrict__ G, int n, double* out) {
   __shared__ double red[32];
   double s = 0.0;
@@ -93,7 +99,7 @@ __global__ void k_loo_from_gram(const double* __restrict__ G, int n, double* out
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
     out[0] = sqrt(t);
-    out[1] = fmax(out[1], out[0]);
+    if (!isnan(out[1]) && !(out[0] <= out[1])) out[1] = out[0];   // a NaN stays
   }
 }
 
@@ -102,8 +108,8 @@ kc_status launch_gram(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int6
   if (ncols < 1 || ncols > NMAX || m < 1 || ldq < m)
     return fail(ctx, KC_ERR_INVALID_ARG, "gram: need 1 <= ncols <= %d, m >= 1, ldq >= m", NMAX);
   KC_CUDA(ctx, cudaMemsetAsync(G, 0, (size_t)ncols * ncols * sizeof(double), ctx->stream));
+  // at most 128 x 33 doubles (33 KB): within the default dynamic shared-memory limit
   const size_t smem = (size_t)ncols * (GRAM_ROWS + 1) * sizeof(double);
-  static std::atomic<unsigned long long> a64{0}, a32{0}, a16{0};
   const int npairs = ncols * (ncols + 1) / 2;
   const int64_t ntiles = (m + GRAM_ROWS - 1) / GRAM_ROWS;
   int64_t gx = (int64_t)ctx->num_sms * 4;
@@ -111,18 +117,18 @@ kc_status launch_gram(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int6
   const dim3 grid((unsigned int)gx, (unsigned int)((npairs + GRAM_PAIRS - 1) / GRAM_PAIRS));
   timing_begin(ctx, KID_OTHER);
   if (q_dtype == KC_F64) {
-    KC_TRY(smem_attr_once(ctx, a64, k_gram<double>, (int)smem, "gram"));
     k_gram<double><<<grid, GRAM_THREADS, smem, ctx->stream>>>((const double*)Q, ldq, m, ncols, G);
   } else if (q_dtype == KC_F32) {
-    KC_TRY(smem_attr_once(ctx, a32, k_gram<float>, (int)smem, "gram"));
     k_gram<float><<<grid, GRAM_THREADS, smem, ctx->stream>>>((const float*)Q, ldq, m, ncols, G);
   } else if (q_dtype == KC_BF16) {
-    KC_TRY(smem_attr_once(ctx, a16, k_gram<__nv_bfloat16>, (int)smem, "gram"));
     k_gram<__nv_bfloat16><<<grid, GRAM_THREADS, smem, ctx->stream>>>(
         (const __nv_bfloat16*)Q, ldq, m, ncols, G);
   } else {
     return fail(ctx, KC_ERR_INVALID_ARG, "gram: unknown basis type %d", q_dtype);
   }
+  KC_LAUNCHED(ctx);
+  timing_begin(ctx, KID_SMALL);
+  k_gram_mirror<<<(ncols * ncols + 255) / 256, 256, 0, ctx->stream>>>(G, ncols);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }

@@ -84,6 +84,7 @@ enum Epilogue : int {
   EPI_STORE_C = 1,      // store Q^T x into C (finish first pass, CGS2 second projection)
   EPI_STORE_C2 = 2,     // store Q^T x into C2
   EPI_STORE_S = 3,      // store Q^T x into S (CGS2 first projection)
+  EPI_PARTIAL = 4,      // row-partitioned step: store the (k + 1) x NRHS sums to sa.part
 };
 
 enum NormEpilogue : int {
@@ -105,6 +106,7 @@ struct StepArgs {
   int row;              // MGS inner product: row index i of H(i, k-1)
   int flags;            // bit 0: flexible (no H C / alpha correction); bit 1: GMRES Givens
   double pyth_tol;      // relative threshold on (beta - C^T C)/beta
+  double* part;         // EPI_PARTIAL: destination of this rank's sums (device)
 };
 
 // SF_QR: DCGS2 QR of given columns (Algorithm 2): v is the next column a_{k+1}, not A w,
@@ -224,6 +226,14 @@ kc_status launch_scale_to(kc_ctx* ctx, const void* x, void* qcol, int q_dtype, i
                           int vec_dtype);
 kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_t m,
                         int vec_dtype);
+// row-partitioned DCGS2 (kc_ortho.cu): the scalar step of Algorithm 4 from all-reduced sums
+// [C_0, S_0, ..., C_{k-1}, S_{k-1}, beta, s]; the coefficients of a finish projection
+// (which 0: C, 1: C2) and the squared norm from all-reduced sums; the finish's last
+// column from an all-reduced ||u||^2
+kc_status launch_scalar_from_totals(kc_ctx* ctx, const double* totals, int k,
+                                    const StepArgs& sa);
+kc_status launch_store_totals(kc_ctx* ctx, const double* totals, int k, int which);
+kc_status launch_finish_from_norm(kc_ctx* ctx, const double* totals, const StepArgs& sa);
 kc_status ensure_workspace(kc_ctx* ctx, size_t bytes);
 // Gram matrix G = Q^T Q (FP64, ncols x ncols, column-major) and ||I - G||_F (kc_gram.cu):
 // out[0] = the value, out[1] = max(out[1], value)

@@ -254,15 +254,17 @@ __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __
 
 // Last CTA of a reduction: deterministic sum of the per-CTA partials, then either a plain
 // store of Q^T x or the scalar step of Algorithm 4.
-__device__ void reduce_epilogue(const double* __restrict__ partials, int k, int NRHS,
-                                Scalars* __restrict__ sc, int epilogue, const StepArgs& sa,
-                                int nparts = -1) {
-  __shared__ double tot[PSTRIDE];
+// The epilogue on the summed values tot[0 : (k + 1) NRHS] (shared memory; all threads of
+// one CTA): a store of this rank's sums (row-partitioned step), a store of Q^T x, or the
+// scalar step of Algorithm 4.
+__device__ void epilogue_from_tot(const double* tot, int k, int NRHS, Scalars* __restrict__ sc,
+                                  int epilogue, const StepArgs& sa) {
   __shared__ double s_alpha;
   const int nval = (k + 1) * NRHS;
-  sum_partials(partials, nparts < 0 ? (int)gridDim.x : nparts, nval, tot);
-  __syncthreads();
-
+  if (epilogue == EPI_PARTIAL) {
+    for (int i = threadIdx.x; i < nval; i += blockDim.x) sa.part[i] = tot[i];
+    return;
+  }
   if (epilogue != EPI_DCGS2) {
     double* dst = epilogue == EPI_STORE_C ? sc->C : (epilogue == EPI_STORE_C2 ? sc->C2 : sc->S);
     for (int i = threadIdx.x; i < k; i += blockDim.x) dst[i] = tot[i * NRHS];
@@ -311,6 +313,16 @@ __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int 
   }
   __syncthreads();
   if (s_ok) scalar_step(sc, sa, k, s_alpha);
+}
+
+__device__ void reduce_epilogue(const double* __restrict__ partials, int k, int NRHS,
+                                Scalars* __restrict__ sc, int epilogue, const StepArgs& sa,
+                                int nparts = -1) {
+  __shared__ double tot[PSTRIDE];
+  const int nval = (k + 1) * NRHS;
+  sum_partials(partials, nparts < 0 ? (int)gridDim.x : nparts, nval, tot);
+  __syncthreads();
+  epilogue_from_tot(tot, k, NRHS, sc, epilogue, sa);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -509,18 +521,81 @@ k_dcgs2_update(TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ w,
 }
 
 // x <- x - Q_k c, c = C (which 0), C2 (1) or S (2).  Used by CGS2 passes.
+// With `allow32` (FP64 basis and vectors, FP64 offload mode) a launch whose coefficients
+// are small against the result takes Q c in FP32, under the bound of
+// k_dcgs2_update_f64x: (k + 3) 2^-24 ||c||_1 <= 2^-53 ||x - Q c||, where
+// ||x - Q c||^2 = x^T x - ||c||^2 from the reduction that produced c (sc->norm_sq).  The
+// second projection of the CGS2 finish (and the first, whose x is the pending vector,
+// already projected once) meets it; a first projection (c = S) does not and stays FP64.
 template <typename TQ, typename TV>
 __global__ void __launch_bounds__(UPD_THREADS)
 k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int64_t m,
-           const Scalars* __restrict__ sc, int which) {
+           const Scalars* __restrict__ sc, int which, int allow32) {
   using TA = typename Acc<TV>::T;
   constexpr int R = Grp<TV>::R;
   if (sc->stop) return;
   __shared__ TA sc_[NMAX];
+  __shared__ float sf_[NMAX];
+  __shared__ double s_scale;
+  __shared__ int s_fast;
   const double* src = which == 0 ? sc->C : (which == 1 ? sc->C2 : sc->S);
   for (int i = threadIdx.x; i < k; i += blockDim.x) sc_[i] = (TA)src[i];
+  if (threadIdx.x == 0) {
+    int fast = 0;
+    double sc2 = 1.0;
+    if (allow32 && sizeof(TQ) == 8 && sizeof(TV) == 8) {
+      double cmax = 0.0, l1 = 0.0, c2 = 0.0;
+      for (int i = 0; i < k; i++) {
+        const double c = src[i];
+        cmax = fmax(cmax, fabs(c));
+        l1 += fabs(c);
+        c2 += c * c;
+      }
+      const double rest = sc->norm_sq - c2;
+      int ex = 0;
+      if (cmax > 0.0) frexp(cmax, &ex);
+      sc2 = ldexp(1.0, ex);
+      fast = (rest > 0.0 && cmax > 0.0 && ex > -900 &&
+              l1 * (double)(k + 3) <= 0x1p-29 * sqrt(rest)) ? 1 : 0;
+    }
+    s_fast = fast;
+    s_scale = sc2;
+  }
   __syncthreads();
   const int64_t ngroups = m / R;
+  if (sizeof(TQ) == 8 && sizeof(TV) == 8 && s_fast) {
+    const double scale = s_scale, inv = 1.0 / scale;        // powers of two
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sf_[i] = d2f_trunc(src[i] * inv);
+    __syncthreads();
+    const double* Qd = reinterpret_cast<const double*>(Q);
+    double* xd = reinterpret_cast<double*>(x);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < m / 2;
+         g += (int64_t)gridDim.x * blockDim.x) {
+      double xv[2];
+      ldv_cg(xd, g, xv);
+      float z[2] = {0.0f, 0.0f};
+      int i = 0;
+      for (; i + 4 <= k; i += 4) {
+        double q[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; j++) load_q(Qd + (int64_t)(i + j) * ldq, g, q[j]);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          z[0] = fmaf(d2f_trunc(q[j][0]), sf_[i + j], z[0]);
+          z[1] = fmaf(d2f_trunc(q[j][1]), sf_[i + j], z[1]);
+        }
+      }
+      for (; i < k; i++) {
+        double q[2];
+        load_q(Qd + (int64_t)i * ldq, g, q);
+        z[0] = fmaf(d2f_trunc(q[0]), sf_[i], z[0]);
+        z[1] = fmaf(d2f_trunc(q[1]), sf_[i], z[1]);
+      }
+      xv[0] = fma(-f2d_bits(z[0]), scale, xv[0]);
+      xv[1] = fma(-f2d_bits(z[1]), scale, xv[1]);
+      stv(xd, g, xv);
+    }
+  } else
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
        g += (int64_t)gridDim.x * blockDim.x) {
     TV xv[R];
@@ -652,7 +727,7 @@ __global__ void __launch_bounds__(1024)
 k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
               const double* __restrict__ y, int64_t m, double* __restrict__ partials,
               unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa,
-              int nsplit, int nt) {
+              int nsplit, int nt, int epi) {
   if (sc->stop) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int h = blockIdx.x % nsplit, r = blockIdx.x / nsplit, nr = gridDim.x / nsplit;
@@ -725,7 +800,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
     }
   }
   if (!last_cta(counter)) return;
-  reduce_epilogue(partials, k, 2, sc, EPI_DCGS2, sa, nr);
+  reduce_epilogue(partials, k, 2, sc, epi, sa, nr);
 }
 
 // Two basis columns of the offloaded update for one group of two rows: u -= Q C in
@@ -750,29 +825,42 @@ __device__ __forceinline__ void f64x_update_pair(const double (&q)[2][2], const 
   }
 }
 
-// DCGS2 update, FP64 with offload: u = w - Q C in float-float (C scaled by a power of two
-// into float range), w <- v/alpha - Q T - q T_k in FP64.  The float-float / FP64 choice is
-// warp-uniform per pair of columns (see k_reduce_f64x).
+// DCGS2 update, FP64 with offload: u = w - Q C with C scaled by a power of two into float
+// range, w <- v/alpha - Q T - q T_k in FP64.  Q C is small against w (C holds the delayed
+// reorthogonalisation coefficients), so it needs far fewer correct digits than the FP64
+// terms: in FP32 (basis entries truncated to 24 bits, k-term FP32 sums) its error per row
+// is at most (k + 3) 2^-24 sum_j |q_j| |C_j|, whose 2-norm is at most (k + 3) 2^-24 ||C||_1;
+// when that is below 2^-53 alpha (= 2^-53 ||w - Q C||, the FP64 rounding of w itself) the
+// launch takes the FP32 products ("fast"), otherwise float-float (split doubles, exact
+// leading products), and FP64 for operands outside the float-float range (warp-uniform
+// per pair of columns, see k_reduce_f64x).  The choice is made per launch from the device
+// scalars, identically in every CTA.
 __global__ void __launch_bounds__(UPD_THREADS)
 k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__ w,
-                    const double* __restrict__ v, int64_t m, const Scalars* __restrict__ sc) {
+                    const double* __restrict__ v, int64_t m, const Scalars* __restrict__ sc,
+                    int allow32) {
   if (sc->stop) return;
   __shared__ double sC[NMAX + 1], sT[NMAX + 1];
   __shared__ float cH[NMAX + 1], cL[NMAX + 1];
   __shared__ double s_scale;
-  __shared__ int s_cok;
+  __shared__ int s_cok, s_fast;
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
     sC[i] = i < k ? sc->C[i] : 0.0;            // sC[k] = 0 pads an odd k to a column pair
     sT[i] = sc->T[i];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double cmax = 0.0;
-    for (int i = 0; i < k; i++) cmax = fmax(cmax, fabs(sC[i]));
+    double cmax = 0.0, l1 = 0.0;
+    for (int i = 0; i < k; i++) {
+      cmax = fmax(cmax, fabs(sC[i]));
+      l1 += fabs(sC[i]);
+    }
     int ex = 0;
     if (cmax > 0.0) frexp(cmax, &ex);
     s_scale = ldexp(1.0, ex);                 // C / scale lies in (-1, 1)
     s_cok = 1;
+    // 0x1p-29 = 2^-53 / 2^-24; l1 is FP64 (relative error far below the bound's margin)
+    s_fast = (allow32 && l1 * (double)(k + 3) <= 0x1p-29 * sc->alpha) ? 1 : 0;
   }
   __syncthreads();
   const double inv_scale = 1.0 / s_scale;     // exact: a power of two
@@ -787,6 +875,49 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
   const double inva = sc->inv_alpha, vsc = sc->vscale, scale = s_scale;
   double* qk = Q + (int64_t)k * ldq;
   const int64_t ngroups = m / 2;
+  if (s_fast && cok) {
+    // cH holds C / scale truncated to 24 bits (the leading float of its split); with the
+    // truncated basis entries that is 2 x 2^-23 of each product, and the FP32 sum adds at
+    // most (k - 1) 2^-24: together the (k + 3) 2^-24 of the bound above
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+      double wv[2], vv[2];
+      ldv_cg(w, g, wv);
+      ldv_cg(v, g, vv);
+      double wn[2] = {vv[0] * vsc, vv[1] * vsc};
+      float z[2] = {0.0f, 0.0f};
+      int i = 0;
+      for (; i + 4 <= k; i += 4) {      // four columns' loads in flight before arithmetic
+        double q[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; j++) load_q(Q + (int64_t)(i + j) * ldq, g, q[j]);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          wn[0] = fma(-q[j][0], sT[i + j], wn[0]);
+          wn[1] = fma(-q[j][1], sT[i + j], wn[1]);
+          z[0] = fmaf(d2f_trunc(q[j][0]), cH[i + j], z[0]);
+          z[1] = fmaf(d2f_trunc(q[j][1]), cH[i + j], z[1]);
+        }
+      }
+      for (; i < k; i++) {
+        double q[2];
+        load_q(Q + (int64_t)i * ldq, g, q);
+        wn[0] = fma(-q[0], sT[i], wn[0]);
+        wn[1] = fma(-q[1], sT[i], wn[1]);
+        z[0] = fmaf(d2f_trunc(q[0]), cH[i], z[0]);
+        z[1] = fmaf(d2f_trunc(q[1]), cH[i], z[1]);
+      }
+      double qn[2], wo[2];
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        const double u = fma(-f2d_bits(z[r]), scale, wv[r]);
+        qn[r] = u * inva;
+        wo[r] = fma(-qn[r], sT[k], wn[r]);
+      }
+      store_q(qk, g, qn);
+      stv(w, g, wo);
+    }
+  } else
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
        g += (int64_t)gridDim.x * blockDim.x) {
     double wv[2], vv[2];
@@ -937,6 +1068,46 @@ k_fallback_norm(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restri
   scalar_step(sc, sa, k, s_alpha);
 }
 
+// The epilogue of a norm / dot reduction from xx = x^T x and xy = x^T y (one thread).
+__device__ void norm_epilogue(double xx, double xy, Scalars* __restrict__ sc, int nepi,
+                              const StepArgs& sa) {
+  const int k = sa.k;
+  sc->norm_sq = xx;
+  if (!isfinite(xx) || !isfinite(xy)) set_status(sc, KC_ERR_NONFINITE);
+  if (nepi == NEPI_DOT) {
+    sc->h = xy;
+    sa.H[sa.row + (int64_t)(k - 1) * sa.ldh] = xy;       // H(i, k-1), i = sa.row
+    return;
+  }
+  double alpha = sqrt(xx);
+  sc->alpha = alpha;
+  sc->inv_alpha = 1.0 / alpha;
+  sc->vscale = 1.0 / alpha;
+  if (nepi == NEPI_INIT) {
+    if (!(alpha > 0.0)) set_status(sc, KC_ERR_BREAKDOWN);
+    return;
+  }
+  // finalise column k-1 of H
+  double* Hc = sa.H + (int64_t)(k - 1) * sa.ldh;
+  double cn = alpha * alpha;
+  if (nepi == NEPI_FINISH) {
+    for (int i = 0; i < k; i++) {
+      Hc[i] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + sc->C[i] + sc->C2[i];
+      cn += Hc[i] * Hc[i];
+    }
+  } else if (nepi == NEPI_CGS2) {
+    for (int i = 0; i < k; i++) {
+      Hc[i] = sc->S[i] + sc->C[i];
+      cn += Hc[i] * Hc[i];
+    }
+  } else {  // MGS: the inner products are already in H
+    for (int i = 0; i < k; i++) cn += Hc[i] * Hc[i];
+  }
+  Hc[k] = alpha;
+  if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
+  if (sa.flags & SF_GIVENS) givens_column(sc, sa.H, sa.ldh, k - 1, sa.R, sa.ldr);
+}
+
 // K3': x^T x (and x^T y) with a last-CTA epilogue (norms, MGS inner products).
 template <typename TV, int NRHS>
 __global__ void __launch_bounds__(RED_THREADS)
@@ -981,42 +1152,7 @@ k_norm(const TV* __restrict__ x, const TV* __restrict__ y, int64_t m,
   sum_partials(partials, gridDim.x, 2, tot);
   __syncthreads();
   if (threadIdx.x != 0) return;
-  const double xx = tot[0], xy = tot[1];
-  const int k = sa.k;
-  sc->norm_sq = xx;
-  if (!isfinite(xx) || !isfinite(xy)) set_status(sc, KC_ERR_NONFINITE);
-  if (nepi == NEPI_DOT) {
-    sc->h = xy;
-    sa.H[sa.row + (int64_t)(k - 1) * sa.ldh] = xy;       // H(i, k-1), i = sa.row
-    return;
-  }
-  double alpha = sqrt(xx);
-  sc->alpha = alpha;
-  sc->inv_alpha = 1.0 / alpha;
-  sc->vscale = 1.0 / alpha;
-  if (nepi == NEPI_INIT) {
-    if (!(alpha > 0.0)) set_status(sc, KC_ERR_BREAKDOWN);
-    return;
-  }
-  // finalise column k-1 of H
-  double* Hc = sa.H + (int64_t)(k - 1) * sa.ldh;
-  double cn = alpha * alpha;
-  if (nepi == NEPI_FINISH) {
-    for (int i = 0; i < k; i++) {
-      Hc[i] = sa.K[i + (int64_t)(k - 1) * sa.ldk] + sc->C[i] + sc->C2[i];
-      cn += Hc[i] * Hc[i];
-    }
-  } else if (nepi == NEPI_CGS2) {
-    for (int i = 0; i < k; i++) {
-      Hc[i] = sc->S[i] + sc->C[i];
-      cn += Hc[i] * Hc[i];
-    }
-  } else {  // MGS: the inner products are already in H
-    for (int i = 0; i < k; i++) cn += Hc[i] * Hc[i];
-  }
-  Hc[k] = alpha;
-  if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
-  if (sa.flags & SF_GIVENS) givens_column(sc, sa.H, sa.ldh, k - 1, sa.R, sa.ldr);
+  norm_epilogue(tot[0], tot[1], sc, nepi, sa);
 }
 
 // qcol = x * inv_alpha (converted to the basis type)
@@ -1168,8 +1304,8 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     kc_status st = launch_reduce_tma(ctx, (const double*)Q, ldq, k, (const double*)x,
                                      (const double*)y, m, ctx->fp64_mode >= 1, sa);
     if (st != KC_OK) return st;
-  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
-      ctx->fp64_mode >= 1) {
+  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two &&
+             (epilogue == EPI_DCGS2 || epilogue == EPI_PARTIAL) && ctx->fp64_mode >= 1) {
     // Task layout: nsplit subsets of nt tasks (ceil(ntask / 48) <= nsplit <= ceil(ntask /
     // 32)), CTAs of nw <= 16 warps with tpw slots, chosen once per k and size class to
     // maximise resident warps x used slots.  Three slots (one row group per iteration,
@@ -1239,7 +1375,7 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     auto go = [&](auto kern) {
       kern<<<g, 32 * nw, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
                                            (const double*)y, m, ctx->partials, ctx->counters,
-                                           ctx->scal, sa, nsplit, nt);
+                                           ctx->scal, sa, nsplit, nt, epilogue);
     };
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
     else if (tpw == 2) go(k_reduce_f64x<2, 2>);
@@ -1266,7 +1402,7 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_UPDATE);
   if (q_dtype == KC_F64 && ctx->fp64_mode >= 1)
-    k_dcgs2_update_f64x<<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
+    k_dcgs2_update_f64x<<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal, !(ctx->staged & 4));
   else if (q_dtype == KC_F64)
     k_dcgs2_update<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
   else if (q_dtype == KC_F32)
@@ -1283,11 +1419,11 @@ kc_status launch_gemv_sub(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, 
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_GEMV_SUB);
   if (q_dtype == KC_F64)
-    k_gemv_sub<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((const double*)Q, ldq, k, (double*)x, m, ctx->scal, which);
+    k_gemv_sub<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((const double*)Q, ldq, k, (double*)x, m, ctx->scal, which, ctx->fp64_mode >= 1 && which != 2 && !(ctx->staged & 4));
   else if (q_dtype == KC_F32)
-    k_gemv_sub<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)Q, ldq, k, (float*)x, m, ctx->scal, which);
+    k_gemv_sub<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)Q, ldq, k, (float*)x, m, ctx->scal, which, 0);
   else
-    k_gemv_sub<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const __nv_bfloat16*)Q, ldq, k, (float*)x, m, ctx->scal, which);
+    k_gemv_sub<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const __nv_bfloat16*)Q, ldq, k, (float*)x, m, ctx->scal, which, 0);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }
@@ -1346,6 +1482,68 @@ kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_
     k_axpy_h<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const float*)q, (float*)v, m, ctx->scal);
   else
     k_axpy_h<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((const __nv_bfloat16*)q, (float*)v, m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+}  // namespace kc
+
+// ----------------------------------------------------------------------------------------
+// Row-partitioned DCGS2 (Section 4's distributed layout): each rank owns a block of rows of
+// Q, w, v and A; its reduction stores its partial sums (EPI_PARTIAL), the caller sums them
+// over the ranks (the one global reduction of the step), and the kernels below continue
+// from those sums.  The scalar step runs redundantly on every rank on identical sums, so
+// H and K stay replicated.
+// ----------------------------------------------------------------------------------------
+namespace kc {
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_scalar_from_totals(const double* __restrict__ totals, int k, Scalars* __restrict__ sc,
+                     StepArgs sa) {
+  __shared__ double tot[PSTRIDE];
+  if (sc->stop) return;
+  for (int i = threadIdx.x; i < 2 * (k + 1); i += blockDim.x) tot[i] = __ldcg(totals + i);
+  __syncthreads();
+  epilogue_from_tot(tot, k, 2, sc, EPI_DCGS2, sa);
+}
+
+// totals = [c_0 .. c_{k-1}, x^T x]: the coefficients of a finish projection and the
+// squared norm of the vector they came from (which 0: C, 1: C2)
+__global__ void k_store_totals(const double* __restrict__ totals, int k, int which,
+                               Scalars* __restrict__ sc) {
+  double* dst = which == 0 ? sc->C : sc->C2;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) dst[i] = __ldcg(totals + i);
+  if (threadIdx.x == 0) {
+    sc->norm_sq = __ldcg(totals + k);
+    if (!isfinite(sc->norm_sq)) set_status(sc, KC_ERR_NONFINITE);
+  }
+}
+
+// totals[0] = ||u||^2 over all ranks: the finish's H column, alpha and 1/alpha
+__global__ void k_finish_from_norm(const double* __restrict__ totals, Scalars* __restrict__ sc,
+                                   StepArgs sa) {
+  if (threadIdx.x == 0) norm_epilogue(__ldcg(totals), 0.0, sc, NEPI_FINISH, sa);
+}
+
+kc_status launch_scalar_from_totals(kc_ctx* ctx, const double* totals, int k,
+                                    const StepArgs& sa) {
+  if (k + 1 > NMAX) return fail(ctx, KC_ERR_INVALID_ARG, "scalar step: k = %d too large", k);
+  timing_begin(ctx, KID_SMALL);
+  k_scalar_from_totals<<<1, RED_THREADS, 0, ctx->stream>>>(totals, k, ctx->scal, sa);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_store_totals(kc_ctx* ctx, const double* totals, int k, int which) {
+  timing_begin(ctx, KID_SMALL);
+  k_store_totals<<<1, 128, 0, ctx->stream>>>(totals, k, which, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_finish_from_norm(kc_ctx* ctx, const double* totals, const StepArgs& sa) {
+  timing_begin(ctx, KID_SMALL);
+  k_finish_from_norm<<<1, 32, 0, ctx->stream>>>(totals, ctx->scal, sa);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }

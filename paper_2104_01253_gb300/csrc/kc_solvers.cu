@@ -184,9 +184,10 @@ static kc_status gmres_cycle(kc_ctx* ctx, const kc_csr* A, const Cycle& c, void*
   if ((s = read_scalars(ctx)) != KC_OK) return s;
   const Scalars* h = ctx->scal_host;
   if (c.gram) {
-    // loss of orthogonality of this cycle's basis: n + 1 columns after the CGS2 finish, the
-    // ncols columns built before an early stop
-    const int cols = h->stop ? h->ncols : c.n + 1;
+    // loss of orthogonality of the basis that formed this cycle's correction: its n
+    // columns (the cycle's finish normalises no column n), or the ncols built before an
+    // early stop
+    const int cols = h->stop ? h->ncols : c.n;
     if (cols >= 1) {
       if ((s = launch_gram(ctx, c.Q, c.ldq, c.qdt, m, cols, c.gram)) != KC_OK) return s;
       if ((s = launch_loo_from_gram(ctx, c.gram, cols, c.loo)) != KC_OK) return s;

@@ -19,8 +19,11 @@ from oracle import cnn  # noqa: E402
 from oracle.gmres import gmres as orc_gmres  # noqa: E402
 from synth import convdiff_csr, gaussian_vector, varcoef_fields_2d  # noqa: E402
 
-TOL_Y = 2e-2       # outputs: max-abs error over max-abs value
-TOL_G = 3e-2       # weight gradients, per layer
+# A flipped BF16 rounding changes a hidden value by one BF16 unit, 2^-8 of it; measured,
+# the largest output and weight-gradient differences stay below 5e-3 of the largest value
+# (0.3e-3 .. 4.9e-3 over the cases below), so the bound is 1e-2, about 2.5 BF16 units.
+TOL_Y = 1e-2       # outputs: max-abs error over max-abs value
+TOL_G = 1e-2       # weight gradients, per layer
 
 
 def elementwise(a, ref):

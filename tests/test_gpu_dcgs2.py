@@ -70,15 +70,16 @@ def test_spmv_matches_scipy(kc, ctx, name, make):
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("staged", [0, 2, 3])
+@pytest.mark.parametrize("staged", [0, 2, 3, 4])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("name,make", CASES)
 @pytest.mark.parametrize("n", [1, 2, 17, 50])
 def test_dcgs2_matches_oracle(kc, ctx, name, make, n, mode, staged):
     """The FP64 modes: all-FP64 products (0), FP64 with float-float offload (1) and the
     reduction as exact digit products on the tensor cores (2, which takes precedence over
-    the staged reduction); the register-streaming kernels (staged 0), the tensor-copy
-    staged reduction (2) and that with the bulk-copy staged update (3)."""
+    the staged reduction); the register-streaming kernels with the bounded FP32 products
+    of Q C (staged 0) and without them (4), the tensor-copy staged reduction (2) and that
+    with the bulk-copy staged update (3)."""
     Ah = make()
     r0 = gaussian_vector(Ah.m, 1002)
     ctx.set_fp64_mode(mode)

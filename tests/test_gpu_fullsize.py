@@ -39,14 +39,16 @@ def problem():
     return Ah, r0, Qo, Ho
 
 
-@pytest.mark.parametrize("mode", [1, 0, 2])
-def test_dcgs2_long_basis_matches_oracle(kc, problem, mode):
+@pytest.mark.parametrize("mode,flags", [(1, 0), (0, 0), (2, 0), (1, 4)])
+def test_dcgs2_long_basis_matches_oracle(kc, problem, mode, flags):
+    """flags 4: mode 1 without the bounded FP32 products of Q C (float-float always)."""
     Ah, r0, Qo, Ho = problem
     ctx = kc.Context(0)
     n = N_STEPS
     A = kc.DeviceCSR(Ah)
     st = kc.ArnoldiState(Ah.m, n + 1, kc.KC_F64)
     ctx.set_fp64_mode(mode)
+    ctx.set_staged(flags)
     try:
         kc.dcgs2_arnoldi_init(ctx, A, st, torch.as_tensor(r0, device="cuda"))
         for _ in range(n):
@@ -55,12 +57,13 @@ def test_dcgs2_long_basis_matches_oracle(kc, problem, mode):
         torch.cuda.synchronize()
     finally:
         ctx.set_fp64_mode(1)
+        ctx.set_staged(0)
     assert ctx.read_status() == 0
     Hg = st.H(n + 1, n).cpu().numpy()
     Qg = st.Q(n + 1).cpu().numpy()
     herr = np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho)
     qerr = np.abs(Qg - Qo).max()
-    print("mode %d: H rel %.2e, Q abs %.2e" % (mode, herr, qerr))
+    print("mode %d flags %d: H rel %.2e, Q abs %.2e" % (mode, flags, herr, qerr))
     assert herr <= 1e-12
     assert qerr <= 1e-10
     assert loo(Qg) <= 1e-13
