@@ -11,7 +11,10 @@ Householder QR (LAPACK) of the Krylov matrix, the k = 0 start, breakdown on A = 
 diagonal-matrix Lanczos case, and the Manteuffel spectrum through Krylov-Schur.
 The QR variants (tests/test_oracle_stability.py): the loss-of-orthogonality classes of
 Table 3 over graded condition numbers (CGS eps kappa^2, MGS eps kappa, CGS2 and DCGS2 at
-O(eps)), the representation error at O(eps), agreement with Householder QR.
+O(eps)), the representation error at O(eps), agreement with Householder QR.  ICWY-MGS
+(Section 6): the MGS class eps kappa of Table 3's level-2 MGS row, equality with MGS level 1
+in exact arithmetic (agreement on well-conditioned inputs), an exact Arnoldi relation, and
+planted mistakes (no L correction, L transposed) that leave its class.
 """
 from __future__ import annotations
 
@@ -246,3 +249,80 @@ def dcgs2_qr(B):
     R[:n - 1, n - 1] = S_prev + C1 + C2
     R[n - 1, n - 1] = alpha
     return Q, R
+
+
+def _forward_solve_unit_lower(L, r):
+    """y with (I + L) y = r, L strictly lower triangular (forward substitution)."""
+    y = np.array(r, dtype=np.float64, copy=True)
+    for i in range(y.shape[0]):
+        y[i] -= L[i, :i] @ y[:i]
+    return y
+
+
+def icwy_qr(B):
+    """ICWY-MGS QR of B (Section 6): the inverse compact WY projector
+    P a = (I - Q T Q^T) a with T = (I + L)^{-1}, L strictly lower triangular whose row i
+    holds the inner products q_i^T q_{0:i-1} (the strictly lower part of Q^T Q).  One
+    reduction per column: at iteration j (j >= 1) the single reduction
+    [Q_{0:j-2}, u_{j-1}]^T [u_{j-1}, a_j] gives row j-1 of L (scaled by the norm), the
+    norm of the pending u_{j-1} and Q^T a_j; then q_{j-1} = u_{j-1} / ||u_{j-1}||,
+    R(0:j, j) = (I + L)^{-1} Q_{0:j-1}^T a_j and u_j = a_j - Q_{0:j-1} R(0:j, j).  The last
+    column is normalised by one more reduction."""
+    m, n = B.shape
+    Q = np.zeros((m, n))
+    R = np.zeros((n, n))
+    L = np.zeros((n, n))
+    u = np.array(B[:, 0], dtype=np.float64, copy=True)       # u_0 = a_0
+    for j in range(1, n):
+        a = B[:, j]
+        Qp = Q[:, :j - 1]
+        ell = Qp.T @ u                    # the one reduction: Q^T u, u^T u, Q^T a, u^T a
+        beta = u @ u
+        r = Qp.T @ a
+        rho = u @ a
+        alpha = np.sqrt(beta)
+        Q[:, j - 1] = u / alpha
+        R[j - 1, j - 1] = alpha
+        L[j - 1, :j - 1] = ell / alpha    # row j-1 of L: q_{j-1}^T q_{0:j-2}
+        y = _forward_solve_unit_lower(L[:j, :j], np.concatenate([r, [rho / alpha]]))
+        R[:j, j] = y
+        u = a - Q[:, :j] @ y
+    alpha = np.sqrt(u @ u)
+    Q[:, n - 1] = u / alpha
+    R[n - 1, n - 1] = alpha
+    return Q, R
+
+
+def icwy_arnoldi(A, r0, n: int):
+    """ICWY-MGS Arnoldi (Section 6's projector in the Arnoldi expansion, one reduction per
+    step).  The pending vector w is the projected, unnormalised A q_{k-1} (w = r0 at the
+    start); step k applies A to w (v = A w, so A q_k = v / alpha), and its one reduction
+    [Q_k, w]^T [w, v] gives C = Q_k^T w, S = Q_k^T v, beta = w^T w and s = w^T v.  Then
+    alpha = sqrt(beta), q_k = w / alpha, H(k, k-1) = alpha, row k of L = C / alpha,
+    H(0:k+1, k) = (I + L)^{-1} [S / alpha; s / alpha^2] and w <- v / alpha - Q_{k+1} H(0:k+1, k).
+    The last column is normalised by one more reduction.  Q (m x (n+1)), H ((n+1) x n)."""
+    m = r0.shape[0]
+    Q = np.zeros((m, n + 1))
+    H = np.zeros((n + 1, n))
+    L = np.zeros((n + 1, n + 1))
+    w = np.array(r0, dtype=np.float64, copy=True)
+    for k in range(n):
+        v = _matvec(A, w)
+        Qk = Q[:, :k]
+        C = Qk.T @ w                      # the one reduction of the step
+        S = Qk.T @ v
+        beta = w @ w
+        s = w @ v
+        alpha = np.sqrt(beta)
+        Q[:, k] = w / alpha
+        if k >= 1:
+            H[k, k - 1] = alpha
+        L[k, :k] = C / alpha
+        y = _forward_solve_unit_lower(L[:k + 1, :k + 1],
+                                      np.concatenate([S / alpha, [s / alpha ** 2]]))
+        H[:k + 1, k] = y
+        w = v / alpha - Q[:, :k + 1] @ y
+    alpha = np.sqrt(w @ w)
+    H[n, n - 1] = alpha
+    Q[:, n] = w / alpha
+    return Q, H
