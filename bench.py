@@ -57,7 +57,7 @@ def parse():
                    help="skip the matrix-free stencil expansions and solves")
     p.add_argument("--no-solvers", action="store_true",
                    help="skip the GMRES time-to-1e-10 runs (plain FP64 vs FP32/BF16 IR)")
-    p.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1])
+    p.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1, 2])
     p.add_argument("--staged", type=int, default=None, choices=[0, 1, 2, 3],
                    help="kernel variants of the basis passes (kc_set_staged flags); "
                         "default: the library's")
@@ -95,11 +95,14 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
     m k f + 2 m (f = 1 with offload, 2 all-FP64) against the method's 2 m k + 2 m.  Update:
     bytes 8 m k + 32 m; FP64-pipe FMAs m k f + 5 m (offload; all-FP64 2 m k + 3 m) against
     2 m k + 3 m.  SpMV: 4 (m + 1) + 12 nnz + 16 m bytes, nnz FMAs.  The CGS2 finish (k = n):
-    two single-vector reductions (8 m k + 8 m bytes, m k + m FMAs each)."""
+    two single-vector reductions (8 m k + 8 m bytes, m k + m FMAs each).  In FP64 mode 2
+    the reduction's products are exact integer digit products on the tensor cores (no FP64
+    FMA per element)."""
     f = 2 if fp64_mode == 0 else 1
+    fr = {0: 2, 1: 1, 2: 0}[fp64_mode]            # mode 2: the reduction has no FP64 FMA
     rows = {
         "reduce": (sum(8 * m * k + 16 * m for k in range(n)),
-                   sum(m * k * f + 2 * m for k in range(n)),
+                   sum(m * k * fr + (2 * m if fr else 0) for k in range(n)),
                    sum(2 * m * k + 2 * m for k in range(n)), n),
         "dcgs2_update": (sum(8 * m * k + 32 * m for k in range(n)),
                          sum(m * k * f + (5 if f == 1 else 3) * m for k in range(n)),
@@ -120,7 +123,8 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
                      "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
                      "fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS,
                      "method_tflops": 2.0 * fma_method * steps / t / 1e12,
-                     "fp64_fma_per_elem": f if name in ("reduce", "dcgs2_update") else None}
+                     "fp64_fma_per_elem": (fr if name == "reduce" else
+                                           (f if name == "dcgs2_update" else None))}
     return out
 
 
@@ -745,7 +749,8 @@ def main():
             "loo": loo, "rre": rre, "device_status": status,
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
             "kernel_rooflines": per,
-            "fp64_mode": ["all-fp64", "fp64-with-float-float-offload"][ctx.fp64_mode],
+            "fp64_mode": ["all-fp64", "fp64-with-float-float-offload",
+                          "fp64-exact-digit-reduction-on-tensor-cores"][ctx.fp64_mode],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "same_gpu_baselines": baselines,
             "gpu_launches": launches, "clocks": clocks,
             "gmres_time_to_1e-10": solvers, "matrix_free": matrix_free,

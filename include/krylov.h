@@ -125,7 +125,7 @@ const char* kc_last_error(const kc_ctx* ctx);
  *     tensor cores as exact integer dot products of fixed-point digit expansions (the
  *     Ozaki scheme: basis entries as round(q 2^56), w and v scaled per 512-row chunk,
  *     FP16 digits, FP32 accumulators that stay exact, one FP64 rounding per chunk), with
- *     no FP64 arithmetic per basis entry; steps with more than 62 basis columns, or a
+ *     no FP64 arithmetic per basis entry; steps with more than 59 basis columns, or a
  *     basis, w or v not 16-byte aligned (odd leading dimension), use mode 1's reduction.
  *     A basis entry of magnitude >= 2 or a non-finite operand sets KC_ERR_NONFINITE.
  * Other values return KC_ERR_INVALID_ARG. */

@@ -454,6 +454,78 @@ kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, 
   return KC_OK;
 }
 
+// ---- ICWY-MGS (Section 6): the fused reduction with the ICWY epilogue, then the DCGS2
+// update with C = 0 (q_k = w / alpha, w <- v / alpha - Q_{k+1} y) -------------------------
+
+kc_status icwy_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  KC_TRY(validate_state(ctx, A, st));
+  if (st->q_dtype != KC_F64) return fail(ctx, KC_ERR_INVALID_ARG, "ICWY-MGS: FP64 basis only");
+  const int k = st->k;
+  if (k + 2 > st->ncap)
+    return fail(ctx, KC_ERR_INVALID_ARG, "basis full: k = %d, ncap = %d", k, st->ncap);
+  if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
+  KC_TRY(launch_spmv(ctx, A, st->w, st->v, KC_F64));                  // v = A w
+  StepArgs sa = step_args(st, k, 0);
+  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, KC_F64, k, st->w, st->v, A->m, KC_F64, EPI_ICWY,
+                       sa));                                          // the one reduction
+  KC_TRY(launch_dcgs2_update(ctx, st->Q, st->ldq, KC_F64, k, st->w, st->v, A->m, KC_F64));
+  st->k = k + 1;
+  return KC_OK;
+}
+
+kc_status icwy_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  KC_TRY(validate_csr(ctx, A));
+  KC_TRY(validate_state(ctx, A, st));
+  const int k = st->k;
+  if (k < 1) return fail(ctx, KC_ERR_INVALID_ARG, "finish needs at least one step");
+  if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
+  StepArgs sa = step_args(st, k, 0);
+  KC_TRY(launch_norm(ctx, st->w, nullptr, A->m, KC_F64, NEPI_MGS, sa));   // H(k, k-1) = ||w||
+  KC_TRY(launch_scale_to(ctx, st->w, qcol(st, k), KC_F64, A->m, KC_F64));
+  st->finished = 1;
+  return KC_OK;
+}
+
+kc_status icwy_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, double* Q,
+                  int64_t ldq, double* R, int ldr) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  if (!A || !Q || !R) return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
+  if (m < 1 || n < 1 || n + 1 > NMAX)
+    return fail(ctx, KC_ERR_INVALID_ARG, "icwy_qr: need m >= 1 and 1 <= n <= %d", NMAX - 1);
+  if (lda < m || ldq < m || ldr < n)
+    return fail(ctx, KC_ERR_INVALID_ARG, "icwy_qr: leading dimensions too small");
+  if ((lda & 1) || (ldq & 1) || ((uintptr_t)A & 15) || ((uintptr_t)Q & 15))
+    return fail(ctx, KC_ERR_INVALID_ARG,
+                "icwy_qr: A, Q must be 16-byte aligned with even leading dimensions");
+  const int64_t ldw = (m + 31) / 32 * 32;
+  const size_t lbytes = (size_t)(n + 1) * n * 8;
+  KC_TRY(ensure_workspace(ctx, (size_t)ldw * 8 + lbytes));
+  double* w = (double*)ctx->ws;
+  double* L = w + ldw;                 // the strictly lower triangular L, ld n + 1
+  KC_CUDA(ctx, cudaMemsetAsync(L, 0, lbytes, ctx->stream));
+  KC_CUDA(ctx, cudaMemset2DAsync(R, (size_t)ldr * 8, 0, (size_t)n * 8, (size_t)n, ctx->stream));
+  KC_CUDA(ctx, cudaMemcpyAsync(w, A, (size_t)m * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  StepArgs sa = {};
+  sa.H = R + ldr;                      // H(i, j) = R(i, j + 1)
+  sa.ldh = ldr;
+  sa.K = L;
+  sa.ldk = n + 1;
+  sa.flags = SF_QR;
+  for (int k = 0; k + 1 < n; k++) {    // step k: q_k, R(k, k) and R(0:k+1, k+1); pending a_{k+1}
+    const double* v = A + (int64_t)(k + 1) * lda;
+    sa.k = k;
+    KC_TRY(launch_reduce(ctx, Q, ldq, KC_F64, k, w, v, m, KC_F64, EPI_ICWY, sa));
+    KC_TRY(launch_dcgs2_update(ctx, Q, ldq, KC_F64, k, w, v, m, KC_F64));
+  }
+  sa.k = n - 1;                        // the last column: its norm (R(n-1, n-1)) and q_{n-1}
+  KC_TRY(launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_MGS, sa));
+  KC_TRY(launch_scale_to(ctx, w, Q + (int64_t)(n - 1) * ldq, KC_F64, m, KC_F64));
+  return KC_OK;
+}
+
 kc_status cgs2_arnoldi_init(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st, const void* r0) {
   if (!ctx) return KC_ERR_INVALID_ARG;
   KC_TRY(validate_csr(ctx, A));

@@ -254,15 +254,73 @@ __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __
 
 // Last CTA of a reduction: deterministic sum of the per-CTA partials, then either a plain
 // store of Q^T x or the scalar step of Algorithm 4.
+// The ICWY-MGS step (Section 6) from the summed [C, S, beta, s] of the fused reduction
+// (all threads of one CTA): alpha = sqrt(beta) = ||w|| normalises the pending w into q_k
+// (H(k, k-1) = alpha), row k of the strictly lower triangular L is C / alpha (stored in the
+// K workspace, K(k, i)), and the projection coefficients of the next vector are
+// y = (I + L)^{-1} r with r = [S / alpha; s / alpha^2] (QR of given columns: [S; s / alpha]),
+// by forward substitution; y is H(0:k+1, k) and, with C = 0, the update's T.
+__device__ void icwy_step(const double* tot, int k, Scalars* __restrict__ sc,
+                          const StepArgs& sa) {
+  __shared__ double s_r[NMAX + 1];
+  __shared__ double s_a;
+  const bool qr = (sa.flags & SF_QR) != 0;
+  if (threadIdx.x == 0) {
+    const double beta = tot[2 * k], s = tot[2 * k + 1];
+    double alpha = sqrt(beta);
+    if (!isfinite(beta) || !isfinite(s)) set_status(sc, KC_ERR_NONFINITE);
+    if (!(alpha > 0.0)) {
+      set_status(sc, KC_ERR_BREAKDOWN);
+      alpha = 1e-300;
+    }
+    sc->alpha = alpha;
+    sc->inv_alpha = 1.0 / alpha;
+    sc->vscale = qr ? 1.0 : 1.0 / alpha;
+    if (k >= 1 || qr) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;
+    s_r[k] = qr ? s / alpha : s / (alpha * alpha);
+    s_a = alpha;
+  }
+  __syncthreads();
+  const double alpha = s_a;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    sa.K[k + (int64_t)i * sa.ldk] = tot[2 * i] / alpha;        // L(k, i)
+    sc->C[i] = 0.0;                                            // the update projects with T only
+    s_r[i] = qr ? tot[2 * i + 1] : tot[2 * i + 1] / alpha;
+  }
+  __syncthreads();
+  for (int i = 0; i <= k; i++) {                               // (I + L) y = r, column by column
+    const double yi = s_r[i];
+    for (int l = i + 1 + threadIdx.x; l <= k; l += blockDim.x)
+      s_r[l] -= __ldcg(sa.K + l + (int64_t)i * sa.ldk) * yi;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
+    sc->T[i] = s_r[i];
+    sa.H[i + (int64_t)k * sa.ldh] = s_r[i];
+  }
+  if (threadIdx.x == 0 && k >= 1) {                            // happy breakdown test
+    double cn = alpha * alpha;
+    for (int i = 0; i < k; i++) {
+      const double h = sa.H[i + (int64_t)(k - 1) * sa.ldh];
+      cn += h * h;
+    }
+    if (alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
+  }
+}
+
 // The epilogue on the summed values tot[0 : (k + 1) NRHS] (shared memory; all threads of
-// one CTA): a store of this rank's sums (row-partitioned step), a store of Q^T x, or the
-// scalar step of Algorithm 4.
+// one CTA): a store of this rank's sums (row-partitioned step), a store of Q^T x, the
+// ICWY-MGS step, or the scalar step of Algorithm 4.
 __device__ void epilogue_from_tot(const double* tot, int k, int NRHS, Scalars* __restrict__ sc,
                                   int epilogue, const StepArgs& sa) {
   __shared__ double s_alpha;
   const int nval = (k + 1) * NRHS;
   if (epilogue == EPI_PARTIAL) {
     for (int i = threadIdx.x; i < nval; i += blockDim.x) sa.part[i] = tot[i];
+    return;
+  }
+  if (epilogue == EPI_ICWY) {
+    icwy_step(tot, k, sc, sa);
     return;
   }
   if (epilogue != EPI_DCGS2) {
@@ -1305,7 +1363,8 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
                                      (const double*)y, m, ctx->fp64_mode >= 1, sa);
     if (st != KC_OK) return st;
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two &&
-             (epilogue == EPI_DCGS2 || epilogue == EPI_PARTIAL) && ctx->fp64_mode >= 1) {
+             (epilogue == EPI_DCGS2 || epilogue == EPI_PARTIAL || epilogue == EPI_ICWY) &&
+             ctx->fp64_mode >= 1) {
     // Task layout: nsplit subsets of nt tasks (ceil(ntask / 48) <= nsplit <= ceil(ntask /
     // 32)), CTAs of nw <= 16 warps with tpw slots, chosen once per k and size class to
     // maximise resident warps x used slots.  Three slots (one row group per iteration,

@@ -82,7 +82,9 @@ def test_constants_describe_a_consistent_scheme():
     assert NA * BA >= 58 and NB * BB >= 59          # |X| < 2^57, |Y| < 2^58 plus the offset
     assert OFFA < 2 ** 60 and OFFB + 2 ** 58 <= 2 ** 60
     assert R * (2 ** (BA + 1) - 1) * (1 << (BB - 1)) <= 2 ** 24
-    assert NA * (128 // NA) <= 126                 # a tile keeps row 126 for the ones
+    # a 32-row quarter of an A tile holds TX_CPQ columns of NA digit rows, below the row
+    # of ones (row TX_ONES of the first quarter)
+    assert _const("TX_CPQ") * NA <= _const("TX_ONES") < 32
 
 
 @pytest.mark.parametrize("case", ["random", "wide_range", "q_near_2", "max_equal", "max_neg"])
