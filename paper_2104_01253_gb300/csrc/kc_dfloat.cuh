@@ -23,6 +23,26 @@ __device__ __forceinline__ bool split_df(double x, float& hi, float& lo) {
   return zero || (e - 943u) <= (1120u - 943u);
 }
 
+// The split of split_df for an operand that passed split_fast_ok (non-zero, magnitude in
+// [2^-80, 2^98)): no zero or range handling, the high float by one funnel shift.
+__device__ __forceinline__ void split_fast(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int H = (unsigned int)(b >> 32), L = (unsigned int)b;
+  const unsigned int sgn = H & 0x80000000u;
+  // exponent e - 896 (1..255 in range) and the top 23 significand bits, truncated
+  hi = __uint_as_float(__funnelshift_l(L, H - (896u << 20), 3) | sgn);
+  // the next 23 significand bits as an integer, times 2^(e - 1069) (in range: a normal float)
+  const float rf = __uint_as_float(0x4b000000u | ((L >> 6) & 0x7fffffu)) - 8388608.0f;
+  const float sc = __uint_as_float(((H & 0x7ff00000u) << 3) - (942u << 23));
+  lo = __uint_as_float(__float_as_uint(rf * sc) | sgn);
+}
+
+// true for the operands split_fast takes: non-zero with a magnitude in [2^-80, 2^98)
+__device__ __forceinline__ bool split_fast_ok(double x) {
+  const unsigned int H = (unsigned int)((unsigned long long)__double_as_longlong(x) >> 32);
+  return ((H & 0x7ff00000u) - (943u << 20)) <= (177u << 20);
+}
+
 // the range test of split_df alone: zero, or a magnitude in [2^-80, 2^98)
 __device__ __forceinline__ bool df_in_range(double x) {
   const unsigned int e = ((unsigned int)((unsigned long long)__double_as_longlong(x) >> 52)) & 0x7ffu;

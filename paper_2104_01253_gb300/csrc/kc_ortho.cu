@@ -704,7 +704,7 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // multiplied by the tiny C.  Both are evaluated here in float-float arithmetic
 // (operands split into two floats by integer operations, exact TwoProd products,
 // TwoSum accumulation; about 2^-44 relative), on the FP32/INT pipes, concurrently with
-// the FP64 FMAs of C and Q T.  Elements whose magnitude is outside [2^-80, 2^97] take
+// the FP64 FMAs of C and Q T.  Zeros and elements whose magnitude is outside [2^-80, 2^98) take
 // the FP64 path.
 // ----------------------------------------------------------------------------------------
 
@@ -733,7 +733,7 @@ __device__ __forceinline__ void f64x_group(const int (&tk)[TPW], int k,
                                            const double (&av)[TPW][2], double* ac,
                                            double* as64, float* sh, float* sl) {
   float yh[2], yl[2];
-  if (OFF) { split_df(yv[0], yh[0], yl[0]); split_df(yv[1], yh[1], yl[1]); }
+  if (OFF) { split_fast(yv[0], yh[0], yl[0]); split_fast(yv[1], yh[1], yl[1]); }
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
     if (tk[i] > k + 1) continue;                 // idle slot (warp-uniform)
@@ -742,8 +742,8 @@ __device__ __forceinline__ void f64x_group(const int (&tk)[TPW], int k,
     if (tk[i] < k) {
       if (OFF) {
         float ah[2], al[2];
-        split_df(av[i][0], ah[0], al[0]);
-        split_df(av[i][1], ah[1], al[1]);
+        split_fast(av[i][0], ah[0], al[0]);
+        split_fast(av[i][1], ah[1], al[1]);
         df_mac(sh[i], sl[i], ah[0], al[0], yh[0], yl[0]);
         df_mac(sh[i], sl[i], ah[1], al[1], yh[1], yl[1]);
       } else {
@@ -754,15 +754,16 @@ __device__ __forceinline__ void f64x_group(const int (&tk)[TPW], int k,
   }
 }
 
-// true when every operand that the float-float path splits lies in its range
+// true when every operand that the float-float path splits lies in its range (zero and
+// magnitudes outside [2^-80, 2^98) take the FP64 path)
 template <int TPW>
 __device__ __forceinline__ bool f64x_in_range(const int (&tk)[TPW], int k,
                                               const double (&yv)[2],
                                               const double (&av)[TPW][2]) {
-  bool ok = df_in_range(yv[0]) & df_in_range(yv[1]);
+  bool ok = split_fast_ok(yv[0]) & split_fast_ok(yv[1]);
 #pragma unroll
   for (int i = 0; i < TPW; i++)
-    if (tk[i] < k) ok = ok & df_in_range(av[i][0]) & df_in_range(av[i][1]);
+    if (tk[i] < k) ok = ok & split_fast_ok(av[i][0]) & split_fast_ok(av[i][1]);
   return ok;
 }
 
