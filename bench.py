@@ -8,6 +8,15 @@ per second; HBM GB/s (algorithmic bytes) is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Measurement suites (one GPU, one JSON line each; not the benchmark line):
+  python bench.py --suite steps  [--N 252] [--n 50] [--modes 1 2] [--basis f64|f32|bf16]
+      per-step kernel times of one expansion (reduction, update, SpMV), by FP64 mode;
+  python bench.py --suite solver [--config 1|2] [--grid2d N] [--path 0..3] [--precision 0..2]
+                                 [--matrix-free] [--restart n] [--reps 3]
+      one restarted GMRES solve to 1e-10, wall time and device time by kernel kind;
+  python bench.py --suite cnn    [--N 1024] [--batch 1] [--conv 0|1] [--forward 20] [--train 5]
+      the learned preconditioner's forward pass and training step.
+
 Under torchrun each rank runs an independent replica of the workload on its own GPU
 (weak scaling, no data-path collective); rank 0 prints one JSON line.  The reference arm
 (--impl reference) times the FP64 CPU oracle on the host cores on a bounded sample of
@@ -63,6 +72,21 @@ def parse():
                         "default: the library's")
     p.add_argument("--no-check", action="store_true",
                    help="skip the loss-of-orthogonality / Arnoldi-relation check")
+    p.add_argument("--suite", default=None, choices=["steps", "solver", "cnn"],
+                   help="a measurement suite instead of the benchmark line (module docstring)")
+    p.add_argument("--modes", type=int, nargs="+", default=[1], choices=[0, 1, 2])
+    p.add_argument("--basis", default="f64", choices=["f64", "f32", "bf16"])
+    p.add_argument("--config", type=int, default=1, choices=[1, 2])
+    p.add_argument("--grid2d", type=int, default=None)
+    p.add_argument("--path", type=int, default=0, choices=[0, 1, 2, 3])
+    p.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
+    p.add_argument("--matrix-free", action="store_true")
+    p.add_argument("--restart", type=int, default=None)
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--batch", type=int, default=1)
+    p.add_argument("--conv", type=int, default=1, choices=[0, 1])
+    p.add_argument("--forward", type=int, default=20)
+    p.add_argument("--train", type=int, default=5)
     p.add_argument("--no-parity", action="store_true",
                    help="skip the full-size comparison of H and sampled Q rows with the FP64 "
                         "oracle (about a minute of host time, outside the timed region)")
@@ -507,9 +531,156 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def suite_steps(args):
+    """Per-step kernel times of one n-step DCGS2 expansion of the N^3 operator (start vector
+    seed 1002): after one untimed expansion, every step of a second one is timed kernel by
+    kernel with per-launch CUDA events and a synchronize after the step."""
+    import torch
+    import paper_2104_01253_gb300 as kc
+    import synth
+    Ah = synth.config2_operator(args.N)
+    ctx = kc.Context(0)
+    qdt = {"f64": kc.KC_F64, "f32": kc.KC_F32, "bf16": kc.KC_BF16}[args.basis]
+    fdt = torch.float64 if args.basis == "f64" else torch.float32
+    A = kc.DeviceCSR(Ah, dtype=fdt)
+    st = kc.ArnoldiState(Ah.m, args.n + 1, qdt)
+    r0 = torch.as_tensor(synth.gaussian_vector(Ah.m, 1002), device="cuda", dtype=fdt)
+    for mode in args.modes:
+        ctx.set_fp64_mode(mode)
+        kc.dcgs2_arnoldi_init(ctx, A, st, r0)
+        for _ in range(args.n):
+            kc.dcgs2_arnoldi_step(ctx, A, st)
+        kc.dcgs2_arnoldi_init(ctx, A, st, r0)
+        torch.cuda.synchronize()
+        ctx.timing_enable(True)
+        ctx.timing_read()
+        per_k = []
+        for k in range(args.n):
+            kc.dcgs2_arnoldi_step(ctx, A, st)
+            torch.cuda.synchronize()
+            d = {kk: v[0] for kk, v in ctx.timing_read().items()}
+            per_k.append([k] + [round(1e3 * d.get(kk, 0.0), 1)
+                                for kk in ("reduce", "dcgs2_update", "spmv")])
+        ctx.timing_enable(False)
+        print(json.dumps({"suite": "steps", "m": Ah.m, "basis": args.basis, "fp64_mode": mode,
+                          "status": ctx.read_status(),
+                          "ms": {kk: round(sum(r[i] for r in per_k) / 1e3, 3)
+                                 for i, kk in enumerate(("reduce", "update", "spmv"), 1)},
+                          "per_step_us": {"columns": ["k", "reduce", "update", "spmv"],
+                                          "rows": per_k}}), flush=True)
+    ctx.set_fp64_mode(1)
+
+
+def suite_solver(args):
+    """One restarted DCGS2-GMRES solve to 1e-10 from x0 = 0 after a warm-up solve: config 1
+    (100^2, b seed 1001, GMRES(30)), config 2 (252^3, b seed 1004, GMRES(50)) or config 1's
+    family on an N x N grid; wall time (CUDA events around the C-ABI call, b and x resident)
+    and, from a separate solve, device time by kernel kind."""
+    import torch
+    import paper_2104_01253_gb300 as kc
+    import synth
+    if args.grid2d:
+        wind = 10.0 * np.array([1.0, 1.0]) / np.sqrt(2.0)
+        op = (synth.convdiff_stencil7(args.grid2d, 2, wind) if args.matrix_free
+              else synth.convdiff_csr(args.grid2d, 2, wind))
+        seed, restart = 1001, 30
+    elif args.config == 1:
+        op = synth.config1_stencil() if args.matrix_free else synth.config1_operator()
+        seed, restart = 1001, 30
+    else:
+        op = synth.config2_stencil() if args.matrix_free else synth.config2_operator()
+        seed, restart = 1004, 50
+    restart = args.restart or restart
+    ctx = kc.Context(0)
+    ctx.set_gmres_path(args.path)
+    mk = kc.DeviceStencil7 if args.matrix_free else kc.DeviceCSR
+    A = mk(op)
+    A32 = mk(op, dtype=torch.float32) if args.precision else None
+    b = torch.as_tensor(synth.gaussian_vector(A.m, seed), device="cuda")
+    x = torch.zeros_like(b)
+    solve = lambda: kc.gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10,
+                                   precision=args.precision, A32=A32, inner_rtol=1e-4,
+                                   inner_max_cycles=3)
+    solve()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count()
+    t0.record()
+    for _ in range(args.reps):
+        x.zero_()
+        info = solve()
+    t1.record()
+    torch.cuda.synchronize()
+    launches = (ctx.launch_count() - launches0) // args.reps
+    ms = t0.elapsed_time(t1) / args.reps
+    x.zero_()
+    ctx.timing_enable(True)
+    solve()
+    torch.cuda.synchronize()
+    kinds = ctx.timing_read()
+    ctx.timing_enable(False)
+    print(json.dumps({"suite": "solver",
+                      "config": ("2d N=%d" % args.grid2d) if args.grid2d else args.config,
+                      "operator": "stencil" if args.matrix_free else "csr",
+                      "path": ["auto", "multi-kernel", "cluster", "grid"][args.path],
+                      "precision": ["fp64", "fp32-inner-ir", "bf16-basis-ir"][args.precision],
+                      "m": A.m, "restart": restart, "ms_per_solve": ms, "iters": info["iters"],
+                      "status": info["status"], "rel_resid_true": info["rel_resid_true"],
+                      "launches_per_solve": launches,
+                      "us_per_iteration": 1e3 * ms / max(info["iters"], 1),
+                      "device_ms_by_kind": {k: v[0] for k, v in kinds.items()},
+                      "launches_by_kind": {k: v[1] for k, v in kinds.items()}}), flush=True)
+
+
+def suite_cnn(args):
+    """kc_cnn_forward and kc_cnn_train_step (regression loss, no Adam update) on a seeded
+    random batch of N x N images with He-initialised weights, after two warm-up calls of
+    each: mean time per call (CUDA events) and the forward pass's FLOP rate."""
+    import torch
+    import paper_2104_01253_gb300 as kc
+    from paper_2104_01253_gb300.train import he_init
+    ctx = kc.Context(0)
+    ctx.set_conv_kernel(args.conv)
+    B, N = args.batch, args.N
+    w = torch.as_tensor(he_init(0), device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(B, 1, N, N, device="cuda", generator=g)
+    e = torch.randn(B, 1, N, N, device="cuda", generator=g)
+    y = torch.empty_like(x)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(reps):
+            fn()
+        t1.record()
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / max(reps, 1)
+
+    out = {"suite": "cnn", "N": N, "batch": B, "conv": ["mma.sync", "tcgen05"][args.conv]}
+    if args.forward > 0:
+        ms = timed(lambda: kc.kc_cnn_forward(ctx, w, x, y, B, N, N), args.forward)
+        flop = B * N * N * (4 * 32 * 32 * 9 * 2 + 2 * 32 * 9 * 2)
+        out.update(forward_ms=ms, forward_tflops=flop / ms / 1e9)
+    if args.train > 0:
+        wt = w.clone()
+        out["train_step_ms"] = timed(
+            lambda: kc.kc_cnn_train_step(ctx, wt, None, None, 0, 0.0, x, e, B, N, N, y),
+            args.train)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
+    if args.suite:
+        if args.suite == "cnn" and args.N == 252:
+            args.N = 1024
+        return {"steps": suite_steps, "solver": suite_solver, "cnn": suite_cnn}[args.suite](args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 
