@@ -293,6 +293,21 @@ kc_status dcgs2_noalloc_read_status(int* status, void* cuda_stream);
 kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, double* Q,
                    int64_t ldq, double* R, int ldr);
 
+/* ICWY-MGS (Section 6): MGS with its rank-1 projections batched into the inverse compact
+ * WY projector I - Q T Q^T, T = (I + L)^{-1} with L the strictly lower triangular part of
+ * Q^T Q, one reduction per iteration (the fused reduction [Q_k, w]^T [w, A w] of the DCGS2
+ * step: its C gives row k of L, beta the norm of the pending w, S and s the projections),
+ * a triangular solve for the coefficients, and the update with C = 0.  Its loss of
+ * orthogonality is MGS's, O(eps) kappa (Table 3).  FP64 basis, every product in FP64.
+ *   icwy_arnoldi_step: start with dcgs2_arnoldi_init (w = r0); step k normalises w into q_k
+ *     (H(k, k-1) = ||w||), stores row k of L in the K workspace and appends H(0:k+1, k) with
+ *     the next pending w;  icwy_arnoldi_finish normalises the last pending w into q_k.
+ *   icwy_qr: Q R of a tall-skinny matrix, the arguments and layout of dcgs2_qr. */
+kc_status icwy_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
+kc_status icwy_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
+kc_status icwy_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, double* Q,
+                  int64_t ldq, double* R, int ldr);
+
 /* CGS2-Arnoldi (Algorithm 3) and MGS-Arnoldi (Section 2, "MGS Level 1"): init sets
  * q_0 = r0/||r0|| (k = 1); each step appends column k-1 of H and q_k.  CGS2 does three
  * reductions per step (two projections + norm), MGS one per inner product. */

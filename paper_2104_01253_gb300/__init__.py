@@ -219,6 +219,23 @@ def dcgs2_qr(ctx: Context, A, Q, R):
                                _ptr(R), R.stride(0)))
 
 
+def icwy_qr(ctx: Context, A, Q, R):
+    """ICWY-MGS QR (Section 6) in the layout of dcgs2_qr."""
+    n, m = A.shape
+    ctx.check(ctx.lib.icwy_qr(ctx.handle, _ptr(A), A.stride(0), m, n, _ptr(Q), Q.stride(0),
+                              _ptr(R), R.stride(0)))
+
+
+def icwy_arnoldi_step(ctx: Context, A: DeviceCSR, st: ArnoldiState):
+    """One ICWY-MGS Arnoldi step (start with dcgs2_arnoldi_init)."""
+    ctx.check(ctx.lib.icwy_arnoldi_step(ctx.handle, C.byref(A.c), C.byref(st.c)))
+
+
+def icwy_arnoldi_finish(ctx: Context, A: DeviceCSR, st: ArnoldiState):
+    """Normalise the pending vector into the last basis column."""
+    ctx.check(ctx.lib.icwy_arnoldi_finish(ctx.handle, C.byref(A.c), C.byref(st.c)))
+
+
 def dcgs2_arnoldi_init(ctx: Context, A: DeviceCSR, st: ArnoldiState, r0):
     ctx.check(ctx.lib.dcgs2_arnoldi_init(ctx.handle, C.byref(A.c), C.byref(st.c), _ptr(r0)))
 

@@ -79,6 +79,9 @@ _SIGS = {
                           C.c_int),
     "kc_basis_gram": ([_P, _P, C.c_int64, C.c_int, C.c_int64, C.c_int, _P], C.c_int),
     "dcgs2_qr": ([_P, _P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int], C.c_int),
+    "icwy_qr": ([_P, _P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int], C.c_int),
+    "icwy_arnoldi_step": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),
+    "icwy_arnoldi_finish": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),
     "cgs2_arnoldi_init": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi), _P], C.c_int),
     "cgs2_arnoldi_step": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),
     "mgs_arnoldi_step": ([_P, C.POINTER(kc_csr), C.POINTER(kc_arnoldi)], C.c_int),

@@ -709,9 +709,9 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
 // ----------------------------------------------------------------------------------------
 
 // Offloaded reduction, task layout.  ntask = k + 2 tasks of equal FP64 cost (two FP64
-// FMAs per group of two rows): task t < k is column t (C_t = q_t^T w in FP64 and
-// S_t = q_t^T v in float-float), task k is beta = w^T w and task k + 1 is s = w^T v, both
-// in FP64.  The tasks are cut into nsplit subsets of at most 48 (nt each); the grid is
+// FMAs per group of two rows): task t < k is column t
+// (C_t = q_t^T w in FP64 and S_t = q_t^T v in float-float), task k is beta = w^T w and
+// task k + 1 is s = w^T v, both in FP64.  The tasks are cut into nsplit subsets of at most 48 (nt each); the grid is
 // nsplit CTAs per row block, CTA (row block r, subset h) has nw = ceil(nt / TPW) warps and
 // warp w takes the subset's tasks w, w + nw, ... (TPW slots, TPW <= 3), so at most TPW - 1
 // slots of a CTA are idle and every CTA has at most 16 warps (two or more CTAs per SM
@@ -725,8 +725,9 @@ __device__ __forceinline__ const double* f64x_operand(const double* Q, int64_t l
   return t < k ? Q + (int64_t)t * ldq : (t == k ? x : (t == k + 1 ? y : nullptr));
 }
 
-// One group of two rows for every slot: ac += a . w (FP64); for columns S += a . v in
-// float-float (OFF) or FP64 (!OFF, operands outside the float-float range).
+// One group of two rows for every slot: ac += a . w (FP64; C, beta and s); for columns
+// S += a . v in float-float (OFF) or FP64 (!OFF, operands outside the float-float range).
+// (s = w^T v in float-float as well measured slower: the warp that holds it then splits w.)
 template <int TPW, bool OFF>
 __device__ __forceinline__ void f64x_group(const int (&tk)[TPW], int k,
                                            const double (&xv)[2], const double (&yv)[2],
@@ -758,12 +759,13 @@ __device__ __forceinline__ void f64x_group(const int (&tk)[TPW], int k,
 // magnitudes outside [2^-80, 2^98) take the FP64 path)
 template <int TPW>
 __device__ __forceinline__ bool f64x_in_range(const int (&tk)[TPW], int k,
-                                              const double (&yv)[2],
+                                              const double (&xv)[2], const double (&yv)[2],
                                               const double (&av)[TPW][2]) {
   bool ok = split_fast_ok(yv[0]) & split_fast_ok(yv[1]);
 #pragma unroll
   for (int i = 0; i < TPW; i++)
     if (tk[i] < k) ok = ok & split_fast_ok(av[i][0]) & split_fast_ok(av[i][1]);
+  (void)xv;
   return ok;
 }
 
@@ -814,7 +816,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
       ldv(y, g + 32, yb);
       f64x_load<TPW>(ap, g, qa);
       f64x_load<TPW>(ap, g + 32, qb);
-      const bool ok = f64x_in_range<TPW>(tk, k, ya, qa) & f64x_in_range<TPW>(tk, k, yb, qb);
+      const bool ok = f64x_in_range<TPW>(tk, k, xa, ya, qa) & f64x_in_range<TPW>(tk, k, xb, yb, qb);
       if (__builtin_expect(__all_sync(__activemask(), ok), 1)) {
         f64x_group<TPW, true>(tk, k, xa, ya, qa, ac, as64, sh, sl);
         f64x_group<TPW, true>(tk, k, xb, yb, qb, ac, as64, sh, sl);
@@ -829,7 +831,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
     ldv(x, g, xa);
     ldv(y, g, ya);
     f64x_load<TPW>(ap, g, qa);
-    if (__builtin_expect(__all_sync(__activemask(), f64x_in_range<TPW>(tk, k, ya, qa)), 1))
+    if (__builtin_expect(__all_sync(__activemask(), f64x_in_range<TPW>(tk, k, xa, ya, qa)), 1))
       f64x_group<TPW, true>(tk, k, xa, ya, qa, ac, as64, sh, sl);
     else
       f64x_group<TPW, false>(tk, k, xa, ya, qa, ac, as64, sh, sl);
@@ -842,7 +844,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
         if (!ap[i]) continue;
         const double a = __ldcg(ap[i] + row);
         ac[i] = fma(a, xs, ac[i]);
-        as64[i] = fma(a, ys1, as64[i]);
+        if (tk[i] < k) as64[i] = fma(a, ys1, as64[i]);   // S of columns only
       }
     }
   }
@@ -860,6 +862,81 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
   }
   if (!last_cta(counter)) return;
   reduce_epilogue(partials, k, 2, sc, epi, sa, nr);
+}
+
+// Q_k^T x and x^T x (one vector: the CGS2 finish's projections) with the offload
+// reduction's task layout: tasks t < k are columns, task k is x^T x, every product in FP64
+// (one FMA per basis element, no float-float part); GR row groups per iteration with all
+// loads first.  Partials hold the k + 1 sums of each row block in task order.
+template <int TPW, int GR>
+__global__ void __launch_bounds__(1024)
+k_reduce1_f64(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
+              int64_t m, double* __restrict__ partials, unsigned int* __restrict__ counter,
+              Scalars* __restrict__ sc, StepArgs sa, int nsplit, int nt, int epi) {
+  if (sc->stop) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int h = blockIdx.x % nsplit, r = blockIdx.x / nsplit, nr = gridDim.x / nsplit;
+  const double* ap[TPW];
+  int tk[TPW];
+  double ac[TPW];
+#pragma unroll
+  for (int i = 0; i < TPW; i++) {
+    const int tl = warp + nw * i;
+    tk[i] = tl < nt ? h * nt + tl : k + 1;             // k + 1 and above: idle slot
+    ap[i] = tk[i] < k ? Q + (int64_t)tk[i] * ldq : (tk[i] == k ? x : nullptr);
+    ac[i] = 0.0;
+  }
+  const int64_t ngroups = m / 2;
+  const int64_t g0 = (int64_t)r * ngroups / nr;
+  const int64_t g1 = (int64_t)(r + 1) * ngroups / nr;
+  int64_t g = g0 + lane;
+  if (GR == 2) {
+    for (; g + 32 < g1; g += 64) {
+      double xa[2], xb[2], qa[TPW][2], qb[TPW][2];
+      ldv(x, g, xa);
+      ldv(x, g + 32, xb);
+#pragma unroll
+      for (int i = 0; i < TPW; i++)
+        if (ap[i]) { load_q(ap[i], g, qa[i]); load_q(ap[i], g + 32, qb[i]); }
+#pragma unroll
+      for (int i = 0; i < TPW; i++) {
+        if (!ap[i]) continue;                        // idle slot (warp-uniform)
+        ac[i] = fma(qa[i][0], xa[0], ac[i]);
+        ac[i] = fma(qa[i][1], xa[1], ac[i]);
+        ac[i] = fma(qb[i][0], xb[0], ac[i]);
+        ac[i] = fma(qb[i][1], xb[1], ac[i]);
+      }
+    }
+  }
+  for (; g < g1; g += 32) {
+    double xa[2], qa[TPW][2];
+    ldv(x, g, xa);
+#pragma unroll
+    for (int i = 0; i < TPW; i++)
+      if (ap[i]) load_q(ap[i], g, qa[i]);
+#pragma unroll
+    for (int i = 0; i < TPW; i++) {
+      if (!ap[i]) continue;
+      ac[i] = fma(qa[i][0], xa[0], ac[i]);
+      ac[i] = fma(qa[i][1], xa[1], ac[i]);
+    }
+  }
+  if (r == nr - 1) {                             // ragged tail (m odd)
+    for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
+      const double xs = __ldcg(x + row);
+#pragma unroll
+      for (int i = 0; i < TPW; i++)
+        if (ap[i]) ac[i] = fma(__ldcg(ap[i] + row), xs, ac[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TPW; i++) {
+    if (!ap[i]) continue;
+    const double c = warp_sum(ac[i]);
+    if (lane == 0) partials[(int64_t)r * PSTRIDE + tk[i]] = c;
+  }
+  if (!last_cta(counter)) return;
+  reduce_epilogue(partials, k, 1, sc, epi, sa, nr);
 }
 
 // Two basis columns of the offloaded update for one group of two rows: u -= Q C in
@@ -1341,48 +1418,24 @@ static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int
   else args(k_reduce<TQ, TV, 8, NRHS>);
 }
 
-kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
-                        const void* x, const void* y, int64_t m, int vec_dtype, int epilogue,
-                        const StepArgs& sa) {
-  if (k + 1 > NMAX) return fail(ctx, KC_ERR_INVALID_ARG, "reduce: k = %d too large", k);
-  const int R = vec_dtype == KC_F64 ? 2 : 4;
-  const int grid = reduce_grid_for(ctx, m / R);
-  const bool two = y != nullptr;
-  const bool ok = (q_dtype == KC_F64 && vec_dtype == KC_F64) ||
-                  (q_dtype != KC_F64 && vec_dtype == KC_F32);
-  if (!ok)
-    return fail(ctx, KC_ERR_INVALID_ARG, "reduce: unsupported basis/vector types %d/%d", q_dtype, vec_dtype);
-  timing_begin(ctx, KID_REDUCE);
-  if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
-      ctx->fp64_mode == 2 && reduce_tcx_supported(k, m, Q, ldq, x, y)) {
-    kc_status st = launch_reduce_tcx(ctx, (const double*)Q, ldq, k, (const double*)x,
-                                     (const double*)y, m, sa);
-    if (st != KC_OK) return st;
-  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
-      (ctx->staged & 2) && reduce_tma_supported(k, m)) {
-    kc_status st = launch_reduce_tma(ctx, (const double*)Q, ldq, k, (const double*)x,
-                                     (const double*)y, m, ctx->fp64_mode >= 1, sa);
-    if (st != KC_OK) return st;
-  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two &&
-             (epilogue == EPI_DCGS2 || epilogue == EPI_PARTIAL || epilogue == EPI_ICWY) &&
-             ctx->fp64_mode >= 1) {
-    // Task layout: nsplit subsets of nt tasks (ceil(ntask / 48) <= nsplit <= ceil(ntask /
-    // 32)), CTAs of nw <= 16 warps with tpw slots, chosen once per k and size class to
-    // maximise resident warps x used slots.  Three slots (one row group per iteration,
-    // which fits 64 registers) keep 33-48 tasks in one subset, so that w and v are read
-    // once per row block.  Below 33 tasks their small CTAs pay off only on long vectors:
-    // at m = 16 M, 8 warps x 3 slots beat 12 x 2 for 21-24 tasks (753-822 us against
-    // 833-872), while at m = 10^6 the larger CTAs won (83-86 us against 90-97).  (Three
-    // subsets and more, or more subsets than needed, measured slower.)  Sweeps of every
-    // layout at each k (m = 16 M and 10^6) found three ranges where the score misjudges,
-    // taken from the measurements instead: 33-36 tasks run fastest as two subsets of two
-    // slots (5% at both sizes), and up to 16 tasks as one subset of two slots on long
-    // vectors (up to 14%) but of one slot on short ones.
-    const int ntask = k + 2;
-    const int big = m >= ((int64_t)1 << 22);
-    int nsplit, nt, tpw, nw, occ;
-    {
-      int* pick = ctx->red_pick[big][k];
+// Task layout of the offload reduction for ntask equal tasks (the DCGS2 step: k + 2; the
+// finish's one-vector reductions: k + 1, which share the entry of ntask - 2):
+// Task layout: nsplit subsets of nt tasks (ceil(ntask / 48) <= nsplit <= ceil(ntask /
+// 32)), CTAs of nw <= 16 warps with tpw slots, chosen once per k and size class to
+// maximise resident warps x used slots.  Three slots (one row group per iteration,
+// which fits 64 registers) keep 33-48 tasks in one subset, so that w and v are read
+// once per row block.  Below 33 tasks their small CTAs pay off only on long vectors:
+// at m = 16 M, 8 warps x 3 slots beat 12 x 2 for 21-24 tasks (753-822 us against
+// 833-872), while at m = 10^6 the larger CTAs won (83-86 us against 90-97).  (Three
+// subsets and more, or more subsets than needed, measured slower.)  Sweeps of every
+// layout at each k (m = 16 M and 10^6) found three ranges where the score misjudges,
+// taken from the measurements instead: 33-36 tasks run fastest as two subsets of two
+// slots (5% at both sizes), and up to 16 tasks as one subset of two slots on long
+// vectors (up to 14%) but of one slot on short ones.
+static void f64x_layout(kc_ctx* ctx, int ntask, int big, int& nsplit, int& nt, int& tpw,
+                        int& nw, int& occ) {
+  {
+      int* pick = ctx->red_pick[big][ntask - 2];
       if (pick[0] == 0) {
         auto occ_of = [&](int tp, int nww) {
           int& o = ctx->red_occ[tp - 1][nww];
@@ -1428,6 +1481,35 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
       }
       nsplit = pick[0]; nt = pick[1]; tpw = pick[2]; nw = pick[3]; occ = pick[4];
     }
+}
+
+kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
+                        const void* x, const void* y, int64_t m, int vec_dtype, int epilogue,
+                        const StepArgs& sa) {
+  if (k + 1 > NMAX) return fail(ctx, KC_ERR_INVALID_ARG, "reduce: k = %d too large", k);
+  const int R = vec_dtype == KC_F64 ? 2 : 4;
+  const int grid = reduce_grid_for(ctx, m / R);
+  const bool two = y != nullptr;
+  const bool ok = (q_dtype == KC_F64 && vec_dtype == KC_F64) ||
+                  (q_dtype != KC_F64 && vec_dtype == KC_F32);
+  if (!ok)
+    return fail(ctx, KC_ERR_INVALID_ARG, "reduce: unsupported basis/vector types %d/%d", q_dtype, vec_dtype);
+  timing_begin(ctx, KID_REDUCE);
+  if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
+      ctx->fp64_mode == 2 && reduce_tcx_supported(k, m, Q, ldq, x, y)) {
+    kc_status st = launch_reduce_tcx(ctx, (const double*)Q, ldq, k, (const double*)x,
+                                     (const double*)y, m, sa);
+    if (st != KC_OK) return st;
+  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
+      (ctx->staged & 2) && reduce_tma_supported(k, m)) {
+    kc_status st = launch_reduce_tma(ctx, (const double*)Q, ldq, k, (const double*)x,
+                                     (const double*)y, m, ctx->fp64_mode >= 1, sa);
+    if (st != KC_OK) return st;
+  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two &&
+             (epilogue == EPI_DCGS2 || epilogue == EPI_PARTIAL) && ctx->fp64_mode >= 1) {
+    const int ntask = k + 2;
+    int nsplit, nt, tpw, nw, occ;
+    f64x_layout(ctx, ntask, m >= ((int64_t)1 << 22), nsplit, nt, tpw, nw, occ);
     int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);            // row blocks: >= 4 groups/lane
     int64_t nr = ((int64_t)ctx->num_sms * occ + nsplit - 1) / nsplit;
     if (nr > gcap) nr = gcap < 1 ? 1 : gcap;
@@ -1440,6 +1522,24 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
     else if (tpw == 2) go(k_reduce_f64x<2, 2>);
     else go(k_reduce_f64x<3, 1>);
+  } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && !two && k >= 1 &&
+             (epilogue == EPI_STORE_C || epilogue == EPI_STORE_C2 || epilogue == EPI_PARTIAL) &&
+             ctx->fp64_mode >= 1) {
+    // one vector (the CGS2 finish): the offload layout for k + 1 FP64 tasks
+    int nsplit, nt, tpw, nw, occ;
+    f64x_layout(ctx, k + 1, m >= ((int64_t)1 << 22), nsplit, nt, tpw, nw, occ);
+    int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);
+    int64_t nr = ((int64_t)ctx->num_sms * occ + nsplit - 1) / nsplit;
+    if (nr > gcap) nr = gcap < 1 ? 1 : gcap;
+    const int g = (int)(nr * nsplit);
+    auto go = [&](auto kern) {
+      kern<<<g, 32 * nw, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x, m,
+                                           ctx->partials, ctx->counters, ctx->scal, sa, nsplit,
+                                           nt, epilogue);
+    };
+    if (tpw == 1) go(k_reduce1_f64<1, 2>);
+    else if (tpw == 2) go(k_reduce1_f64<2, 2>);
+    else go(k_reduce1_f64<3, 2>);
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
     if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
     else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);

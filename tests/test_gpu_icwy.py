@@ -1,0 +1,91 @@
+"""GPU parity of ICWY-MGS (Section 6: the inverse compact WY projector with
+T = (I + L)^{-1}, one reduction per iteration) against the FP64 oracle: the Arnoldi
+expansion (H to 1e-12 relative, basis to 1e-10, exact Arnoldi relation) and the QR of
+given columns (elementwise on a well-conditioned matrix; on ill-conditioned ones the loss
+of orthogonality in MGS's class O(eps) kappa of Table 3, as the oracle's)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import arnoldi as orc  # noqa: E402
+from oracle.metrics import loo, rre  # noqa: E402
+from synth import convdiff_csr, gaussian_vector, graded_matrix, manteuffel_csr  # noqa: E402
+
+EPS = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def kc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2104_01253_gb300 as kc
+    return kc
+
+
+@pytest.fixture(scope="module")
+def ctx(kc):
+    return kc.Context(0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("make,n", [(lambda: convdiff_csr(10, 3, [1.0, 0.5, 0.25]), 20),
+                                    (lambda: manteuffel_csr(23), 30),
+                                    (lambda: convdiff_csr(37, 3, [50.0, 25.0, 12.5]), 12)])
+def test_icwy_arnoldi_matches_oracle(kc, ctx, make, n, mode):
+    Ah = make()
+    r0 = gaussian_vector(Ah.m, 1002)
+    A = kc.DeviceCSR(Ah)
+    st = kc.ArnoldiState(Ah.m, n + 1, kc.KC_F64)
+    ctx.set_fp64_mode(mode)
+    try:
+        kc.dcgs2_arnoldi_init(ctx, A, st, torch.as_tensor(r0, device="cuda"))
+        for _ in range(n):
+            kc.icwy_arnoldi_step(ctx, A, st)
+        kc.icwy_arnoldi_finish(ctx, A, st)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_fp64_mode(1)
+    assert ctx.read_status() == 0
+    Hg = st.H(n + 1, n).cpu().numpy()
+    Qg = st.Q(n + 1).cpu().numpy()
+    Qo, Ho = orc.icwy_arnoldi(Ah.to_scipy(), r0, n)
+    assert np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho) <= 1e-12
+    assert np.abs(Qg - Qo).max() <= 1e-10
+    assert rre(Ah.to_scipy(), Qg, Hg) <= 1e-14
+    assert abs(loo(Qg) - loo(Qo)) <= 1e-12
+
+
+def _qr(kc, ctx, B):
+    """B (m x n) through icwy_qr, columns stored with an even leading dimension."""
+    m, n = B.shape
+    ld = m + (m & 1)
+    At = np.zeros((n, ld))
+    At[:, :m] = B.T
+    Ad = torch.as_tensor(At, device="cuda")
+    Q = torch.zeros_like(Ad)
+    R = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    kc.icwy_qr(ctx, Ad[:, :m], Q[:, :m], R)
+    torch.cuda.synchronize()
+    return Q[:, :m].cpu().numpy().T, R.cpu().numpy().T
+
+
+def test_icwy_qr_matches_oracle_when_well_conditioned(kc, ctx):
+    B = graded_matrix(100003, 40, 10.0, 77)
+    Q, R = _qr(kc, ctx, B)
+    Qo, Ro = orc.icwy_qr(B)
+    assert np.abs(Q - Qo).max() <= 1e-12
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-13
+    assert ctx.read_status() == 0
+
+
+@pytest.mark.parametrize("e", [4, 8, 12])
+def test_icwy_qr_orthogonality_class(kc, ctx, e):
+    B = graded_matrix(20000, 30, 10.0 ** e, 500 + e)
+    Q, R = _qr(kc, ctx, B)
+    Qo, _ = orc.icwy_qr(B)
+    lg, lo = loo(Q), loo(Qo)
+    assert 1e-3 * EPS * 10.0 ** e <= lg <= 1e2 * EPS * 10.0 ** e, (e, lg)
+    assert 0.1 <= lg / lo <= 10.0, (e, lg, lo)
+    assert np.linalg.norm(B - Q @ R) / np.linalg.norm(B) <= 10 * EPS
