@@ -116,22 +116,26 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
     """Achieved rates of the step's kernels from their CUDA-event times (kc_timing_read):
     algorithmic bytes and FLOPs per expansion (the n DCGS2 steps) over each kernel's summed
     launch time.  Reduction at step k: bytes 8 m k + 16 m (Q_k, w, v); FP64-pipe FMAs
-    m k f + 2 m (f = 1 with offload, 2 all-FP64) against the method's 2 m k + 2 m.  Update:
+    m k f (+ 2 m for beta and s in the all-FP64 mode; with offload the SpMV forms them) with
+    f = 1 with offload, 2 all-FP64, against the method's 2 m k + 2 m.  Update:
     bytes 8 m k + 32 m; FP64-pipe FMAs m k f + 5 m (offload; all-FP64 2 m k + 3 m) against
-    2 m k + 3 m.  SpMV: 4 (m + 1) + 12 nnz + 16 m bytes, nnz FMAs.  The CGS2 finish (k = n):
+    2 m k + 3 m.  SpMV: 4 (m + 1) + 12 nnz + 16 m bytes, nnz + 2 m FMAs (the matvec, beta and
+    s).  The CGS2 finish (k = n):
     two single-vector reductions (8 m k + 8 m bytes, m k + m FMAs each).  In FP64 mode 2
     the reduction's products are exact integer digit products on the tensor cores (no FP64
     FMA per element)."""
     f = 2 if fp64_mode == 0 else 1
     fr = {0: 2, 1: 1, 2: 0}[fp64_mode]            # mode 2: the reduction has no FP64 FMA
+    bs = 2 if fp64_mode == 0 else 0               # beta, s FMAs per row in the reduction
     rows = {
         "reduce": (sum(8 * m * k + 16 * m for k in range(n)),
-                   sum(m * k * fr + (2 * m if fr else 0) for k in range(n)),
+                   sum(m * k * fr + bs * m for k in range(n)),
                    sum(2 * m * k + 2 * m for k in range(n)), n),
         "dcgs2_update": (sum(8 * m * k + 32 * m for k in range(n)),
                          sum(m * k * f + (5 if f == 1 else 3) * m for k in range(n)),
                          sum(2 * m * k + 3 * m for k in range(n)), n),
-        "spmv": (n * (4 * (m + 1) + 12 * nnz + 16 * m), n * nnz, n * nnz, n),
+        "spmv": (n * (4 * (m + 1) + 12 * nnz + 16 * m), n * (nnz + 2 * m), n * (nnz + 2 * m),
+                 n),
         "finish_reduce": (2 * (8 * m * n + 8 * m), 2 * (m * n + m), 2 * (m * n + m), 2),
     }
     out = {}

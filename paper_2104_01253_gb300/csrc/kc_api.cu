@@ -130,6 +130,8 @@ kc_status kc_create(kc_ctx** out, int device, void* cuda_stream) {
   const size_t plen =
       (size_t)PARTIAL_CTAS_PER_SM * p.multiProcessorCount * (2 * NMAX + 4) * sizeof(double);
   bool ok = cudaMalloc(&ctx->partials, plen) == cudaSuccess &&
+            cudaMalloc(&ctx->dots, (size_t)16 * p.multiProcessorCount * sizeof(double)) ==
+                cudaSuccess &&
             cudaMalloc(&ctx->counters, 16 * sizeof(unsigned int)) == cudaSuccess &&
             cudaMalloc(&ctx->scal, sizeof(Scalars)) == cudaSuccess &&
             cudaMallocHost(&ctx->scal_host, sizeof(Scalars)) == cudaSuccess;
@@ -154,6 +156,7 @@ kc_status kc_destroy(kc_ctx* ctx) {
   }
   delete[] ctx->trec;
   if (ctx->partials) cudaFree(ctx->partials);
+  if (ctx->dots) cudaFree(ctx->dots);
   if (ctx->counters) cudaFree(ctx->counters);
   if (ctx->scal) cudaFree(ctx->scal);
   if (ctx->scal_host) cudaFreeHost(ctx->scal_host);
@@ -284,7 +287,8 @@ kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
     return fail(ctx, KC_ERR_INVALID_ARG, "basis full: k = %d, ncap = %d", k, st->ncap);
   if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
   const int vec = vec_of(st);
-  KC_TRY(launch_spmv(ctx, A, st->w, st->v, vec));                       // v = A w
+  if (vec == KC_F64) KC_TRY(launch_spmv_dots(ctx, A, st->w, st->v, vec));  // v = A w
+  else KC_TRY(launch_spmv(ctx, A, st->w, st->v, vec));
   StepArgs sa = step_args(st, k, vec == KC_F32 ? SF_FALLBACK : 0);
   KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec,
                        EPI_DCGS2, sa));                                  // one reduction

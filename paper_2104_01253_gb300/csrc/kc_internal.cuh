@@ -134,6 +134,10 @@ struct kc_ctx {
   int red_occ[4][33];      // resident CTAs per SM of the offload reduction, by (TPW, warps)
   int red_pick[2][kc::NMAX][5]; // its task layout per size class (m >= 2^22) and k: nsplit, tasks per subset, TPW, warps, CTAs/SM
   double* partials;        // PARTIAL_CTAS_PER_SM * num_sms * (2*NMAX + 4) doubles
+  double* dots;            // the DCGS2 step's SpMV: per-CTA (w^T w, w^T v), 8 * num_sms pairs
+  int dots_pending;        // CTAs whose pairs the next reduction of (dots_x, dots_y) takes
+  const void* dots_x;
+  const void* dots_y;
   unsigned int* counters;  // ticket counters for last-CTA reductions
   kc::Scalars* scal;       // device scalars
   kc::Scalars* scal_host;  // pinned host mirror for reads
@@ -212,6 +216,10 @@ inline kc_status smem_attr_once(kc_ctx* ctx, std::atomic<unsigned long long>& do
 
 // Launch helpers implemented in kc_ortho.cu, used by the drivers in kc_solvers.cu.
 kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype);
+// v = A w of a DCGS2 step (FP64) that also forms beta = w^T w and s = w^T v per CTA; the
+// next launch_reduce of (w, v) with the DCGS2 epilogue in the offload mode takes them
+// instead of computing them (any other launch_reduce drops them)
+kc_status launch_spmv_dots(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype);
 kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
                         const void* x, const void* y, int64_t m, int vec_dtype, int epilogue,
                         const StepArgs& sa);

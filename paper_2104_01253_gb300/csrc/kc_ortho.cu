@@ -202,20 +202,47 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
 // ----------------------------------------------------------------------------------------
 // K4': CSR SpMV, one thread per row.
 // ----------------------------------------------------------------------------------------
-template <typename TA, typename TV>
+// CTA sums of x^T x and x^T y (FP64, fixed order) into dots[2 b], dots[2 b + 1]
+__device__ __forceinline__ void store_dots(double ab, double as, double* dots) {
+  __shared__ double red[2][8];
+  ab = warp_sum(ab);
+  as = warp_sum(as);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[0][warp] = ab; red[1][warp] = as; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0, t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) { b += red[0][i]; t += red[1][i]; }
+    dots[2 * blockIdx.x] = b;
+    dots[2 * blockIdx.x + 1] = t;
+  }
+}
+
+// DOTS (FP64 DCGS2 step): the same pass also sums beta = x^T x and s = x^T y per CTA, the
+// two FP64 tasks of the step's reduction, at the cost of one more load of x[r] (in cache)
+// and two FMAs per row in this HBM-bound kernel.
+template <typename TA, typename TV, bool DOTS = false>
 __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rp,
                                               const int32_t* __restrict__ ci,
                                               const TA* __restrict__ val,
                                               const TV* __restrict__ x, TV* __restrict__ y,
-                                              int64_t m, const Scalars* __restrict__ sc) {
+                                              int64_t m, const Scalars* __restrict__ sc,
+                                              double* __restrict__ dots = nullptr) {
   if (sc->stop) return;
+  double ab = 0.0, as = 0.0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
        r += (int64_t)gridDim.x * blockDim.x) {
     int b = __ldg(rp + r), e = __ldg(rp + r + 1);
     TA s = 0;
     for (int j = b; j < e; j++) s += __ldg(val + j) * (TA)__ldcg(x + __ldg(ci + j));
     y[r] = (TV)s;
+    if (DOTS) {
+      const double xr = (double)__ldcg(x + r);
+      ab = fma(xr, xr, ab);
+      as = fma(xr, (double)s, as);
+    }
   }
+  if (DOTS) store_dots(ab, as, dots);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -229,11 +256,13 @@ struct Stencil7 {
   T c[7];       // centre, x-1, x+1, y-1, y+1, z-1, z+1
 };
 
-template <typename T>
+template <typename T, bool DOTS = false>
 __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __restrict__ y,
                                                   int nx, int ny, int nz, Stencil7<T> c,
-                                                  const Scalars* __restrict__ sc) {
+                                                  const Scalars* __restrict__ sc,
+                                                  double* __restrict__ dots = nullptr) {
   if (sc->stop) return;
+  double ab = 0.0, as = 0.0;
   const int64_t m = (int64_t)nx * ny * nz, pl = (int64_t)nx * ny;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -249,11 +278,15 @@ __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __
     if (iy < ny - 1) s += c.c[4] * __ldcg(x + r + nx);
     if (iz < nz - 1) s += c.c[6] * __ldcg(x + r + pl);
     y[r] = s;
+    if (DOTS) {
+      const double xr = (double)__ldcg(x + r);
+      ab = fma(xr, xr, ab);
+      as = fma(xr, (double)s, as);
+    }
   }
+  if (DOTS) store_dots(ab, as, dots);
 }
 
-// Last CTA of a reduction: deterministic sum of the per-CTA partials, then either a plain
-// store of Q^T x or the scalar step of Algorithm 4.
 // The ICWY-MGS step (Section 6) from the summed [C, S, beta, s] of the fused reduction
 // (all threads of one CTA): alpha = sqrt(beta) = ||w|| normalises the pending w into q_k
 // (H(k, k-1) = alpha), row k of the strictly lower triangular L is C / alpha (stored in the
@@ -373,12 +406,26 @@ __device__ void epilogue_from_tot(const double* tot, int k, int NRHS, Scalars* _
   if (s_ok) scalar_step(sc, sa, k, s_alpha);
 }
 
+// Last CTA of a reduction: deterministic sum of the per-CTA partials, then the epilogue.
+// With `dots` (the DCGS2 step whose SpMV formed beta = w^T w and s = w^T v, ndots CTAs of
+// two sums each), the partials hold the 2k column sums only and beta, s are the
+// fixed-order sums of the SpMV's.
 __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int NRHS,
                                 Scalars* __restrict__ sc, int epilogue, const StepArgs& sa,
-                                int nparts = -1) {
+                                int nparts = -1, const double* __restrict__ dots = nullptr,
+                                int ndots = 0) {
   __shared__ double tot[PSTRIDE];
   const int nval = (k + 1) * NRHS;
-  sum_partials(partials, nparts < 0 ? (int)gridDim.x : nparts, nval, tot);
+  sum_partials(partials, nparts < 0 ? (int)gridDim.x : nparts, dots ? 2 * k : nval, tot);
+  if (dots) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+    for (int which = warp; which < 2; which += nwp) {         // 0: beta, 1: s
+      double v = 0.0;
+      for (int c = lane; c < ndots; c += 32) v += __ldcg(dots + 2 * c + which);
+      v = warp_sum(v);
+      if (lane == 0) tot[2 * k + which] = v;
+    }
+  }
   __syncthreads();
   epilogue_from_tot(tot, k, NRHS, sc, epilogue, sa);
 }
@@ -788,10 +835,11 @@ __global__ void __launch_bounds__(1024)
 k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
               const double* __restrict__ y, int64_t m, double* __restrict__ partials,
               unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa,
-              int nsplit, int nt, int epi) {
+              int nsplit, int nt, int epi, const double* __restrict__ dots, int ndots) {
   if (sc->stop) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int h = blockIdx.x % nsplit, r = blockIdx.x / nsplit, nr = gridDim.x / nsplit;
+  const int tmax = ndots ? k : k + 2;             // tasks of this launch (columns first)
   int tk[TPW];
   const double* ap[TPW];
   double ac[TPW], as64[TPW];
@@ -799,13 +847,16 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
     const int tl = warp + nw * i;                      // task within the subset
-    tk[i] = tl < nt ? h * nt + tl : k + 2;             // k + 2 and above: idle slot
+    tk[i] = tl < nt && h * nt + tl < tmax ? h * nt + tl : k + 2;   // k + 2: idle slot
     ap[i] = f64x_operand(Q, ldq, k, x, y, tk[i]);
     ac[i] = 0.0; as64[i] = 0.0; sh[i] = 0.0f; sl[i] = 0.0f;
   }
+  bool busy = false;                             // a warp without a task skips the rows
+#pragma unroll
+  for (int i = 0; i < TPW; i++) busy |= ap[i] != nullptr;
   const int64_t ngroups = m / 2;
   const int64_t g0 = (int64_t)r * ngroups / nr;
-  const int64_t g1 = (int64_t)(r + 1) * ngroups / nr;
+  const int64_t g1 = busy ? (int64_t)(r + 1) * ngroups / nr : g0;
   int64_t g = g0 + lane;
   if (GR == 2) {
     for (; g + 32 < g1; g += 64) {
@@ -836,7 +887,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
     else
       f64x_group<TPW, false>(tk, k, xa, ya, qa, ac, as64, sh, sl);
   }
-  if (r == nr - 1) {                             // ragged tail (m odd): FP64
+  if (r == nr - 1 && busy) {                     // ragged tail (m odd): FP64
     for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
       const double xs = __ldcg(x + row), ys1 = __ldcg(y + row);
 #pragma unroll
@@ -861,7 +912,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
     }
   }
   if (!last_cta(counter)) return;
-  reduce_epilogue(partials, k, 2, sc, epi, sa, nr);
+  reduce_epilogue(partials, k, 2, sc, epi, sa, nr, dots, ndots);
 }
 
 // Q_k^T x and x^T x (one vector: the CGS2 finish's projections) with the offload
@@ -1346,6 +1397,7 @@ static int reduce_grid_for(const kc_ctx* ctx, int64_t ngroups) {
 namespace kc {
 
 kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype) {
+  ctx->dots_pending = 0;                        // a new matvec: earlier SpMV sums are stale
   int grid = grid_for(ctx, A->m, 256, 8);
   if ((A->val_dtype == KC_F64) != (vec_dtype == KC_F64))
     return fail(ctx, KC_ERR_INVALID_ARG, "spmv: matrix value type %d does not match vector type %d",
@@ -1371,6 +1423,27 @@ kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int 
     k_spmv<float, float><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
         (const float*)A->val, (const float*)x, (float*)y, A->m, ctx->scal);
   KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_spmv_dots(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype) {
+  ctx->dots_pending = 0;
+  if (vec_dtype != KC_F64 || A->val_dtype != KC_F64) return launch_spmv(ctx, A, x, y, vec_dtype);
+  const int grid = grid_for(ctx, A->m, 256, 8);         // <= 8 * num_sms (the dots buffer)
+  timing_begin(ctx, KID_SPMV);
+  if (is_stencil(A)) {
+    Stencil7<double> c;
+    for (int i = 0; i < 7; i++) c.c[i] = A->stencil[i];
+    k_stencil7<double, true><<<grid, 256, 0, ctx->stream>>>((const double*)x, (double*)y,
+        A->grid[0], A->grid[1], A->grid[2], c, ctx->scal, ctx->dots);
+  } else {
+    k_spmv<double, double, true><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
+        (const double*)A->val, (const double*)x, (double*)y, A->m, ctx->scal, ctx->dots);
+  }
+  KC_LAUNCHED(ctx);
+  ctx->dots_pending = grid;
+  ctx->dots_x = x;
+  ctx->dots_y = y;
   return KC_OK;
 }
 
@@ -1494,6 +1567,10 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
                   (q_dtype != KC_F64 && vec_dtype == KC_F32);
   if (!ok)
     return fail(ctx, KC_ERR_INVALID_ARG, "reduce: unsupported basis/vector types %d/%d", q_dtype, vec_dtype);
+  // beta and s from the step's SpMV (launch_spmv_dots), taken only by the offload kernel
+  const int ndots = (ctx->dots_pending > 0 && ctx->dots_x == x && ctx->dots_y == y &&
+                     epilogue == EPI_DCGS2) ? ctx->dots_pending : 0;
+  ctx->dots_pending = 0;
   timing_begin(ctx, KID_REDUCE);
   if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two && epilogue == EPI_DCGS2 &&
       ctx->fp64_mode == 2 && reduce_tcx_supported(k, m, Q, ldq, x, y)) {
@@ -1507,17 +1584,26 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     if (st != KC_OK) return st;
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && two &&
              (epilogue == EPI_DCGS2 || epilogue == EPI_PARTIAL) && ctx->fp64_mode >= 1) {
-    const int ntask = k + 2;
+    // with beta and s from the SpMV the step's tasks are its k columns only
+    const int ntask = ndots ? k : k + 2;
     int nsplit, nt, tpw, nw, occ;
-    f64x_layout(ctx, ntask, m >= ((int64_t)1 << 22), nsplit, nt, tpw, nw, occ);
+    f64x_layout(ctx, ntask < 2 ? 2 : ntask, m >= ((int64_t)1 << 22), nsplit, nt, tpw, nw, occ);
     int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);            // row blocks: >= 4 groups/lane
     int64_t nr = ((int64_t)ctx->num_sms * occ + nsplit - 1) / nsplit;
     if (nr > gcap) nr = gcap < 1 ? 1 : gcap;
+    if (ntask == 0) {                        // k = 0: the epilogue alone, on the SpMV's sums
+      nr = 1;
+      nsplit = 1;
+      nt = 0;
+      nw = 1;
+      tpw = 1;
+    }
     const int g = (int)(nr * nsplit);
     auto go = [&](auto kern) {
       kern<<<g, 32 * nw, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
                                            (const double*)y, m, ctx->partials, ctx->counters,
-                                           ctx->scal, sa, nsplit, nt, epilogue);
+                                           ctx->scal, sa, nsplit, nt, epilogue,
+                                           ndots ? ctx->dots : nullptr, ndots);
     };
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
     else if (tpw == 2) go(k_reduce_f64x<2, 2>);
