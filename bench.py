@@ -120,8 +120,8 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
     f = 1 with offload, 2 all-FP64, against the method's 2 m k + 2 m.  Update:
     bytes 8 m k + 32 m; FP64-pipe FMAs m k f + 5 m (offload; all-FP64 2 m k + 3 m) against
     2 m k + 3 m.  SpMV: 4 (m + 1) + 12 nnz + 16 m bytes, nnz + 2 m FMAs (the matvec, beta and
-    s).  The CGS2 finish (k = n):
-    two single-vector reductions (8 m k + 8 m bytes, m k + m FMAs each).  In FP64 mode 2
+    s).  The CGS2 finish (k = n): the first projection's sums (8 m k + 8 m bytes) and the fused
+    u = w - Q C1 with the second projection's sums (8 m k + 16 m bytes), m k + m FMAs each.  In FP64 mode 2
     the reduction's products are exact integer digit products on the tensor cores (no FP64
     FMA per element)."""
     f = 2 if fp64_mode == 0 else 1
@@ -136,7 +136,8 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
                          sum(2 * m * k + 3 * m for k in range(n)), n),
         "spmv": (n * (4 * (m + 1) + 12 * nnz + 16 * m), n * (nnz + 2 * m), n * (nnz + 2 * m),
                  n),
-        "finish_reduce": (2 * (8 * m * n + 8 * m), 2 * (m * n + m), 2 * (m * n + m), 2),
+        "finish_reduce": ((8 * m * n + 8 * m) + (8 * m * n + 16 * m), 2 * (m * n + m),
+                          2 * (m * n + m), 2),
     }
     out = {}
     for name, (byts, fma_pipe, fma_method, launches) in rows.items():

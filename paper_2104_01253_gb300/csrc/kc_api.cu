@@ -315,9 +315,8 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
   } phase(ctx);
   KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, nullptr, A->m, vec,
                        EPI_STORE_C, sa));                                // C1 = Q^T w
-  KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec, 0));
-  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, nullptr, A->m, vec,
-                       EPI_STORE_C2, sa));                               // C2 = Q^T u
+  KC_TRY(launch_proj_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec,
+                            sa));                  // u = w - Q C1, C2 = Q^T u in one pass
   KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec, 1));
   KC_TRY(launch_norm(ctx, st->w, nullptr, A->m, vec, NEPI_FINISH, sa));  // alpha = ||u||
   KC_TRY(launch_scale_to(ctx, st->w, qcol(st, k), st->q_dtype, A->m, vec));

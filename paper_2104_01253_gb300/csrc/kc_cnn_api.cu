@@ -433,8 +433,7 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
     }
     sa.k = n;
     if ((s = launch_reduce(ctx, Q, ld, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C, sa)) != KC_OK) return s;
-    if ((s = launch_gemv_sub(ctx, Q, ld, KC_F64, n, w, m, KC_F64, 0)) != KC_OK) return s;
-    if ((s = launch_reduce(ctx, Q, ld, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C2, sa)) != KC_OK) return s;
+    if ((s = launch_proj_reduce(ctx, Q, ld, KC_F64, n, w, m, KC_F64, sa)) != KC_OK) return s;
     if ((s = launch_gemv_sub(ctx, Q, ld, KC_F64, n, w, m, KC_F64, 1)) != KC_OK) return s;
     if ((s = launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_FINISH, sa)) != KC_OK) return s;
     timing_begin(ctx, KID_SMALL);

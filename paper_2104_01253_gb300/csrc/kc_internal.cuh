@@ -227,6 +227,10 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
                               const void* v, int64_t m, int vec_dtype);
 kc_status launch_gemv_sub(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k, void* x,
                           int64_t m, int vec_dtype, int which);
+// the CGS2 finish's u = w - Q C1 and the sums [Q^T u, u^T u] (EPI_STORE_C2) in one pass over
+// Q where it can (FP64 offload modes, k <= 64), else the two launches apart
+kc_status launch_proj_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k, void* w,
+                             int64_t m, int vec_dtype, const StepArgs& sa);
 kc_status launch_fallback_norm(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
                                const void* w, int64_t m, const StepArgs& sa);
 kc_status launch_norm(kc_ctx* ctx, const void* x, const void* y, int64_t m, int vec_dtype,

@@ -990,6 +990,159 @@ k_reduce1_f64(const double* __restrict__ Q, int64_t ldq, int k, const double* __
   reduce_epilogue(partials, k, 1, sc, epi, sa, nr);
 }
 
+// ----------------------------------------------------------------------------------------
+// The CGS2 finish's middle passes in one: u = w - Q_k C1 (row-local) and the sums
+// [Q_k^T u, u^T u] of the second projection, over tiles of PR_TR rows of Q staged in shared
+// memory (double-buffered 16-byte asynchronous copies), so the basis is read once for both.
+// u is formed as in k_gemv_sub with allow32: FP32 products of the truncated entries when
+// (k + 3) 2^-24 ||C1||_1 <= 2^-53 ||w - Q C1||, else FP64 (decided per launch from the
+// device scalars); the sums are FP64, accumulated per (task, row) slot across tiles and
+// combined in a fixed order, then stored by the last CTA like a one-vector reduction
+// (EPI_STORE_C2: C2 and the squared norm of u).
+// ----------------------------------------------------------------------------------------
+constexpr int PR_TR = 64;                       // rows per tile
+constexpr int PR_THREADS = 256;
+constexpr int PR_MAXK = 64;                     // basis columns the fused pass takes
+constexpr int PR_LD = PR_TR;                    // tile column stride (doubles)
+constexpr int PR_TPW = (PR_MAXK + 1 + PR_THREADS / 32 - 1) / (PR_THREADS / 32);  // tasks per warp
+
+__device__ __forceinline__ void pr_cp16(void* dst, const void* src) {
+  const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" :: "r"(d), "l"(src) : "memory");
+}
+
+__global__ void __launch_bounds__(PR_THREADS)
+k_proj_reduce(const double* __restrict__ Q, int64_t ldq, int k, double* __restrict__ w,
+              int64_t m, double* __restrict__ partials, unsigned int* __restrict__ counter,
+              Scalars* __restrict__ sc, StepArgs sa) {
+  if (sc->stop) return;
+  extern __shared__ double pr_smem[];
+  double* tile = pr_smem;                                // 2 x k x PR_LD
+  __shared__ double su[PR_TR];
+  __shared__ float zp32[4][PR_TR];
+  __shared__ double zp64[4][PR_TR];
+  __shared__ float sf[PR_MAXK];
+  __shared__ double sd[PR_MAXK];
+  __shared__ double s_scale;
+  __shared__ int s_fast;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < k; i += PR_THREADS) sd[i] = sc->C[i];
+  if (tid == 0) {
+    double cmax = 0.0, l1 = 0.0, c2 = 0.0;
+    for (int i = 0; i < k; i++) {
+      const double c = sc->C[i];
+      cmax = fmax(cmax, fabs(c));
+      l1 += fabs(c);
+      c2 += c * c;
+    }
+    const double rest = sc->norm_sq - c2;
+    int ex = 0;
+    if (cmax > 0.0) frexp(cmax, &ex);
+    s_scale = ldexp(1.0, ex);
+    s_fast = (rest > 0.0 && cmax > 0.0 && ex > -900 &&
+              l1 * (double)(k + 3) <= 0x1p-29 * sqrt(rest)) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool fast = s_fast;
+  const double scale = s_scale;
+  for (int i = tid; i < k; i += PR_THREADS) sf[i] = d2f_trunc(sd[i] / scale);
+  // phase-B slots: warp w owns tasks w, w + 8, ... (columns, then u^T u as task k); its lanes
+  // own rows lane and lane + 32 of every tile
+  double acc[PR_TPW];
+#pragma unroll
+  for (int i = 0; i < PR_TPW; i++) acc[i] = 0.0;
+  const int64_t ntiles = m / PR_TR;                       // whole tiles; the rest below
+  auto fetch = [&](int64_t t, int buf) {
+    const int64_t r0 = t * PR_TR;
+    double* dst = tile + (size_t)buf * k * PR_LD;
+    for (int e = tid; e < k * (PR_TR / 2); e += PR_THREADS) {
+      const int j = e / (PR_TR / 2), c2 = e % (PR_TR / 2);
+      pr_cp16(dst + j * PR_LD + 2 * c2, Q + (int64_t)j * ldq + r0 + 2 * c2);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int buf = 0;
+  int64_t t = blockIdx.x;
+  if (t < ntiles) fetch(t, 0);
+  for (; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) {
+      fetch(tn, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const double* tb = tile + (size_t)buf * k * PR_LD;
+    const int64_t r0 = t * PR_TR;
+    // phase A: u = w - Q C1; thread (part, row) sums the columns j = part mod 4
+    {
+      const int row = tid % PR_TR, part = tid / PR_TR;
+      if (fast) {
+        float z = 0.0f;
+        for (int j = part; j < k; j += 4) z = fmaf(d2f_trunc(tb[j * PR_LD + row]), sf[j], z);
+        zp32[part][row] = z;
+      } else {
+        double z = 0.0;
+        for (int j = part; j < k; j += 4) z = fma(tb[j * PR_LD + row], sd[j], z);
+        zp64[part][row] = z;
+      }
+    }
+    __syncthreads();
+    if (tid < PR_TR) {
+      double u;
+      if (fast) {
+        const float z = (zp32[0][tid] + zp32[1][tid]) + (zp32[2][tid] + zp32[3][tid]);
+        u = fma(-f2d_bits(z), scale, __ldcg(w + r0 + tid));
+      } else {
+        u = __ldcg(w + r0 + tid) -
+            ((zp64[0][tid] + zp64[1][tid]) + (zp64[2][tid] + zp64[3][tid]));
+      }
+      su[tid] = u;
+      w[r0 + tid] = u;
+    }
+    __syncthreads();
+    // phase B: the sums of the second projection
+#pragma unroll
+    for (int i = 0; i < PR_TPW; i++) {
+      const int task = warp + (PR_THREADS / 32) * i;
+      if (task > k) break;
+      const double* col = task < k ? tb + task * PR_LD : su;
+      acc[i] = fma(col[lane], su[lane], acc[i]);
+      acc[i] = fma(col[lane + 32], su[lane + 32], acc[i]);
+    }
+    __syncthreads();                                     // the buffer is refilled next
+  }
+  // rows past the last whole tile (fewer than PR_TR): the last CTA's warp 0, FP64
+  if (blockIdx.x == gridDim.x - 1) {
+    for (int64_t row = ntiles * PR_TR + tid; row < m; row += PR_THREADS) {
+      double z = 0.0;
+      for (int j = 0; j < k; j++) z = fma(__ldcg(Q + (int64_t)j * ldq + row), sd[j], z);
+      w[row] = __ldcg(w + row) - z;
+    }
+    __syncthreads();
+    for (int64_t row = ntiles * PR_TR + lane; row < m; row += 32) {
+      const double u = __ldcg(w + row);
+#pragma unroll
+      for (int i = 0; i < PR_TPW; i++) {
+        const int task = warp + (PR_THREADS / 32) * i;
+        if (task > k) break;
+        const double a = task < k ? __ldcg(Q + (int64_t)task * ldq + row) : u;
+        acc[i] = fma(a, u, acc[i]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < PR_TPW; i++) {
+    const int task = warp + (PR_THREADS / 32) * i;
+    if (task > k) break;
+    const double v = warp_sum(acc[i]);
+    if (lane == 0) partials[(int64_t)blockIdx.x * PSTRIDE + task] = v;
+  }
+  if (!last_cta(counter)) return;
+  reduce_epilogue(partials, k, 1, sc, EPI_STORE_C2, sa);
+}
+
 // Two basis columns of the offloaded update for one group of two rows: u -= Q C in
 // float-float (OFF) or FP64 (!OFF).
 template <bool OFF>
@@ -1655,6 +1808,33 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
     k_dcgs2_update<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((float*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
   else
     k_dcgs2_update<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((__nv_bfloat16*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
+}
+
+kc_status launch_proj_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k, void* w,
+                             int64_t m, int vec_dtype, const StepArgs& sa) {
+  const bool fused = q_dtype == KC_F64 && vec_dtype == KC_F64 && ctx->fp64_mode >= 1 &&
+                     !(ctx->staged & 4) && k >= 1 && k <= PR_MAXK && (ldq & 1) == 0 &&
+                     ((uintptr_t)Q & 15) == 0 && m >= PR_TR;
+  if (!fused) {                                 // the two passes apart
+    KC_TRY(launch_gemv_sub(ctx, Q, ldq, q_dtype, k, w, m, vec_dtype, 0));
+    return launch_reduce(ctx, Q, ldq, q_dtype, k, w, nullptr, m, vec_dtype, EPI_STORE_C2, sa);
+  }
+  static std::atomic<unsigned long long> attr{0};
+  const int smem = 2 * k * PR_LD * (int)sizeof(double);
+  KC_TRY(smem_attr_once(ctx, attr, k_proj_reduce, 2 * PR_MAXK * PR_LD * (int)sizeof(double),
+                        "proj_reduce"));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_proj_reduce, PR_THREADS, smem) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  if (per_sm > PARTIAL_CTAS_PER_SM) per_sm = PARTIAL_CTAS_PER_SM;
+  int64_t grid = (int64_t)ctx->num_sms * per_sm, ntiles = m / PR_TR;
+  if (grid > ntiles) grid = ntiles;
+  timing_begin(ctx, KID_FIN_REDUCE);
+  k_proj_reduce<<<(int)grid, PR_THREADS, smem, ctx->stream>>>((const double*)Q, ldq, k,
+      (double*)w, m, ctx->partials, ctx->counters, ctx->scal, sa);
   KC_LAUNCHED(ctx);
   return KC_OK;
 }

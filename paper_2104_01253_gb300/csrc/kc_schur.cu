@@ -705,8 +705,7 @@ extern "C" kc_status krylov_schur_eigs(kc_ctx* ctx, const kc_csr* A, const doubl
     }
     sa.k = n;
     if ((s = launch_reduce(ctx, Qa, ldq, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C, sa)) != KC_OK) return s;
-    if ((s = launch_gemv_sub(ctx, Qa, ldq, KC_F64, n, w, m, KC_F64, 0)) != KC_OK) return s;
-    if ((s = launch_reduce(ctx, Qa, ldq, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C2, sa)) != KC_OK) return s;
+    if ((s = launch_proj_reduce(ctx, Qa, ldq, KC_F64, n, w, m, KC_F64, sa)) != KC_OK) return s;
     if ((s = launch_gemv_sub(ctx, Qa, ldq, KC_F64, n, w, m, KC_F64, 1)) != KC_OK) return s;
     if ((s = launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_FINISH, sa)) != KC_OK) return s;
     if ((s = launch_scale_to(ctx, w, Qa + (size_t)n * ldq, KC_F64, m, KC_F64)) != KC_OK) return s;
