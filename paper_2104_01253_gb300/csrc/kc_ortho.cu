@@ -1227,12 +1227,12 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
       double wn[2] = {vv[0] * vsc, vv[1] * vsc};
       float z[2] = {0.0f, 0.0f};
       int i = 0;
-      for (; i + 4 <= k; i += 4) {      // four columns' loads in flight before arithmetic
-        double q[4][2];
+      for (; i + 8 <= k; i += 8) {      // eight columns' loads in flight before arithmetic
+        double q[8][2];
 #pragma unroll
-        for (int j = 0; j < 4; j++) load_q(Q + (int64_t)(i + j) * ldq, g, q[j]);
+        for (int j = 0; j < 8; j++) load_q(Q + (int64_t)(i + j) * ldq, g, q[j]);
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < 8; j++) {
           wn[0] = fma(-q[j][0], sT[i + j], wn[0]);
           wn[1] = fma(-q[j][1], sT[i + j], wn[1]);
           z[0] = fmaf(d2f_trunc(q[j][0]), cH[i + j], z[0]);
