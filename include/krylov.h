@@ -136,10 +136,12 @@ int kc_get_fp64_mode(const kc_ctx* ctx);
  *     (one producer thread and an mbarrier ring per SM);
  *  2: the fused DCGS2 reduction stages 2D tiles of the basis with tensor-memory copies
  *     (cp.async.bulk.tensor, one producer thread, sixteen consumer warps per SM);
- *  4: FP64 mode 1 / 2 without the bounded FP32 products: Q C of the update and of the
- *     CGS2 finish's projections then always take float-float (update) or FP64 (finish),
- *     instead of FP32 products on the launches whose error bound,
- *     (k + 3) 2^-24 ||C||_1 <= 2^-53 ||w - Q C||, holds.
+ *  4: FP64 mode 1 / 2 without the bounded FP32 products and the float-float first
+ *     projection: Q C of the update and of the CGS2 finish's projections then always
+ *     take float-float (update) or FP64 (finish), instead of FP32 products on the
+ *     launches whose error bound, (k + 3) 2^-24 ||C||_1 <= 2^-53 ||w - Q C||, holds; and
+ *     the finish's first projection C1 = Q^T w is summed in FP64 instead of float-float
+ *     (its error is removed by the second projection either way).
  * 0 streams both passes through registers, with the bounded FP32 products. */
 kc_status kc_set_staged(kc_ctx* ctx, int flags);
 /* Kernel of the network's 32 -> 32 convolutions: 0 mma.sync (m16n8k16, registers);
@@ -409,6 +411,17 @@ kc_status kc_cnn_train_step_residual(kc_ctx* ctx, float* w32, float* adam_m, flo
                                      int64_t t, float lr, const kc_csr* A, const float* x,
                                      const float* r, int B, int H, int W, float* y, float* grad,
                                      double* loss);
+
+/* One training sample of the residual loss from the current iterate of a solve (the
+ * (residual, correction) pairs of Section 7, the correction left implicit):
+ *   r = b - A x,  u = D^{-1} r,  s = rms(u) = sqrt(u^T u / m),
+ *   xin = u / s,  res = r / s   (FP32, m each, device),
+ * D = diag(A) as in fgmres_solve.  A: FP64 CSR (device); b, x: FP64 device vectors of
+ * length m, 16-byte aligned; xin, res: caller-owned FP32 outputs.  *rnorm (host, required)
+ * receives ||r||_2; reading it synchronises.  When r = 0 (s = 0) xin and res are zero.
+ * Uses context workspace (4 m doubles, grown on demand). */
+kc_status kc_cnn_residual_sample(kc_ctx* ctx, const kc_csr* A, const double* b,
+                                 const double* x, float* xin, float* res, double* rnorm);
 
 /* Restarted flexible GMRES(opts->restart) with flexible DCGS2 and a right preconditioner
  * chosen by opts->precond:

@@ -361,6 +361,15 @@ def kc_cnn_train_step_residual(ctx: Context, w32, adam_m, adam_v, t: int, lr: fl
     return loss.value
 
 
+def kc_cnn_residual_sample(ctx: Context, A: DeviceCSR, b, x, xin, res) -> float:
+    """r = b - A x, u = D^{-1} r, s = rms(u): writes xin = u / s and res = r / s (FP32,
+    device) and returns ||r||."""
+    rn = C.c_double()
+    ctx.check(ctx.lib.kc_cnn_residual_sample(ctx.handle, C.byref(A.c), _ptr(b), _ptr(x),
+                                             _ptr(xin), _ptr(res), C.byref(rn)))
+    return rn.value
+
+
 PREC_AUTO, PREC_JACOBI = 0, 1
 
 

@@ -97,6 +97,8 @@ _SIGS = {
     "kc_cnn_train_step_residual": ([_P, _P, _P, _P, C.c_int64, C.c_float, C.POINTER(kc_csr), _P,
                                     _P, C.c_int, C.c_int, C.c_int, _P, _P,
                                     C.POINTER(C.c_double)], C.c_int),
+    "kc_cnn_residual_sample": ([_P, C.POINTER(kc_csr), _P, _P, _P, _P, C.POINTER(C.c_double)],
+                               C.c_int),
     "fgmres_solve": ([_P, C.POINTER(kc_csr), _P, C.c_int, C.c_int, _P, _P,
                       C.POINTER(kc_gmres_opts), C.POINTER(kc_gmres_info)], C.c_int),
     "krylov_schur_eigs": ([_P, C.POINTER(kc_csr), _P, C.POINTER(kc_ks_opts),

@@ -314,7 +314,7 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
     ~Phase() { c->timing_phase = 0; }
   } phase(ctx);
   KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, nullptr, A->m, vec,
-                       EPI_STORE_C, sa));                                // C1 = Q^T w
+                       EPI_STORE_C1, sa));                               // C1 = Q^T w
   KC_TRY(launch_proj_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec,
                             sa));                  // u = w - Q C1, C2 = Q^T u in one pass
   KC_TRY(launch_gemv_sub(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, vec, 1));
@@ -448,7 +448,7 @@ kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, 
   }
   const int k = n - 1;                 // last column: CGS2 with an explicit norm
   sa.k = k;
-  KC_TRY(launch_reduce(ctx, Q, ldq, KC_F64, k, w, nullptr, m, KC_F64, EPI_STORE_C, sa));
+  KC_TRY(launch_reduce(ctx, Q, ldq, KC_F64, k, w, nullptr, m, KC_F64, EPI_STORE_C1, sa));
   KC_TRY(launch_gemv_sub(ctx, Q, ldq, KC_F64, k, w, m, KC_F64, 0));
   KC_TRY(launch_reduce(ctx, Q, ldq, KC_F64, k, w, nullptr, m, KC_F64, EPI_STORE_C2, sa));
   KC_TRY(launch_gemv_sub(ctx, Q, ldq, KC_F64, k, w, m, KC_F64, 1));

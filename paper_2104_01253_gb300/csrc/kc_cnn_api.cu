@@ -218,9 +218,10 @@ static int g1d(const kc_ctx* ctx, int64_t m) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-static kc_status host_norm64(kc_ctx* ctx, const double* x, int64_t m, double* out) {
+static kc_status host_norm64(kc_ctx* ctx, const double* x, int64_t m, double* out,
+                             int nepi = NEPI_INIT) {
   StepArgs sa = {};
-  kc_status s = launch_norm(ctx, x, nullptr, m, KC_F64, NEPI_INIT, sa);
+  kc_status s = launch_norm(ctx, x, nullptr, m, KC_F64, nepi, sa);
   if (s != KC_OK) return s;
   KC_CUDA(ctx, cudaMemcpyAsync(&ctx->scal_host->norm_sq, &ctx->scal->norm_sq, sizeof(double),
                                cudaMemcpyDeviceToHost, ctx->stream));
@@ -312,6 +313,45 @@ kc_status kc_cnn_train_step_residual(kc_ctx* ctx, float* w32, float* adam_m, flo
                                      double* loss) {
   if (ctx && !A) return fail(ctx, KC_ERR_INVALID_ARG, "NULL operator");
   return train_step(ctx, w32, adam_m, adam_v, t, lr, A, x, r, B, H, W, y, grad, loss);
+}
+
+kc_status kc_cnn_residual_sample(kc_ctx* ctx, const kc_csr* A, const double* b,
+                                 const double* x, float* xin, float* res, double* rnorm) {
+  if (!ctx) return KC_ERR_INVALID_ARG;
+  kc_status s = validate_csr_entries(ctx, A);
+  if (s != KC_OK) return s;
+  if (!b || !x || !xin || !res || !rnorm) return fail(ctx, KC_ERR_INVALID_ARG, "NULL argument");
+  if (A->val_dtype != KC_F64) return fail(ctx, KC_ERR_INVALID_ARG, "A must have FP64 values");
+  if (((uintptr_t)b & 15) || ((uintptr_t)x & 15))
+    return fail(ctx, KC_ERR_INVALID_ARG, "b and x must be 16-byte aligned");
+  const int64_t m = A->m;
+  const int64_t ld = (m + 31) / 32 * 32;
+  if ((s = ensure_workspace(ctx, 4 * (size_t)ld * 8)) != KC_OK) return s;
+  double* v = (double*)ctx->ws;
+  double* r = v + ld;
+  double* dinv = r + ld;
+  double* u = dinv + ld;
+  const int g = g1d(ctx, m);
+  if ((s = launch_spmv(ctx, A, x, v, KC_F64)) != KC_OK) return s;
+  timing_begin(ctx, KID_OTHER);
+  k_fgm_sub<<<g, 256, 0, ctx->stream>>>(b, v, r, m);
+  KC_LAUNCHED(ctx);
+  timing_begin(ctx, KID_OTHER);
+  k_fgm_dinv<<<g, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx, (const double*)A->val, dinv, m);
+  KC_LAUNCHED(ctx);
+  if ((s = host_norm64(ctx, r, m, rnorm, NEPI_SQ)) != KC_OK) return s;   // r = 0 is no error
+  // norm_sq = u^T u, then both outputs are divided by s = sqrt(norm_sq / m)
+  timing_begin(ctx, KID_OTHER);
+  k_fgm_jacobi_sq<<<g, 256, 0, ctx->stream>>>(r, dinv, u, m, ctx->partials, ctx->counters + 3,
+                                               ctx->scal);
+  KC_LAUNCHED(ctx);
+  timing_begin(ctx, KID_OTHER);
+  k_fgm_prep<<<g, 256, 0, ctx->stream>>>(u, xin, m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  timing_begin(ctx, KID_OTHER);
+  k_fgm_prep<<<g, 256, 0, ctx->stream>>>(r, res, m, ctx->scal);
+  KC_LAUNCHED(ctx);
+  return KC_OK;
 }
 
 kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, int W,
@@ -432,7 +472,7 @@ kc_status fgmres_solve(kc_ctx* ctx, const kc_csr* A, const float* w32, int H, in
       if ((s = launch_dcgs2_update(ctx, Q, ld, KC_F64, k, w, v, m, KC_F64)) != KC_OK) return s;
     }
     sa.k = n;
-    if ((s = launch_reduce(ctx, Q, ld, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C, sa)) != KC_OK) return s;
+    if ((s = launch_reduce(ctx, Q, ld, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C1, sa)) != KC_OK) return s;
     if ((s = launch_proj_reduce(ctx, Q, ld, KC_F64, n, w, m, KC_F64, sa)) != KC_OK) return s;
     if ((s = launch_gemv_sub(ctx, Q, ld, KC_F64, n, w, m, KC_F64, 1)) != KC_OK) return s;
     if ((s = launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_FINISH, sa)) != KC_OK) return s;

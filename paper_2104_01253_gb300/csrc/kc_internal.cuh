@@ -81,11 +81,14 @@ __device__ inline void givens_column(Scalars* sc, const double* H, int ldh, int 
 
 enum Epilogue : int {
   EPI_DCGS2 = 0,        // full DCGS2 scalar step (flexible variant: see flags)
-  EPI_STORE_C = 1,      // store Q^T x into C (finish first pass, CGS2 second projection)
+  EPI_STORE_C = 1,      // store Q^T x into C (CGS2 second projection), every product FP64
   EPI_STORE_C2 = 2,     // store Q^T x into C2
   EPI_STORE_S = 3,      // store Q^T x into S (CGS2 first projection)
   EPI_PARTIAL = 4,      // row-partitioned step: store the (k + 1) x NRHS sums to sa.part
   EPI_ICWY = 5,         // ICWY-MGS step (Section 6): norm, row of L, triangular solve
+  EPI_STORE_C1 = 6,     // store Q^T x into C as a first projection, whose error a second
+                        // projection removes: the offload reduction may sum it in
+                        // float-float (CGS2 finish first pass)
 };
 
 enum NormEpilogue : int {
@@ -94,6 +97,7 @@ enum NormEpilogue : int {
   NEPI_CGS2 = 2,        // CGS2 step: H(:,j) = S + C, H(j+1,j) = alpha
   NEPI_MGS = 3,         // MGS step: H(j+1,j) = alpha
   NEPI_DOT = 4,         // store x.y into h and H(i,j) (MGS inner product)
+  NEPI_SQ = 5,          // store x^T x into norm_sq only (a host-read norm, no state change)
 };
 
 struct StepArgs {
@@ -132,7 +136,9 @@ struct kc_ctx {
   int num_sms;
   int reduce_grid;
   int red_occ[4][33];      // resident CTAs per SM of the offload reduction, by (TPW, warps)
-  int red_pick[2][kc::NMAX][5]; // its task layout per size class (m >= 2^22) and k: nsplit, tasks per subset, TPW, warps, CTAs/SM
+  int red_pick[2][2][kc::NMAX + 1][6]; // its task layout per kernel (one / two vectors), size
+                                       // class (m >= 2^22) and task count: nsplit, tasks per
+                                       // subset, TPW, warps, CTAs/SM, row sub-blocks
   double* partials;        // PARTIAL_CTAS_PER_SM * num_sms * (2*NMAX + 4) doubles
   double* dots;            // the DCGS2 step's SpMV: per-CTA (w^T w, w^T v), 8 * num_sms pairs
   int dots_pending;        // CTAs whose pairs the next reduction of (dots_x, dots_y) takes

@@ -109,17 +109,57 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Column sums of an nrows x nval table (row c at base + c * stride) in a fixed order
+// (deterministic) into tot[0:nval], by every thread of the CTA (it synchronises; tot may
+// be read after a further __syncthreads).  The last CTA of a reduction runs this while
+// the other SMs idle, so it is arranged for memory-level parallelism: with fewer values
+// than warps, G = nw / nval warps share a value (each over every G-th group of 32 rows)
+// and their sums are added in warp order; otherwise each warp takes four values at a time,
+// so that a lane has four loads of each row in flight.
+__device__ void sum_rows(const double* __restrict__ base, int nrows, int stride, int nval,
+                         double* tot) {
+  __shared__ double gsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (nval > 0 && 2 * nval <= nw) {
+    const int G = nw / nval;
+    const int vi = warp % nval, gi = warp / nval;
+    double acc = 0.0;
+    if (gi < G) {
+#pragma unroll 8
+      for (int c = gi * 32 + lane; c < nrows; c += 32 * G)
+        acc += __ldcg(base + (int64_t)c * stride + vi);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) gsum[warp] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < nval) {
+      double t = 0.0;
+      for (int g = 0; g < G; g++) t += gsum[g * nval + threadIdx.x];
+      tot[threadIdx.x] = t;
+    }
+    return;
+  }
+  for (int v0 = warp; v0 < nval; v0 += 4 * nw) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+    for (int c = lane; c < nrows; c += 32) {
+      const double* p = base + (int64_t)c * stride;
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (v0 + u * nw < nval) acc[u] += __ldcg(p + v0 + u * nw);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const double t = warp_sum(acc[u]);
+      if (lane == 0 && v0 + u * nw < nval) tot[v0 + u * nw] = t;
+    }
+  }
+}
+
 // Sum the per-CTA partials in a fixed order (deterministic), into tot[0:nval].
 __device__ void sum_partials(const double* __restrict__ partials, int nparts, int nval,
                              double* tot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int vi = warp; vi < nval; vi += nw) {
-    double s = 0.0;
-#pragma unroll 8
-    for (int c = lane; c < nparts; c += 32) s += __ldcg(partials + (int64_t)c * PSTRIDE + vi);
-    s = warp_sum(s);
-    if (lane == 0) tot[vi] = s;
-  }
+  sum_rows(partials, nparts, PSTRIDE, nval, tot);
 }
 
 // Last-CTA election: returns true in every thread of the CTA that arrives last.
@@ -179,13 +219,23 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
     cn = warp_sum(cn);
     if (lane == 0 && alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
   }
-  for (int i = threadIdx.x; i <= k; i += blockDim.x) {
-    double hc = 0.0;
-    if (!(sa.flags & (SF_FLEXIBLE | SF_QR))) {
+  // K(i, k) = T_i - H(i, 0:k-1) C / alpha for i <= k: P lanes per row (aligned groups of a
+  // warp), each over every P-th column, added by a fixed xor tree, so that each thread has
+  // only k / P dependent-free loads of H to wait for
+  {
+    const int nt = (int)blockDim.x;
+    const int P = (k + 1) * 8 <= nt ? 8 : ((k + 1) * 4 <= nt ? 4 : ((k + 1) * 2 <= nt ? 2 : 1));
+    const bool corr = !(sa.flags & (SF_FLEXIBLE | SF_QR));
+    for (int base = 0; base <= k; base += nt / P) {          // uniform over the CTA
+      const int i = base + (int)threadIdx.x / P, sub = (int)threadIdx.x % P;
+      double hc = 0.0;
+      if (i <= k && corr) {
 #pragma unroll 4
-      for (int j = 0; j < k; j++) hc += sa.H[i + (int64_t)j * sa.ldh] * s_c[j];
+        for (int j = sub; j < k; j += P) hc += sa.H[i + (int64_t)j * sa.ldh] * s_c[j];
+      }
+      for (int o = P / 2; o > 0; o >>= 1) hc += __shfl_xor_sync(0xffffffffu, hc, o);
+      if (i <= k && sub == 0) sa.K[i + (int64_t)k * sa.ldk] = sc->T[i] - hc / alpha;
     }
-    sa.K[i + (int64_t)k * sa.ldk] = sc->T[i] - hc / alpha;
   }
   if (threadIdx.x == 0 && (sa.flags & SF_GIVENS) && k >= 1) {
     // Givens rotation of column k-1 on the staged copies (the column is s_h, stride 0)
@@ -357,7 +407,9 @@ __device__ void epilogue_from_tot(const double* tot, int k, int NRHS, Scalars* _
     return;
   }
   if (epilogue != EPI_DCGS2) {
-    double* dst = epilogue == EPI_STORE_C ? sc->C : (epilogue == EPI_STORE_C2 ? sc->C2 : sc->S);
+    double* dst = (epilogue == EPI_STORE_C || epilogue == EPI_STORE_C1)
+                      ? sc->C
+                      : (epilogue == EPI_STORE_C2 ? sc->C2 : sc->S);
     for (int i = threadIdx.x; i < k; i += blockDim.x) dst[i] = tot[i * NRHS];
     if (threadIdx.x == 0) {
       sc->norm_sq = tot[k * NRHS];
@@ -418,13 +470,8 @@ __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int 
   const int nval = (k + 1) * NRHS;
   sum_partials(partials, nparts < 0 ? (int)gridDim.x : nparts, dots ? 2 * k : nval, tot);
   if (dots) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwp = blockDim.x >> 5;
-    for (int which = warp; which < 2; which += nwp) {         // 0: beta, 1: s
-      double v = 0.0;
-      for (int c = lane; c < ndots; c += 32) v += __ldcg(dots + 2 * c + which);
-      v = warp_sum(v);
-      if (lane == 0) tot[2 * k + which] = v;
-    }
+    __syncthreads();                                           // sum_rows' scratch
+    sum_rows(dots, ndots, 2, 2, tot + 2 * k);                  // beta -> [2k], s -> [2k+1]
   }
   __syncthreads();
   epilogue_from_tot(tot, k, NRHS, sc, epilogue, sa);
@@ -824,20 +871,34 @@ __device__ __forceinline__ void f64x_load(const double* const (&ap)[TPW], int64_
     if (ap[i]) load_q(ap[i], g, av[i]);
 }
 
+// most warps of a row-split offload reduction CTA (rsub > 1); the task counts that take
+// the row split on long vectors, and the warps per CTA it aims at
+constexpr int F64X_RSUB_MAXW = 16;
+constexpr int F64X_RSUB_TASKS = 4;
+constexpr int F64X_RSUB_WARPS = 8;
+
 // Fused DCGS2 reduction, FP64 with offload (EPI_DCGS2 only).  The choice between the
 // float-float and the FP64 evaluation of S is made once per loop iteration,
 // warp-uniformly, around the whole iteration: a small per-column branch is turned into
 // predicated code by the compiler, and an FP64 FMA issued with every lane predicated off
 // still holds the FP64 pipe for its full issue time.  GR row groups per iteration (all
 // loads issued before any arithmetic).
+//
+// With rsub > 1 (few tasks on long vectors) the CTA's warps form rsub row sub-blocks of
+// nw / rsub task warps each: every sub-block walks its share of the CTA's rows with the
+// whole task set, so that more warps per SM have loads in flight, and the sub-blocks'
+// sums are added in shared memory in sub-block order before the CTA writes its partials.
 template <int TPW, int GR>
 __global__ void __launch_bounds__(1024)
 k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
               const double* __restrict__ y, int64_t m, double* __restrict__ partials,
               unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa,
-              int nsplit, int nt, int epi, const double* __restrict__ dots, int ndots) {
+              int nsplit, int nt, int epi, const double* __restrict__ dots, int ndots,
+              int rsub) {
   if (sc->stop) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5) / rsub;     // task warps per row sub-block
+  const int wt = warp % nw, rs = warp / nw;
   const int h = blockIdx.x % nsplit, r = blockIdx.x / nsplit, nr = gridDim.x / nsplit;
   const int tmax = ndots ? k : k + 2;             // tasks of this launch (columns first)
   int tk[TPW];
@@ -846,7 +907,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
   float sh[TPW], sl[TPW];
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
-    const int tl = warp + nw * i;                      // task within the subset
+    const int tl = wt + nw * i;                        // task within the subset
     tk[i] = tl < nt && h * nt + tl < tmax ? h * nt + tl : k + 2;   // k + 2: idle slot
     ap[i] = f64x_operand(Q, ldq, k, x, y, tk[i]);
     ac[i] = 0.0; as64[i] = 0.0; sh[i] = 0.0f; sl[i] = 0.0f;
@@ -855,8 +916,9 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
 #pragma unroll
   for (int i = 0; i < TPW; i++) busy |= ap[i] != nullptr;
   const int64_t ngroups = m / 2;
-  const int64_t g0 = (int64_t)r * ngroups / nr;
-  const int64_t g1 = busy ? (int64_t)(r + 1) * ngroups / nr : g0;
+  const int64_t b0 = (int64_t)r * ngroups / nr, b1 = (int64_t)(r + 1) * ngroups / nr;
+  const int64_t g0 = b0 + (b1 - b0) * rs / rsub;
+  const int64_t g1 = busy ? b0 + (b1 - b0) * (rs + 1) / rsub : g0;
   int64_t g = g0 + lane;
   if (GR == 2) {
     for (; g + 32 < g1; g += 64) {
@@ -887,7 +949,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
     else
       f64x_group<TPW, false>(tk, k, xa, ya, qa, ac, as64, sh, sl);
   }
-  if (r == nr - 1 && busy) {                     // ragged tail (m odd): FP64
+  if (r == nr - 1 && rs == 0 && busy) {          // ragged tail (m odd): FP64
     for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
       const double xs = __ldcg(x + row), ys1 = __ldcg(y + row);
 #pragma unroll
@@ -899,27 +961,84 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
       }
     }
   }
+  __shared__ double red[F64X_RSUB_MAXW][TPW][2];  // sub-block sums (rsub > 1)
+  double cv[TPW], svv[TPW];
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
-    const int t = tk[i];
-    if (t > k + 1) continue;
-    const double c = warp_sum(ac[i]);
-    const double sv = warp_sum(as64[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])));
-    if (lane == 0) {
-      double* pp = partials + (int64_t)r * PSTRIDE;  // row block r: one writer per task
-      if (t < k) { pp[2 * t] = c; pp[2 * t + 1] = sv; }
-      else pp[2 * k + (t - k)] = c;           // beta -> [2k], s -> [2k + 1]
+    cv[i] = warp_sum(ac[i]);
+    svv[i] = warp_sum(as64[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])));
+  }
+  if (rsub > 1) {
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < TPW; i++) { red[warp][i][0] = cv[i]; red[warp][i][1] = svv[i]; }
+    __syncthreads();
+    if (rs == 0)
+#pragma unroll
+      for (int i = 0; i < TPW; i++) {
+        double c = red[wt][i][0], sv = red[wt][i][1];
+        for (int q = 1; q < rsub; q++) { c += red[q * nw + wt][i][0]; sv += red[q * nw + wt][i][1]; }
+        cv[i] = c;
+        svv[i] = sv;
+      }
+  }
+  if (rs == 0 && lane == 0) {
+    double* pp = partials + (int64_t)r * PSTRIDE;    // row block r: one writer per task
+#pragma unroll
+    for (int i = 0; i < TPW; i++) {
+      const int t = tk[i];
+      if (t > k + 1) continue;
+      if (t < k) { pp[2 * t] = cv[i]; pp[2 * t + 1] = svv[i]; }
+      else pp[2 * k + (t - k)] = cv[i];       // beta -> [2k], s -> [2k + 1]
     }
   }
   if (!last_cta(counter)) return;
   reduce_epilogue(partials, k, 2, sc, epi, sa, nr, dots, ndots);
 }
 
+// One group of two rows of the one-vector reduction for every slot: ac += a . x in FP64,
+// or for a column with OFF, (sh, sl) += a . x in float-float.
+template <int TPW, bool OFF>
+__device__ __forceinline__ void r1_group(const int (&tk)[TPW], int k, const double (&xv)[2],
+                                         const double (&av)[TPW][2], double* ac, float* sh,
+                                         float* sl) {
+  float xh[2], xl[2];
+  if (OFF) { split_fast(xv[0], xh[0], xl[0]); split_fast(xv[1], xh[1], xl[1]); }
+#pragma unroll
+  for (int i = 0; i < TPW; i++) {
+    if (tk[i] > k) continue;                     // idle slot (warp-uniform)
+    if (OFF && tk[i] < k) {
+      float ah[2], al[2];
+      split_fast(av[i][0], ah[0], al[0]);
+      split_fast(av[i][1], ah[1], al[1]);
+      df_mac(sh[i], sl[i], ah[0], al[0], xh[0], xl[0]);
+      df_mac(sh[i], sl[i], ah[1], al[1], xh[1], xl[1]);
+    } else {
+      ac[i] = fma(av[i][0], xv[0], ac[i]);
+      ac[i] = fma(av[i][1], xv[1], ac[i]);
+    }
+  }
+}
+
+// true when x and every column operand of the group lie in split_fast's range
+template <int TPW>
+__device__ __forceinline__ bool r1_in_range(const int (&tk)[TPW], int k, const double (&xv)[2],
+                                            const double (&av)[TPW][2]) {
+  bool ok = split_fast_ok(xv[0]) & split_fast_ok(xv[1]);
+#pragma unroll
+  for (int i = 0; i < TPW; i++)
+    if (tk[i] < k) ok = ok & split_fast_ok(av[i][0]) & split_fast_ok(av[i][1]);
+  return ok;
+}
+
 // Q_k^T x and x^T x (one vector: the CGS2 finish's projections) with the offload
-// reduction's task layout: tasks t < k are columns, task k is x^T x, every product in FP64
-// (one FMA per basis element, no float-float part); GR row groups per iteration with all
-// loads first.  Partials hold the k + 1 sums of each row block in task order.
-template <int TPW, int GR>
+// reduction's task layout: tasks t < k are columns, task k is x^T x; GR row groups per
+// iteration with all loads first.  Partials hold the k + 1 sums of each row block in task
+// order.  With OFF (the first projection, C1 = Q^T w, whose error the second projection
+// removes, as for S in the DCGS2 step) the columns are summed in float-float on the
+// FP32/INT pipes (warp-uniformly per iteration, FP64 for operands outside the range);
+// otherwise, and always for x^T x, every product is an FP64 FMA.
+template <int TPW, int GR, bool OFF>
 __global__ void __launch_bounds__(1024)
 k_reduce1_f64(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
               int64_t m, double* __restrict__ partials, unsigned int* __restrict__ counter,
@@ -930,12 +1049,16 @@ k_reduce1_f64(const double* __restrict__ Q, int64_t ldq, int k, const double* __
   const double* ap[TPW];
   int tk[TPW];
   double ac[TPW];
+  float sh[TPW], sl[TPW];
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
     const int tl = warp + nw * i;
     tk[i] = tl < nt ? h * nt + tl : k + 1;             // k + 1 and above: idle slot
+    if (tk[i] > k) tk[i] = k + 1;
     ap[i] = tk[i] < k ? Q + (int64_t)tk[i] * ldq : (tk[i] == k ? x : nullptr);
     ac[i] = 0.0;
+    sh[i] = 0.0f;
+    sl[i] = 0.0f;
   }
   const int64_t ngroups = m / 2;
   const int64_t g0 = (int64_t)r * ngroups / nr;
@@ -949,13 +1072,13 @@ k_reduce1_f64(const double* __restrict__ Q, int64_t ldq, int k, const double* __
 #pragma unroll
       for (int i = 0; i < TPW; i++)
         if (ap[i]) { load_q(ap[i], g, qa[i]); load_q(ap[i], g + 32, qb[i]); }
-#pragma unroll
-      for (int i = 0; i < TPW; i++) {
-        if (!ap[i]) continue;                        // idle slot (warp-uniform)
-        ac[i] = fma(qa[i][0], xa[0], ac[i]);
-        ac[i] = fma(qa[i][1], xa[1], ac[i]);
-        ac[i] = fma(qb[i][0], xb[0], ac[i]);
-        ac[i] = fma(qb[i][1], xb[1], ac[i]);
+      if (OFF && __builtin_expect(__all_sync(__activemask(), r1_in_range<TPW>(tk, k, xa, qa) &
+                                                             r1_in_range<TPW>(tk, k, xb, qb)), 1)) {
+        r1_group<TPW, OFF>(tk, k, xa, qa, ac, sh, sl);
+        r1_group<TPW, OFF>(tk, k, xb, qb, ac, sh, sl);
+      } else {
+        r1_group<TPW, false>(tk, k, xa, qa, ac, sh, sl);
+        r1_group<TPW, false>(tk, k, xb, qb, ac, sh, sl);
       }
     }
   }
@@ -965,12 +1088,10 @@ k_reduce1_f64(const double* __restrict__ Q, int64_t ldq, int k, const double* __
 #pragma unroll
     for (int i = 0; i < TPW; i++)
       if (ap[i]) load_q(ap[i], g, qa[i]);
-#pragma unroll
-    for (int i = 0; i < TPW; i++) {
-      if (!ap[i]) continue;
-      ac[i] = fma(qa[i][0], xa[0], ac[i]);
-      ac[i] = fma(qa[i][1], xa[1], ac[i]);
-    }
+    if (OFF && __builtin_expect(__all_sync(__activemask(), r1_in_range<TPW>(tk, k, xa, qa)), 1))
+      r1_group<TPW, OFF>(tk, k, xa, qa, ac, sh, sl);
+    else
+      r1_group<TPW, false>(tk, k, xa, qa, ac, sh, sl);
   }
   if (r == nr - 1) {                             // ragged tail (m odd)
     for (int64_t row = ngroups * 2 + lane; row < m; row += 32) {
@@ -983,7 +1104,7 @@ k_reduce1_f64(const double* __restrict__ Q, int64_t ldq, int k, const double* __
 #pragma unroll
   for (int i = 0; i < TPW; i++) {
     if (!ap[i]) continue;
-    const double c = warp_sum(ac[i]);
+    const double c = warp_sum(OFF ? ac[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])) : ac[i]);
     if (lane == 0) partials[(int64_t)r * PSTRIDE + tk[i]] = c;
   }
   if (!last_cta(counter)) return;
@@ -1165,17 +1286,101 @@ __device__ __forceinline__ void f64x_update_pair(const double (&q)[2][2], const 
   }
 }
 
+// below this many basis columns the fast update takes two row groups per thread
+constexpr int UPD_PAIR_K = 64;
+
+// FP32 ("fast") products of the offloaded update for NG row groups gg: w <- v/alpha - Q T
+// - q T_k in FP64 and q = w / alpha - (Q C) / alpha with the FP32 products, in chunks of CH
+// columns whose loads are all issued before their arithmetic; the last, partial chunk is
+// predicated so that its loads are in flight together too.  z = Q (C / scale) in FP32 is
+// scaled by cf = scale / alpha in FP32 as well, so that q takes one FP64 FMA per row.
+template <int NG, int CH>
+__device__ __forceinline__ void upd_fast_rows(const double* __restrict__ Q, int64_t ldq, int k,
+                                              double* __restrict__ w,
+                                              const double* __restrict__ v,
+                                              double* __restrict__ qk, const int64_t (&gg)[NG],
+                                              const double* sT, const float* cH, double vsc,
+                                              double inva, float cf) {
+  double wv[NG][2], wn[NG][2];
+  float z[NG][2];
+#pragma unroll
+  for (int n = 0; n < NG; n++) {
+    double vv[2];
+    ldv_cg(w, gg[n], wv[n]);
+    ldv_cg(v, gg[n], vv);
+    wn[n][0] = vv[0] * vsc;
+    wn[n][1] = vv[1] * vsc;
+    z[n][0] = 0.0f;
+    z[n][1] = 0.0f;
+  }
+  int i = 0;
+  for (; i + CH <= k; i += CH) {
+    double q[CH][NG][2];
+#pragma unroll
+    for (int j = 0; j < CH; j++)
+#pragma unroll
+      for (int n = 0; n < NG; n++) load_q(Q + (int64_t)(i + j) * ldq, gg[n], q[j][n]);
+#pragma unroll
+    for (int j = 0; j < CH; j++)
+#pragma unroll
+      for (int n = 0; n < NG; n++)
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+          wn[n][r] = fma(-q[j][n][r], sT[i + j], wn[n][r]);
+          z[n][r] = fmaf(d2f_trunc(q[j][n][r]), cH[i + j], z[n][r]);
+        }
+  }
+  if (i < k) {
+    double q[CH][NG][2];
+#pragma unroll
+    for (int j = 0; j < CH; j++)
+#pragma unroll
+      for (int n = 0; n < NG; n++) {
+        if (i + j < k) {
+          load_q(Q + (int64_t)(i + j) * ldq, gg[n], q[j][n]);
+        } else {
+          q[j][n][0] = 0.0;
+          q[j][n][1] = 0.0;
+        }
+      }
+#pragma unroll
+    for (int j = 0; j < CH; j++) {
+      if (i + j < k) {
+#pragma unroll
+        for (int n = 0; n < NG; n++)
+#pragma unroll
+          for (int r = 0; r < 2; r++) {
+            wn[n][r] = fma(-q[j][n][r], sT[i + j], wn[n][r]);
+            z[n][r] = fmaf(d2f_trunc(q[j][n][r]), cH[i + j], z[n][r]);
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < NG; n++) {
+    double qn[2], wo[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+      qn[r] = fma(wv[n][r], inva, -f2d_bits(z[n][r] * cf));
+      wo[r] = fma(-qn[r], sT[k], wn[n][r]);
+    }
+    store_q(qk, gg[n], qn);
+    stv(w, gg[n], wo);
+  }
+}
+
 // DCGS2 update, FP64 with offload: u = w - Q C with C scaled by a power of two into float
 // range, w <- v/alpha - Q T - q T_k in FP64.  Q C is small against w (C holds the delayed
 // reorthogonalisation coefficients), so it needs far fewer correct digits than the FP64
-// terms: in FP32 (basis entries truncated to 24 bits, k-term FP32 sums) its error per row
-// is at most (k + 3) 2^-24 sum_j |q_j| |C_j|, whose 2-norm is at most (k + 3) 2^-24 ||C||_1;
-// when that is below 2^-53 alpha (= 2^-53 ||w - Q C||, the FP64 rounding of w itself) the
+// terms: in FP32 (basis entries truncated to 24 bits, k-term FP32 sums, the product by
+// scale / alpha) its error per row of q is at most (k + 4) 2^-24 sum_j |q_j| |C_j| / alpha,
+// whose 2-norm is at most (k + 4) 2^-24 ||C||_1 / alpha; when that is below 2^-53 (the FP64
+// rounding of the unit vector q itself; alpha = ||w - Q C||) the
 // launch takes the FP32 products ("fast"), otherwise float-float (split doubles, exact
 // leading products), and FP64 for operands outside the float-float range (warp-uniform
 // per pair of columns, see k_reduce_f64x).  The choice is made per launch from the device
 // scalars, identically in every CTA.
-__global__ void __launch_bounds__(UPD_THREADS)
+__global__ void __launch_bounds__(UPD_THREADS, 4)
 k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__ w,
                     const double* __restrict__ v, int64_t m, const Scalars* __restrict__ sc,
                     int allow32) {
@@ -1183,6 +1388,7 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
   __shared__ double sC[NMAX + 1], sT[NMAX + 1];
   __shared__ float cH[NMAX + 1], cL[NMAX + 1];
   __shared__ double s_scale;
+  __shared__ float s_cf;
   __shared__ int s_cok, s_fast;
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
     sC[i] = i < k ? sc->C[i] : 0.0;            // sC[k] = 0 pads an odd k to a column pair
@@ -1199,8 +1405,13 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
     if (cmax > 0.0) frexp(cmax, &ex);
     s_scale = ldexp(1.0, ex);                 // C / scale lies in (-1, 1)
     s_cok = 1;
-    // 0x1p-29 = 2^-53 / 2^-24; l1 is FP64 (relative error far below the bound's margin)
-    s_fast = (allow32 && l1 * (double)(k + 3) <= 0x1p-29 * sc->alpha) ? 1 : 0;
+    // 0x1p-29 = 2^-53 / 2^-24; l1 is FP64 (relative error far below the bound's margin);
+    // the FP32 factor scale / alpha must be a normal float small enough that z cf (|z| <= k)
+    // stays finite
+    const double cf = s_scale * sc->inv_alpha;
+    s_cf = (float)cf;
+    s_fast = (allow32 && l1 * (double)(k + 4) <= 0x1p-29 * sc->alpha && fabs(cf) >= 0x1p-120 &&
+              fabs(cf) <= 0x1p100) ? 1 : 0;
   }
   __syncthreads();
   const double inv_scale = 1.0 / s_scale;     // exact: a power of two
@@ -1217,45 +1428,22 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
   const int64_t ngroups = m / 2;
   if (s_fast && cok) {
     // cH holds C / scale truncated to 24 bits (the leading float of its split); with the
-    // truncated basis entries that is 2 x 2^-23 of each product, and the FP32 sum adds at
-    // most (k - 1) 2^-24: together the (k + 3) 2^-24 of the bound above
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
-         g += (int64_t)gridDim.x * blockDim.x) {
-      double wv[2], vv[2];
-      ldv_cg(w, g, wv);
-      ldv_cg(v, g, vv);
-      double wn[2] = {vv[0] * vsc, vv[1] * vsc};
-      float z[2] = {0.0f, 0.0f};
-      int i = 0;
-      for (; i + 8 <= k; i += 8) {      // eight columns' loads in flight before arithmetic
-        double q[8][2];
-#pragma unroll
-        for (int j = 0; j < 8; j++) load_q(Q + (int64_t)(i + j) * ldq, g, q[j]);
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-          wn[0] = fma(-q[j][0], sT[i + j], wn[0]);
-          wn[1] = fma(-q[j][1], sT[i + j], wn[1]);
-          z[0] = fmaf(d2f_trunc(q[j][0]), cH[i + j], z[0]);
-          z[1] = fmaf(d2f_trunc(q[j][1]), cH[i + j], z[1]);
-        }
+    // truncated basis entries that is 2 x 2^-23 of each product, the FP32 sum adds at most
+    // (k - 1) 2^-24, and cf and the product z cf two more roundings of 2^-24: together the
+    // (k + 4) 2^-24 of the bound above (relative to sum_j |q_j| |C_j| / alpha)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < UPD_PAIR_K) {
+      // few columns: the pass is HBM-latency bound, so each thread takes two row groups
+      // a grid stride apart and issues all their loads before the arithmetic
+      for (; g + stride < ngroups; g += 2 * stride) {
+        const int64_t gg[2] = {g, g + stride};
+        upd_fast_rows<2, 4>(Q, ldq, k, w, v, qk, gg, sT, cH, vsc, inva, s_cf);
       }
-      for (; i < k; i++) {
-        double q[2];
-        load_q(Q + (int64_t)i * ldq, g, q);
-        wn[0] = fma(-q[0], sT[i], wn[0]);
-        wn[1] = fma(-q[1], sT[i], wn[1]);
-        z[0] = fmaf(d2f_trunc(q[0]), cH[i], z[0]);
-        z[1] = fmaf(d2f_trunc(q[1]), cH[i], z[1]);
-      }
-      double qn[2], wo[2];
-#pragma unroll
-      for (int r = 0; r < 2; r++) {
-        const double u = fma(-f2d_bits(z[r]), scale, wv[r]);
-        qn[r] = u * inva;
-        wo[r] = fma(-qn[r], sT[k], wn[r]);
-      }
-      store_q(qk, g, qn);
-      stv(w, g, wo);
+    }
+    for (; g < ngroups; g += stride) {
+      const int64_t gg[1] = {g};
+      upd_fast_rows<1, 8>(Q, ldq, k, w, v, qk, gg, sT, cH, vsc, inva, s_cf);
     }
   } else
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
@@ -1414,6 +1602,7 @@ __device__ void norm_epilogue(double xx, double xy, Scalars* __restrict__ sc, in
   const int k = sa.k;
   sc->norm_sq = xx;
   if (!isfinite(xx) || !isfinite(xy)) set_status(sc, KC_ERR_NONFINITE);
+  if (nepi == NEPI_SQ) return;
   if (nepi == NEPI_DOT) {
     sc->h = xy;
     sa.H[sa.row + (int64_t)(k - 1) * sa.ldh] = xy;       // H(i, k-1), i = sa.row
@@ -1658,10 +1847,12 @@ static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int
 // taken from the measurements instead: 33-36 tasks run fastest as two subsets of two
 // slots (5% at both sizes), and up to 16 tasks as one subset of two slots on long
 // vectors (up to 14%) but of one slot on short ones.
-static void f64x_layout(kc_ctx* ctx, int ntask, int big, int& nsplit, int& nt, int& tpw,
-                        int& nw, int& occ) {
+// With `split_rows` (the two-vector kernel only), up to F64X_RSUB_TASKS tasks on long
+// vectors run as one slot per warp in CTAs of rsub row sub-blocks (about eight warps).
+static void f64x_layout(kc_ctx* ctx, int ntask, int big, bool split_rows, int& nsplit,
+                        int& nt, int& tpw, int& nw, int& occ, int& rsub) {
   {
-      int* pick = ctx->red_pick[big][ntask - 2];
+      int* pick = ctx->red_pick[split_rows ? 1 : 0][big][ntask - 1];
       if (pick[0] == 0) {
         auto occ_of = [&](int tp, int nww) {
           int& o = ctx->red_occ[tp - 1][nww];
@@ -1680,8 +1871,13 @@ static void f64x_layout(kc_ctx* ctx, int ntask, int big, int& nsplit, int& nt, i
           const int ntt = (ntask + ns - 1) / ns;
           const int nww = (ntt + tp - 1) / tp;
           pick[0] = ns; pick[1] = ntt; pick[2] = tp; pick[3] = nww; pick[4] = occ_of(tp, nww);
+          pick[5] = 1;
         };
-        if (ntask >= 33 && ntask <= 36) {
+        if (split_rows && big && ntask <= F64X_RSUB_TASKS) {
+          const int rs = F64X_RSUB_WARPS / ntask > 1 ? F64X_RSUB_WARPS / ntask : 1;
+          pick[0] = 1; pick[1] = ntask; pick[2] = 1; pick[3] = ntask * rs;
+          pick[4] = occ_of(1, ntask * rs); pick[5] = rs;
+        } else if (ntask >= 33 && ntask <= 36) {
           take(2, 2);
         } else if (ntask <= 16) {
           take(1, big && ntask >= 5 ? 2 : 1);
@@ -1706,6 +1902,7 @@ static void f64x_layout(kc_ctx* ctx, int ntask, int big, int& nsplit, int& nt, i
         }
       }
       nsplit = pick[0]; nt = pick[1]; tpw = pick[2]; nw = pick[3]; occ = pick[4];
+      rsub = pick[5];
     }
 }
 
@@ -1739,8 +1936,11 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
              (epilogue == EPI_DCGS2 || epilogue == EPI_PARTIAL) && ctx->fp64_mode >= 1) {
     // with beta and s from the SpMV the step's tasks are its k columns only
     const int ntask = ndots ? k : k + 2;
-    int nsplit, nt, tpw, nw, occ;
-    f64x_layout(ctx, ntask < 2 ? 2 : ntask, m >= ((int64_t)1 << 22), nsplit, nt, tpw, nw, occ);
+    int nsplit, nt, tpw, nw, occ, rsub;
+    const bool big = m >= ((int64_t)1 << 22);
+    // (one task on short vectors: a two-warp CTA as for two tasks, one warp idle)
+    f64x_layout(ctx, ntask < 1 ? 1 : (ntask < 2 && !big ? 2 : ntask), big, true, nsplit, nt,
+                tpw, nw, occ, rsub);
     int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);            // row blocks: >= 4 groups/lane
     int64_t nr = ((int64_t)ctx->num_sms * occ + nsplit - 1) / nsplit;
     if (nr > gcap) nr = gcap < 1 ? 1 : gcap;
@@ -1750,23 +1950,25 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
       nt = 0;
       nw = 1;
       tpw = 1;
+      rsub = 1;
     }
     const int g = (int)(nr * nsplit);
     auto go = [&](auto kern) {
       kern<<<g, 32 * nw, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
                                            (const double*)y, m, ctx->partials, ctx->counters,
                                            ctx->scal, sa, nsplit, nt, epilogue,
-                                           ndots ? ctx->dots : nullptr, ndots);
+                                           ndots ? ctx->dots : nullptr, ndots, rsub);
     };
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
     else if (tpw == 2) go(k_reduce_f64x<2, 2>);
     else go(k_reduce_f64x<3, 1>);
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && !two && k >= 1 &&
-             (epilogue == EPI_STORE_C || epilogue == EPI_STORE_C2 || epilogue == EPI_PARTIAL) &&
+             (epilogue == EPI_STORE_C || epilogue == EPI_STORE_C1 || epilogue == EPI_STORE_C2 ||
+              epilogue == EPI_PARTIAL) &&
              ctx->fp64_mode >= 1) {
     // one vector (the CGS2 finish): the offload layout for k + 1 FP64 tasks
-    int nsplit, nt, tpw, nw, occ;
-    f64x_layout(ctx, k + 1, m >= ((int64_t)1 << 22), nsplit, nt, tpw, nw, occ);
+    int nsplit, nt, tpw, nw, occ, rsub;
+    f64x_layout(ctx, k + 1, m >= ((int64_t)1 << 22), false, nsplit, nt, tpw, nw, occ, rsub);
     int64_t gcap = (m / 2 + 32 * 4 - 1) / (32 * 4);
     int64_t nr = ((int64_t)ctx->num_sms * occ + nsplit - 1) / nsplit;
     if (nr > gcap) nr = gcap < 1 ? 1 : gcap;
@@ -1776,9 +1978,17 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
                                            ctx->partials, ctx->counters, ctx->scal, sa, nsplit,
                                            nt, epilogue);
     };
-    if (tpw == 1) go(k_reduce1_f64<1, 2>);
-    else if (tpw == 2) go(k_reduce1_f64<2, 2>);
-    else go(k_reduce1_f64<3, 2>);
+    // the finish's first projection in float-float (the second one corrects it)
+    const bool off = epilogue == EPI_STORE_C1 && !(ctx->staged & 4);
+    if (off) {
+      if (tpw == 1) go(k_reduce1_f64<1, 2, true>);
+      else if (tpw == 2) go(k_reduce1_f64<2, 2, true>);
+      else go(k_reduce1_f64<3, 2, true>);
+    } else {
+      if (tpw == 1) go(k_reduce1_f64<1, 2, false>);
+      else if (tpw == 2) go(k_reduce1_f64<2, 2, false>);
+      else go(k_reduce1_f64<3, 2, false>);
+    }
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
     if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
     else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);

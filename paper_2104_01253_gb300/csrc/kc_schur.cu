@@ -704,7 +704,7 @@ extern "C" kc_status krylov_schur_eigs(kc_ctx* ctx, const kc_csr* A, const doubl
       mv++;
     }
     sa.k = n;
-    if ((s = launch_reduce(ctx, Qa, ldq, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C, sa)) != KC_OK) return s;
+    if ((s = launch_reduce(ctx, Qa, ldq, KC_F64, n, w, nullptr, m, KC_F64, EPI_STORE_C1, sa)) != KC_OK) return s;
     if ((s = launch_proj_reduce(ctx, Qa, ldq, KC_F64, n, w, m, KC_F64, sa)) != KC_OK) return s;
     if ((s = launch_gemv_sub(ctx, Qa, ldq, KC_F64, n, w, m, KC_F64, 1)) != KC_OK) return s;
     if ((s = launch_norm(ctx, w, nullptr, m, KC_F64, NEPI_FINISH, sa)) != KC_OK) return s;

@@ -165,7 +165,7 @@ static kc_status gmres_cycle(kc_ctx* ctx, const kc_csr* A, const Cycle& c, void*
     if ((s = launch_dcgs2_update(ctx, c.Q, c.ldq, c.qdt, k, c.w, c.v, m, c.vec)) != KC_OK) return s;
   }
   sa.k = c.n;
-  if ((s = launch_reduce(ctx, c.Q, c.ldq, c.qdt, c.n, c.w, nullptr, m, c.vec, EPI_STORE_C, sa)) != KC_OK) return s;
+  if ((s = launch_reduce(ctx, c.Q, c.ldq, c.qdt, c.n, c.w, nullptr, m, c.vec, EPI_STORE_C1, sa)) != KC_OK) return s;
   if ((s = launch_proj_reduce(ctx, c.Q, c.ldq, c.qdt, c.n, c.w, m, c.vec, sa)) != KC_OK) return s;
   if ((s = launch_gemv_sub(ctx, c.Q, c.ldq, c.qdt, c.n, c.w, m, c.vec, 1)) != KC_OK) return s;
   if ((s = launch_norm(ctx, c.w, nullptr, m, c.vec, NEPI_FINISH, sa)) != KC_OK) return s;

@@ -10,7 +10,8 @@ correction e_j = A^{-1} r_j left implicit: the residual loss
 is ||A (M(r_b) - e_b)||^2 / ||r_b||^2 for the preconditioner M that fgmres_solve applies
 (M(w) = D^{-1} w + s net(D^{-1} w / s)), so it needs r_b and A only.  Inputs and residuals
 of a sample are divided by s = rms(D^{-1} r_b) (the network is positively homogeneous).
-Every forward, backward and Adam update runs in libkrylov (kc_cnn_train_step_residual);
+The residual, its Jacobi scaling and s come from libkrylov (kc_cnn_residual_sample), and
+every forward, backward and Adam update runs there too (kc_cnn_train_step_residual);
 each step draws its batch from one operator, cycling through the training operators.
 """
 from __future__ import annotations
@@ -18,22 +19,14 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (Context, DeviceCSR, gmres_solve, kc_cnn_param_count,
-               kc_cnn_train_step_residual, kc_spmv)
+from . import (Context, DeviceCSR, gmres_solve, kc_cnn_param_count, kc_cnn_residual_sample,
+               kc_cnn_train_step_residual)
 
 
 def varcoef_operator(N: int, seed: int):
     from synth import convdiff_csr, varcoef_fields_2d
     kappa, wind = varcoef_fields_2d(N, seed)
     return convdiff_csr(N, 2, wind, kappa=kappa)
-
-
-def inverse_diagonal(Ah) -> np.ndarray:
-    """1 / a_ii of a host CSR (1 where the diagonal entry is missing or zero)."""
-    d = np.asarray(Ah.to_scipy().diagonal(), dtype=np.float64)
-    out = np.ones(Ah.m)
-    out[d != 0.0] = 1.0 / d[d != 0.0]
-    return out
 
 
 def he_init(seed: int) -> np.ndarray:
@@ -62,19 +55,18 @@ def generate_pairs(ctx: Context, N: int, seeds, restart: int = 40, max_cycles: i
         Ah = host_ops[oi] if host_ops is not None else varcoef_operator(N, seed)
         A = DeviceCSR(Ah)
         ops.append(A)
-        dinv = torch.as_tensor(inverse_diagonal(Ah), device="cuda")
         b = torch.as_tensor(gaussian_vector(Ah.m, rhs_seed_offset + seed), device="cuda")
         x = torch.zeros_like(b)
-        Ax = torch.empty_like(b)
+        xin = torch.empty(Ah.m, dtype=torch.float32, device="cuda")
+        res = torch.empty_like(xin)
+        bnorm = None
         for _ in range(max_cycles):
-            kc_spmv(ctx, A, x, Ax)
-            r = b - Ax
-            if float(torch.linalg.vector_norm(r)) <= 1e-9 * float(torch.linalg.vector_norm(b)):
+            rn = kc_cnn_residual_sample(ctx, A, b, x, xin, res)
+            bnorm = rn if bnorm is None else bnorm           # x = 0 on the first pass
+            if rn <= 1e-9 * bnorm:
                 break
-            u = r * dinv
-            s = torch.sqrt(torch.mean(u * u))
-            X.append((u / s).float().cpu().numpy())
-            R.append((r / s).float().cpu().numpy())
+            X.append(xin.cpu().numpy())
+            R.append(res.cpu().numpy())
             owner.append(oi)
             gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10, maxit=restart)
     X = np.stack(X).reshape(-1, 1, N, N)

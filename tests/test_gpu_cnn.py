@@ -315,6 +315,37 @@ def near_identity_weights(seed, eps=0.02):
     return ws
 
 
+@pytest.mark.parametrize("N", [2, 33, 100])
+def test_residual_sample_matches_oracle(kc, ctx, N):
+    """kc_cnn_residual_sample: r = b - A x, u = D^{-1} r (oracle.cnn.inverse_diagonal),
+    s = rms(u), inputs u / s and residuals r / s in FP32 (one FP32 rounding each, so
+    2^-24 relative per element, plus the FP64 arithmetic's few units in the last place);
+    ||r|| to 1e-13; r = 0 gives zeros."""
+    Ah = _varcoef(N, 61)
+    As = Ah.to_scipy()
+    b = gaussian_vector(Ah.m, 71)
+    x = gaussian_vector(Ah.m, 72) * 0.1
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(b, device="cuda")
+    xd = torch.as_tensor(x, device="cuda")
+    xin = torch.empty(Ah.m, dtype=torch.float32, device="cuda")
+    res = torch.empty_like(xin)
+    rn = kc.kc_cnn_residual_sample(ctx, A, bd, xd, xin, res)
+    r = b - As @ x
+    u = r * cnn.inverse_diagonal(As)
+    s = np.sqrt(np.mean(u * u))
+    assert abs(rn - np.linalg.norm(r)) <= 1e-13 * np.linalg.norm(r)
+    for got, want in ((xin, u / s), (res, r / s)):
+        g = got.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(g - want) <= 2.0 ** -23 * np.abs(want) + 1e-14 * np.abs(want).max())
+    # x solves A x = b exactly when b = A x: r = 0, outputs zero
+    bd0 = torch.as_tensor(As @ np.zeros(Ah.m), device="cuda")
+    x0 = torch.zeros_like(bd0)
+    assert kc.kc_cnn_residual_sample(ctx, A, bd0, x0, xin, res) == 0.0
+    assert not xin.any() and not res.any()
+    assert ctx.read_status() == 0
+
+
 def test_fgmres_jacobi_matches_oracle(kc, ctx):
     Ah = _varcoef(32, 66)
     b = gaussian_vector(Ah.m, 73)
