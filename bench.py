@@ -118,10 +118,12 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
     launch time.  Reduction at step k: bytes 8 m k + 16 m (Q_k, w, v); FP64-pipe FMAs
     m k f (+ 2 m for beta and s in the all-FP64 mode; with offload the SpMV forms them) with
     f = 1 with offload, 2 all-FP64, against the method's 2 m k + 2 m.  Update:
-    bytes 8 m k + 32 m; FP64-pipe FMAs m k f + 5 m (offload; all-FP64 2 m k + 3 m) against
-    2 m k + 3 m.  SpMV: 4 (m + 1) + 12 nnz + 16 m bytes, nnz + 2 m FMAs (the matvec, beta and
-    s).  The CGS2 finish (k = n): the first projection's sums (8 m k + 8 m bytes) and the fused
-    u = w - Q C1 with the second projection's sums (8 m k + 16 m bytes), m k + m FMAs each.  In FP64 mode 2
+    bytes 8 m k + 32 m; FP64-pipe operations m k f + 3 m (v / alpha, q and w' per row)
+    against 2 m k + 3 m.  SpMV: 4 (m + 1) + 12 nnz + 16 m bytes, nnz + 2 m FMAs (the matvec,
+    beta and s).  The CGS2 finish (k = n): the first projection's sums (8 m k + 8 m bytes;
+    with offload its column sums are float-float, so m FP64 FMAs for x^T x, else m k + m) and
+    the fused u = w - Q C1 with the second projection's sums (8 m k + 16 m bytes, m k + m
+    FMAs).  In FP64 mode 2
     the reduction's products are exact integer digit products on the tensor cores (no FP64
     FMA per element)."""
     f = 2 if fp64_mode == 0 else 1
@@ -132,11 +134,12 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
                    sum(m * k * fr + bs * m for k in range(n)),
                    sum(2 * m * k + 2 * m for k in range(n)), n),
         "dcgs2_update": (sum(8 * m * k + 32 * m for k in range(n)),
-                         sum(m * k * f + (5 if f == 1 else 3) * m for k in range(n)),
+                         sum(m * k * f + 3 * m for k in range(n)),
                          sum(2 * m * k + 3 * m for k in range(n)), n),
         "spmv": (n * (4 * (m + 1) + 12 * nnz + 16 * m), n * (nnz + 2 * m), n * (nnz + 2 * m),
                  n),
-        "finish_reduce": ((8 * m * n + 8 * m) + (8 * m * n + 16 * m), 2 * (m * n + m),
+        "finish_reduce": ((8 * m * n + 8 * m) + (8 * m * n + 16 * m),
+                          (m if fp64_mode >= 1 else m * n + m) + (m * n + m),
                           2 * (m * n + m), 2),
     }
     out = {}

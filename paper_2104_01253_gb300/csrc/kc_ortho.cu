@@ -112,15 +112,15 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Column sums of an nrows x nval table (row c at base + c * stride) in a fixed order
 // (deterministic) into tot[0:nval], by every thread of the CTA (it synchronises; tot may
 // be read after a further __syncthreads).  The last CTA of a reduction runs this while
-// the other SMs idle, so it is arranged for memory-level parallelism: with fewer values
-// than warps, G = nw / nval warps share a value (each over every G-th group of 32 rows)
-// and their sums are added in warp order; otherwise each warp takes four values at a time,
-// so that a lane has four loads of each row in flight.
+// the other SMs idle, so it is arranged for memory-level parallelism: with no more values
+// than warps, G = nw / nval warps share a value (each over every G-th group of 32 rows,
+// eight loads in flight per lane) and their sums are added in warp order; with more, each
+// warp takes four values at a time, so that a lane has sixteen loads in flight.
 __device__ void sum_rows(const double* __restrict__ base, int nrows, int stride, int nval,
                          double* tot) {
   __shared__ double gsum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (nval > 0 && 2 * nval <= nw) {
+  if (nval > 0 && nval <= nw) {
     const int G = nw / nval;
     const int vi = warp % nval, gi = warp / nval;
     double acc = 0.0;
@@ -141,7 +141,7 @@ __device__ void sum_rows(const double* __restrict__ base, int nrows, int stride,
   }
   for (int v0 = warp; v0 < nval; v0 += 4 * nw) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 2
+#pragma unroll 4
     for (int c = lane; c < nrows; c += 32) {
       const double* p = base + (int64_t)c * stride;
 #pragma unroll
@@ -1945,10 +1945,10 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
     int64_t nr = ((int64_t)ctx->num_sms * occ + nsplit - 1) / nsplit;
     if (nr > gcap) nr = gcap < 1 ? 1 : gcap;
     if (ntask == 0) {                        // k = 0: the epilogue alone, on the SpMV's sums
-      nr = 1;
+      nr = 1;                                // (eight warps to share their loads)
       nsplit = 1;
       nt = 0;
-      nw = 1;
+      nw = 8;
       tpw = 1;
       rsub = 1;
     }
