@@ -46,9 +46,9 @@ FALLBACK_HBM_GBS = 6800.0
 # x 2 flop x 2.070 GHz (a DFMA throughput probe measured 1.20 TFLOP/s at 2.0 GHz)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) over algorithmic bytes of the offload-mode register-streaming
-# kernels, from the ncu capture summarised in profiles/dram_f64x_m4096000_n50.md (all 50
-# launches of an expansion at m = 4,096,000).  Valid only for those kernels as captured.
-TRAFFIC_RATIO = {"reduce": 1.004, "dcgs2_update": 0.945}
+# kernels, from the ncu capture summarised in profiles/launches_dcgs2_m16003008_n50.md
+# (steps k = 25 and 26 at m = 4,096,000).  Valid only for those kernels as captured.
+TRAFFIC_RATIO = {"reduce": 1.005, "dcgs2_update": 0.950}
 
 
 def parse():
