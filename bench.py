@@ -72,7 +72,7 @@ def parse():
                         "default: the library's")
     p.add_argument("--no-check", action="store_true",
                    help="skip the loss-of-orthogonality / Arnoldi-relation check")
-    p.add_argument("--suite", default=None, choices=["steps", "solver", "cnn"],
+    p.add_argument("--suite", default=None, choices=["steps", "solver", "cnn", "learn"],
                    help="a measurement suite instead of the benchmark line (module docstring)")
     p.add_argument("--modes", type=int, nargs="+", default=[1], choices=[0, 1, 2])
     p.add_argument("--basis", default="f64", choices=["f64", "f32", "bf16"])
@@ -640,6 +640,118 @@ def suite_solver(args):
                       "launches_by_kind": {k: v[1] for k, v in kinds.items()}}), flush=True)
 
 
+def suite_learn(args):
+    """Config 5 as a study (one-off costs, not the step benchmark): a learning curve of the
+    learned preconditioner on the N x N variable-coefficient family (default 1024^2).
+    Restart residuals of plain GMRES(40) on seeded operators 0..63 (up to 160 cycles each,
+    kept on the device) give three nested training sets: the first 10 cycles of operators
+    0..15, the first 20 of 0..63, and all of them.  Each set trains a network from the same
+    initial weights (Adam, batch 4), which then solves the held-out operators 64..71 with
+    FGMRES(40) to 1e-10.  Plain GMRES(40) and FGMRES(40) with the Jacobi step alone run
+    20,000 iterations on the same operators; their relative residuals after 10,000 and
+    20,000 iterations give a geometric rate per iteration, from which the iterations (and
+    time, at the measured time per iteration) to 1e-10 are extrapolated.  Every solve is
+    timed with CUDA events around the C-ABI call; the training set sizes and all generation
+    and training times are reported."""
+    import torch
+    import paper_2104_01253_gb300 as kc
+    from paper_2104_01253_gb300 import train as tr
+    from synth import gaussian_vector
+    N = 1024 if args.N == 252 else args.N
+    ctx = kc.Context(0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        info = fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        info["seconds"] = t0.elapsed_time(t1) / 1e3
+        return info
+
+    out = {"suite": "learn", "grid": "%d^2" % N}
+    t0 = time.time()
+    host_ops = [tr.varcoef_operator(N, seed) for seed in range(64)]
+    out["host_operator_setup_seconds"] = time.time() - t0
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ops, X, R, owner = tr.generate_pairs(ctx, N, range(64), restart=40, max_cycles=160,
+                                         host_ops=host_ops, on_device=True)
+    torch.cuda.synchronize()
+    out["pair_generation_seconds"] = time.time() - t0
+    out["pairs_generated"] = int(owner.size)
+    del host_ops
+    cycle = np.zeros(owner.size, dtype=np.int64)
+    for o in range(64):
+        idx = np.nonzero(owner == o)[0]
+        cycle[idx] = np.arange(idx.size)
+    held = list(range(64, 72))
+    held_ops = [kc.DeviceCSR(tr.varcoef_operator(N, s)) for s in held]
+    rhs = [torch.as_tensor(gaussian_vector(N * N, 2000 + s), device="cuda") for s in held]
+    curve = []
+    for nops, ncyc, steps in ((16, 10, 600), (64, 20, 1500), (64, 160, 4000)):
+        sel = (owner < nops) & (cycle < ncyc)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        w, hist = tr.train(ctx, ops, X, R, owner, steps=steps, batch=4, lr=2e-3, seed=0,
+                           select=sel)
+        torch.cuda.synchronize()
+        point = {"operators": nops, "cycles_per_operator": ncyc, "pairs": int(sel.sum()),
+                 "adam_steps": steps, "batch": 4, "training_seconds": time.time() - t0,
+                 "loss_first": float(np.mean(hist[:20])),
+                 "loss_last": float(np.mean(hist[-50:])), "held_out": []}
+        for s, A, b in zip(held, held_ops, rhs):
+            x = torch.zeros_like(b)
+            info = timed(lambda: kc.fgmres_solve(ctx, A, w, N, N, b, x, restart=40,
+                                                 rtol=1e-10, maxit=40000))
+            point["held_out"].append({"seed": s, "iters": info["iters"],
+                                      "rel_resid_true": info["rel_resid_true"],
+                                      "seconds": info["seconds"]})
+        its = [h["iters"] for h in point["held_out"]]
+        point["iters_mean"] = float(np.mean(its))
+        point["seconds_mean"] = float(np.mean([h["seconds"] for h in point["held_out"]]))
+        curve.append(point)
+        del w
+    out["curve"] = curve
+    base = []
+    for s, A, b in zip(held, held_ops, rhs):
+        row = {"seed": s}
+        for name, fn in (
+                ("plain_gmres40", lambda x: kc.gmres_solve(ctx, A, b, x, restart=40,
+                                                           rtol=1e-10, maxit=10000)),
+                ("jacobi_fgmres40", lambda x: kc.fgmres_solve(ctx, A, None, N, N, b, x,
+                                                              restart=40, rtol=1e-10,
+                                                              maxit=10000,
+                                                              precond=kc.PREC_JACOBI))):
+            x = torch.zeros_like(b)
+            a = timed(lambda: fn(x))          # restarted: the second call continues the first
+            c = timed(lambda: fn(x)) if a["rel_resid_true"] > 1e-10 else None
+            r10, it10 = a["rel_resid_true"], a["iters"]
+            ent = {"iters": it10, "rel_resid": r10, "seconds": a["seconds"]}
+            if c is not None:
+                r20, it = c["rel_resid_true"], it10 + c["iters"]
+                sec = a["seconds"] + c["seconds"]
+                ent.update(iters=it, rel_resid=r20, seconds=sec, rel_resid_at_10000=r10)
+                rate = (np.log(r20) - np.log(r10)) / max(c["iters"], 1)
+                if r20 <= 1e-10:
+                    ent["converged"] = True
+                elif rate < 0:
+                    est = it + (np.log(1e-10) - np.log(r20)) / rate
+                    ent.update({"converged": False,
+                                "extrapolated_iters_to_1e-10": float(est),
+                                "extrapolated_seconds_to_1e-10": float(est * sec / it)})
+                else:
+                    ent.update(converged=False, stagnated=True)
+            else:
+                ent["converged"] = True
+            row[name] = ent
+        base.append(row)
+    out["baselines"] = base
+    print(json.dumps(out), flush=True)
+
+
 def suite_cnn(args):
     """kc_cnn_forward and kc_cnn_train_step (regression loss, no Adam update) on a seeded
     random batch of N x N images with He-initialised weights, after two warm-up calls of
@@ -688,7 +800,8 @@ def main():
     if args.suite:
         if args.suite == "cnn" and args.N == 252:
             args.N = 1024
-        return {"steps": suite_steps, "solver": suite_solver, "cnn": suite_cnn}[args.suite](args)
+        return {"steps": suite_steps, "solver": suite_solver, "cnn": suite_cnn,
+                "learn": suite_learn}[args.suite](args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 

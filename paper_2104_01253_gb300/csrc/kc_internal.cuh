@@ -281,6 +281,35 @@ kc_status cnn_adam(kc_ctx* ctx, float* w, const float* g, float* m, float* v, in
 int64_t cnn_nparam();
 // the operator is the matrix-free 7-point stencil rather than a CSR matrix
 inline bool is_stencil(const kc_csr* A) { return A->grid[0] > 0; }
+
+// Programmatic dependent launch (griddepcontrol) for the kernels of the DCGS2 step, which
+// follow one another on the stream without a host synchronisation.  A kernel launched with
+// launch_pdl may be scheduled before its predecessor has finished; it calls pdl_wait()
+// before it reads anything (device scalars included), which returns once the predecessor
+// grid has completed and its writes are visible (at once when the launch was an ordinary
+// one).  pdl_trigger() in the predecessor lets the successor's CTAs be scheduled as soon
+// as every CTA of the predecessor has passed it (or exited), so that they are resident
+// while the predecessor's last CTA runs its epilogue.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(cudaStream_t stream, void (*kern)(KArgs...), dim3 grid,
+                              dim3 block, size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 // restarted FP64 DCGS2-GMRES in one launch (kc_gmres_cluster.cu): one thread-block
 // cluster (grid_form 0) or one CTA per SM with a bounded grid barrier (grid_form 1, needs
 // gmres_grid_workspace bytes at grid_ws); writes out_host[0..6] = matvecs, cycles, |g|

@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rp,
                                               const TV* __restrict__ x, TV* __restrict__ y,
                                               int64_t m, const Scalars* __restrict__ sc,
                                               double* __restrict__ dots = nullptr) {
+  pdl_wait();
   if (sc->stop) return;
   double ab = 0.0, as = 0.0;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(256) k_spmv(const int32_t* __restrict__ rp,
       as = fma(xr, (double)s, as);
     }
   }
+  pdl_trigger();
   if (DOTS) store_dots(ab, as, dots);
 }
 
@@ -311,6 +313,7 @@ __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __
                                                   int nx, int ny, int nz, Stencil7<T> c,
                                                   const Scalars* __restrict__ sc,
                                                   double* __restrict__ dots = nullptr) {
+  pdl_wait();
   if (sc->stop) return;
   double ab = 0.0, as = 0.0;
   const int64_t m = (int64_t)nx * ny * nz, pl = (int64_t)nx * ny;
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __
       as = fma(xr, (double)s, as);
     }
   }
+  pdl_trigger();
   if (DOTS) store_dots(ab, as, dots);
 }
 
@@ -895,6 +899,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
               unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa,
               int nsplit, int nt, int epi, const double* __restrict__ dots, int ndots,
               int rsub) {
+  pdl_wait();
   if (sc->stop) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (int)(blockDim.x >> 5) / rsub;     // task warps per row sub-block
@@ -992,6 +997,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
       else pp[2 * k + (t - k)] = cv[i];       // beta -> [2k], s -> [2k + 1]
     }
   }
+  pdl_trigger();
   if (!last_cta(counter)) return;
   reduce_epilogue(partials, k, 2, sc, epi, sa, nr, dots, ndots);
 }
@@ -1384,6 +1390,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 4)
 k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restrict__ w,
                     const double* __restrict__ v, int64_t m, const Scalars* __restrict__ sc,
                     int allow32) {
+  pdl_wait();
   if (sc->stop) return;
   __shared__ double sC[NMAX + 1], sT[NMAX + 1];
   __shared__ float cH[NMAX + 1], cL[NMAX + 1];
@@ -1519,6 +1526,7 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
     store_q(qk, g, qn);
     stv(w, g, wo);
   }
+  pdl_trigger();
   if (blockIdx.x == 0) {        // ragged tail: FP64
     for (int64_t row = ngroups * 2 + threadIdx.x; row < m; row += blockDim.x) {
       double u = w[row], wn1 = v[row] * vsc;
@@ -1776,11 +1784,13 @@ kc_status launch_spmv_dots(kc_ctx* ctx, const kc_csr* A, const void* x, void* y,
   if (is_stencil(A)) {
     Stencil7<double> c;
     for (int i = 0; i < 7; i++) c.c[i] = A->stencil[i];
-    k_stencil7<double, true><<<grid, 256, 0, ctx->stream>>>((const double*)x, (double*)y,
-        A->grid[0], A->grid[1], A->grid[2], c, ctx->scal, ctx->dots);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_stencil7<double, true>, grid, 256, 0,
+                            (const double*)x, (double*)y, A->grid[0], A->grid[1], A->grid[2],
+                            c, (const Scalars*)ctx->scal, ctx->dots));
   } else {
-    k_spmv<double, double, true><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
-        (const double*)A->val, (const double*)x, (double*)y, A->m, ctx->scal, ctx->dots);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_spmv<double, double, true>, grid, 256, 0,
+                            A->row_ptr, A->col_idx, (const double*)A->val, (const double*)x,
+                            (double*)y, A->m, (const Scalars*)ctx->scal, ctx->dots));
   }
   KC_LAUNCHED(ctx);
   ctx->dots_pending = grid;
@@ -1953,15 +1963,17 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
       rsub = 1;
     }
     const int g = (int)(nr * nsplit);
+    cudaError_t le = cudaSuccess;
     auto go = [&](auto kern) {
-      kern<<<g, 32 * nw, 0, ctx->stream>>>((const double*)Q, ldq, k, (const double*)x,
-                                           (const double*)y, m, ctx->partials, ctx->counters,
-                                           ctx->scal, sa, nsplit, nt, epilogue,
-                                           ndots ? ctx->dots : nullptr, ndots, rsub);
+      le = launch_pdl(ctx->stream, kern, g, 32 * nw, 0, (const double*)Q, ldq, k,
+                      (const double*)x, (const double*)y, m, ctx->partials, ctx->counters,
+                      ctx->scal, sa, nsplit, nt, epilogue,
+                      (const double*)(ndots ? ctx->dots : nullptr), ndots, rsub);
     };
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
     else if (tpw == 2) go(k_reduce_f64x<2, 2>);
     else go(k_reduce_f64x<3, 1>);
+    KC_CUDA(ctx, le);
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64 && !two && k >= 1 &&
              (epilogue == EPI_STORE_C || epilogue == EPI_STORE_C1 || epilogue == EPI_STORE_C2 ||
               epilogue == EPI_PARTIAL) &&
@@ -2011,7 +2023,9 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_UPDATE);
   if (q_dtype == KC_F64 && ctx->fp64_mode >= 1)
-    k_dcgs2_update_f64x<<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal, !(ctx->staged & 4));
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_dcgs2_update_f64x, grid, UPD_THREADS, 0, (double*)Q,
+                            ldq, k, (double*)w, (const double*)v, m,
+                            (const Scalars*)ctx->scal, !(ctx->staged & 4)));
   else if (q_dtype == KC_F64)
     k_dcgs2_update<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
   else if (q_dtype == KC_F32)

@@ -42,15 +42,20 @@ def he_init(seed: int) -> np.ndarray:
 
 
 def generate_pairs(ctx: Context, N: int, seeds, restart: int = 40, max_cycles: int = 20,
-                   rhs_seed_offset: int = 1000, host_ops=None):
+                   rhs_seed_offset: int = 1000, host_ops=None, on_device: bool = False):
     """Restart residuals of plain GMRES solves on the seeded operators (host_ops: the host
     CSR operators of `seeds`, if already built).
 
     Returns (ops, X, R, owner): the device operators, the network inputs
-    X = D^{-1} r / s and residuals R = r / s (float32, (n, 1, N, N), host), and the index
-    of each sample's operator."""
+    X = D^{-1} r / s and residuals R = r / s (float32, (n, 1, N, N); host arrays, or device
+    tensors with on_device), and the index of each sample's operator.  A sample's cycle
+    within its operator's solve is its rank among the samples of that operator."""
     from synth import gaussian_vector
     ops, X, R, owner = [], [], [], []
+    seeds = list(seeds)
+    if on_device:                                    # capacity: every cycle of every solve
+        Xd = torch.empty((len(seeds) * max_cycles, N * N), dtype=torch.float32, device="cuda")
+        Rd = torch.empty_like(Xd)
     for oi, seed in enumerate(seeds):
         Ah = host_ops[oi] if host_ops is not None else varcoef_operator(N, seed)
         A = DeviceCSR(Ah)
@@ -65,19 +70,27 @@ def generate_pairs(ctx: Context, N: int, seeds, restart: int = 40, max_cycles: i
             bnorm = rn if bnorm is None else bnorm           # x = 0 on the first pass
             if rn <= 1e-9 * bnorm:
                 break
-            X.append(xin.cpu().numpy())
-            R.append(res.cpu().numpy())
+            if on_device:
+                Xd[len(owner)].copy_(xin)
+                Rd[len(owner)].copy_(res)
+            else:
+                X.append(xin.cpu().numpy())
+                R.append(res.cpu().numpy())
             owner.append(oi)
             gmres_solve(ctx, A, b, x, restart=restart, rtol=1e-10, maxit=restart)
+    if on_device:
+        n = len(owner)
+        return ops, Xd[:n].view(n, 1, N, N), Rd[:n].view(n, 1, N, N), np.asarray(owner)
     X = np.stack(X).reshape(-1, 1, N, N)
     R = np.stack(R).reshape(-1, 1, N, N)
     return ops, X, R, np.asarray(owner)
 
 
-def train(ctx: Context, ops, X: np.ndarray, R: np.ndarray, owner: np.ndarray,
-          steps: int = 600, batch: int = 16, lr: float = 2e-3, seed: int = 0, w0=None):
+def train(ctx: Context, ops, X, R, owner: np.ndarray, steps: int = 600, batch: int = 16,
+          lr: float = 2e-3, seed: int = 0, w0=None, select=None):
     """Adam on the residual loss; returns the FP32 weights (device tensor) and the loss
-    history.  Step t uses operator t mod len(ops) and a batch of its samples."""
+    history.  Step t uses operator t mod len(ops) (among those with samples) and a batch of
+    its samples; `select` (boolean mask over the samples) restricts the training set."""
     n, _, H, W = X.shape
     w = torch.as_tensor(he_init(seed) if w0 is None else w0, device="cuda").contiguous()
     m = torch.zeros_like(w)
@@ -85,13 +98,13 @@ def train(ctx: Context, ops, X: np.ndarray, R: np.ndarray, owner: np.ndarray,
     xd = torch.as_tensor(X, device="cuda")
     rd = torch.as_tensor(R, device="cuda")
     y = torch.empty((batch, 1, H, W), dtype=torch.float32, device="cuda")
-    pools = [np.nonzero(owner == o)[0] for o in range(len(ops))]
+    keep = np.ones(owner.shape, dtype=bool) if select is None else np.asarray(select, dtype=bool)
+    pools = [np.nonzero((owner == o) & keep)[0] for o in range(len(ops))]
+    used = [o for o in range(len(ops)) if pools[o].size > 0]
     rng = np.random.default_rng(seed + 1)
     hist = []
     for t in range(1, steps + 1):
-        o = (t - 1) % len(ops)
-        if pools[o].size == 0:
-            continue
+        o = used[(t - 1) % len(used)]
         idx = torch.as_tensor(rng.choice(pools[o], size=batch), device="cuda")
         xb = xd[idx].contiguous()
         rb = rd[idx].contiguous()
