@@ -1731,6 +1731,23 @@ static int grid_for(const kc_ctx* ctx, int64_t work_items, int per_block, int ma
   return (int)b;
 }
 
+// The grid of a grid-stride kernel capped at one full wave: `want` CTAs, at most the SM
+// count times the CTAs of `kern` that fit on an SM at `threads` per CTA (looked up once
+// per call site into `cache`).  A grid of 1216 CTAs that fit six to an SM would otherwise
+// run as one full and one third-full wave.
+template <typename K>
+static int one_wave(const kc_ctx* ctx, K kern, int threads, int want, std::atomic<int>& cache) {
+  int occ = cache.load(std::memory_order_relaxed);
+  if (occ == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+    cache.store(occ, std::memory_order_relaxed);
+  }
+  const int64_t cap = (int64_t)occ * ctx->num_sms;
+  return want < cap ? want : (int)cap;
+}
+
 static int reduce_grid_for(const kc_ctx* ctx, int64_t ngroups) {
   // at least ~4 groups per lane before splitting across more CTAs
   int64_t b = (ngroups + 32 * 4 - 1) / (32 * 4);
@@ -1756,13 +1773,17 @@ kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int 
   if (is_stencil(A)) {
     const int nx = A->grid[0], ny = A->grid[1], nz = A->grid[2];
     if (vec_dtype == KC_F64) {
+      static std::atomic<int> occ{0};
       Stencil7<double> c;
       for (int i = 0; i < 7; i++) c.c[i] = A->stencil[i];
+      grid = one_wave(ctx, k_stencil7<double, false>, 256, grid, occ);
       k_stencil7<double><<<grid, 256, 0, ctx->stream>>>((const double*)x, (double*)y, nx, ny,
                                                         nz, c, ctx->scal);
     } else {
+      static std::atomic<int> occ{0};
       Stencil7<float> c;
       for (int i = 0; i < 7; i++) c.c[i] = (float)A->stencil[i];
+      grid = one_wave(ctx, k_stencil7<float, false>, 256, grid, occ);
       k_stencil7<float><<<grid, 256, 0, ctx->stream>>>((const float*)x, (float*)y, nx, ny, nz,
                                                        c, ctx->scal);
     }
@@ -1779,15 +1800,19 @@ kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int 
 kc_status launch_spmv_dots(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype) {
   ctx->dots_pending = 0;
   if (vec_dtype != KC_F64 || A->val_dtype != KC_F64) return launch_spmv(ctx, A, x, y, vec_dtype);
-  const int grid = grid_for(ctx, A->m, 256, 8);         // <= 8 * num_sms (the dots buffer)
+  int grid = grid_for(ctx, A->m, 256, 8);               // <= 8 * num_sms (the dots buffer)
   timing_begin(ctx, KID_SPMV);
   if (is_stencil(A)) {
+    static std::atomic<int> occ{0};
     Stencil7<double> c;
     for (int i = 0; i < 7; i++) c.c[i] = A->stencil[i];
+    grid = one_wave(ctx, k_stencil7<double, true>, 256, grid, occ);
     KC_CUDA(ctx, launch_pdl(ctx->stream, k_stencil7<double, true>, grid, 256, 0,
                             (const double*)x, (double*)y, A->grid[0], A->grid[1], A->grid[2],
                             c, (const Scalars*)ctx->scal, ctx->dots));
   } else {
+    static std::atomic<int> occ{0};
+    grid = one_wave(ctx, k_spmv<double, double, true>, 256, grid, occ);
     KC_CUDA(ctx, launch_pdl(ctx->stream, k_spmv<double, double, true>, grid, 256, 0,
                             A->row_ptr, A->col_idx, (const double*)A->val, (const double*)x,
                             (double*)y, A->m, (const Scalars*)ctx->scal, ctx->dots));
@@ -2022,13 +2047,17 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
   const int R = vec_dtype == KC_F64 ? 2 : 4;
   const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_UPDATE);
-  if (q_dtype == KC_F64 && ctx->fp64_mode >= 1)
-    KC_CUDA(ctx, launch_pdl(ctx->stream, k_dcgs2_update_f64x, grid, UPD_THREADS, 0, (double*)Q,
+  if (q_dtype == KC_F64 && ctx->fp64_mode >= 1) {
+    static std::atomic<int> occ{0};
+    const int g = one_wave(ctx, k_dcgs2_update_f64x, UPD_THREADS, grid, occ);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_dcgs2_update_f64x, g, UPD_THREADS, 0, (double*)Q,
                             ldq, k, (double*)w, (const double*)v, m,
                             (const Scalars*)ctx->scal, !(ctx->staged & 4)));
-  else if (q_dtype == KC_F64)
-    k_dcgs2_update<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
-  else if (q_dtype == KC_F32)
+  } else if (q_dtype == KC_F64) {
+    static std::atomic<int> occ{0};
+    const int g = one_wave(ctx, k_dcgs2_update<double, double>, UPD_THREADS, grid, occ);
+    k_dcgs2_update<double, double><<<g, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
+  } else if (q_dtype == KC_F32)
     k_dcgs2_update<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((float*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
   else
     k_dcgs2_update<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((__nv_bfloat16*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
@@ -2066,8 +2095,10 @@ kc_status launch_proj_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtyp
 kc_status launch_gemv_sub(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k, void* x,
                           int64_t m, int vec_dtype, int which) {
   const int R = vec_dtype == KC_F64 ? 2 : 4;
-  const int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
+  int grid = grid_for(ctx, m / R, UPD_THREADS, 8);
   timing_begin(ctx, KID_GEMV_SUB);
+  static std::atomic<int> occ{0};
+  if (q_dtype == KC_F64) grid = one_wave(ctx, k_gemv_sub<double, double>, UPD_THREADS, grid, occ);
   if (q_dtype == KC_F64)
     k_gemv_sub<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((const double*)Q, ldq, k, (double*)x, m, ctx->scal, which, ctx->fp64_mode >= 1 && which != 2 && !(ctx->staged & 4));
   else if (q_dtype == KC_F32)
