@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--no-solvers", action="store_true",
                    help="skip the GMRES time-to-1e-10 runs (plain FP64 vs FP32/BF16 IR)")
     p.add_argument("--fp64-mode", type=int, default=1, choices=[0, 1, 2])
-    p.add_argument("--staged", type=int, default=None, choices=[0, 1, 2, 3],
+    p.add_argument("--staged", type=int, default=None, choices=[0, 1, 2, 3, 8],
                    help="kernel variants of the basis passes (kc_set_staged flags); "
                         "default: the library's")
     p.add_argument("--no-check", action="store_true",
@@ -97,8 +97,12 @@ def algorithmic_bytes(m, nnz, n):
     """HBM bytes of one expansion (n DCGS2 steps + finish), FP64, int32 indices.
 
     step k: SpMV 4(m+1) + 12 nnz + 8m (x) + 8m (y); reduction 8mk + 16m (Q_k, w, v);
-    update 8mk + 16m reads + 16m writes (q_k, w).  finish: two (reduction + projection)
-    passes 2*(8mk + 8m) + 2*(8mk + 16m), norm 8m, scaling 16m."""
+    update 8mk + 16m reads + 16m writes (q_k, w).  finish, counted as the method's CGS2
+    pass (two projections' sums and two projections, whatever the kernels fuse):
+    2*(8mk + 8m) + 2*(8mk + 16m), norm 8m, scaling 16m.  The steps alone are 16mk + 48m
+    plus the SpMV each; the fused passes (the first steps' SpMV with
+    the reduction, the finish's u = w - Q C1 with the second projection's sums) move less
+    than this count."""
     spmv = 4 * (m + 1) + 12 * nnz + 16 * m
     total = 0
     per_kernel = {"spmv": 0, "reduce": 0, "dcgs2_update": 0}
@@ -120,7 +124,10 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
     f = 1 with offload, 2 all-FP64, against the method's 2 m k + 2 m.  Update:
     bytes 8 m k + 32 m; FP64-pipe operations m k f + 3 m (v / alpha, q and w' per row)
     against 2 m k + 3 m.  SpMV: 4 (m + 1) + 12 nnz + 16 m bytes, nnz + 2 m FMAs (the matvec,
-    beta and s).  The CGS2 finish (k = n): the first projection's sums (8 m k + 8 m bytes;
+    beta and s).  With the first steps fused (flag 8, k <= 4: `spmv_reduce`) those steps
+    count under that kind, with the SpMV's bytes plus 8 m k and its FMAs plus m k, and the
+    SpMV and reduction rows cover the other steps.  The CGS2 finish (k = n): the first
+    projection's sums (8 m k + 8 m bytes;
     with offload its column sums are float-float, so m FP64 FMAs for x^T x, else m k + m) and
     the fused u = w - Q C1 with the second projection's sums (8 m k + 16 m bytes, m k + m
     FMAs).  In FP64 mode 2
@@ -129,15 +136,23 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
     f = 2 if fp64_mode == 0 else 1
     fr = {0: 2, 1: 1, 2: 0}[fp64_mode]            # mode 2: the reduction has no FP64 FMA
     bs = 2 if fp64_mode == 0 else 0               # beta, s FMAs per row in the reduction
+    # with kc_set_staged flag 8 the first nf steps (FP64 mode 1) form v = A w and the
+    # reduction in one fused pass:
+    # the SpMV's bytes plus the basis columns (w and v are not read again), the SpMV's FMAs
+    # plus m k for C (S is float-float)
+    nf = kern.get("spmv_reduce", (0.0, 0))[1] // max(steps, 1)
+    sp = 4 * (m + 1) + 12 * nnz + 16 * m
     rows = {
-        "reduce": (sum(8 * m * k + 16 * m for k in range(n)),
-                   sum(m * k * fr + bs * m for k in range(n)),
-                   sum(2 * m * k + 2 * m for k in range(n)), n),
+        "reduce": (sum(8 * m * k + 16 * m for k in range(nf, n)),
+                   sum(m * k * fr + bs * m for k in range(nf, n)),
+                   sum(2 * m * k + 2 * m for k in range(nf, n)), n - nf),
         "dcgs2_update": (sum(8 * m * k + 32 * m for k in range(n)),
                          sum(m * k * f + 3 * m for k in range(n)),
                          sum(2 * m * k + 3 * m for k in range(n)), n),
-        "spmv": (n * (4 * (m + 1) + 12 * nnz + 16 * m), n * (nnz + 2 * m), n * (nnz + 2 * m),
-                 n),
+        "spmv": ((n - nf) * sp, (n - nf) * (nnz + 2 * m), (n - nf) * (nnz + 2 * m), n - nf),
+        "spmv_reduce": (sum(sp + 8 * m * k for k in range(nf)),
+                        sum(nnz + 2 * m + m * k for k in range(nf)),
+                        sum(nnz + 2 * m + 2 * m * k for k in range(nf)), nf),
         "finish_reduce": ((8 * m * n + 8 * m) + (8 * m * n + 16 * m),
                           (m if fp64_mode >= 1 else m * n + m) + (m * n + m),
                           2 * (m * n + m), 2),
@@ -145,7 +160,7 @@ def kernel_rooflines(kern, m, nnz, n, steps, fp64_mode, hbm_peak):
     out = {}
     for name, (byts, fma_pipe, fma_method, launches) in rows.items():
         ms_k, cnt_k = kern.get(name, (0.0, 0))
-        if cnt_k == 0 or ms_k <= 0.0:
+        if cnt_k == 0 or ms_k <= 0.0 or launches == 0:
             continue
         t = ms_k / 1e3
         tf = 2.0 * fma_pipe * steps / t / 1e12
@@ -553,6 +568,8 @@ def suite_steps(args):
     A = kc.DeviceCSR(Ah, dtype=fdt)
     st = kc.ArnoldiState(Ah.m, args.n + 1, qdt)
     r0 = torch.as_tensor(synth.gaussian_vector(Ah.m, 1002), device="cuda", dtype=fdt)
+    if args.staged is not None:
+        ctx.set_staged(args.staged)
     for mode in args.modes:
         ctx.set_fp64_mode(mode)
         kc.dcgs2_arnoldi_init(ctx, A, st, r0)
@@ -568,13 +585,15 @@ def suite_steps(args):
             torch.cuda.synchronize()
             d = {kk: v[0] for kk, v in ctx.timing_read().items()}
             per_k.append([k] + [round(1e3 * d.get(kk, 0.0), 1)
-                                for kk in ("reduce", "dcgs2_update", "spmv")])
+                                for kk in ("reduce", "dcgs2_update", "spmv", "spmv_reduce")])
         ctx.timing_enable(False)
         print(json.dumps({"suite": "steps", "m": Ah.m, "basis": args.basis, "fp64_mode": mode,
                           "status": ctx.read_status(),
                           "ms": {kk: round(sum(r[i] for r in per_k) / 1e3, 3)
-                                 for i, kk in enumerate(("reduce", "update", "spmv"), 1)},
-                          "per_step_us": {"columns": ["k", "reduce", "update", "spmv"],
+                                 for i, kk in enumerate(("reduce", "update", "spmv",
+                                                         "spmv_reduce"), 1)},
+                          "per_step_us": {"columns": ["k", "reduce", "update", "spmv",
+                                                      "spmv_reduce"],
                                           "rows": per_k}}), flush=True)
     ctx.set_fp64_mode(1)
 
@@ -960,7 +979,7 @@ def main():
         ms_sp, cnt_sp = ks.get("spmv", (0.0, 0))
         per_launch = ms_sp / max(cnt_sp, 1)
         gbs_sp = 16 * m / (per_launch / 1e3) / 1e9
-        tf_sp = 14 * m / (per_launch / 1e3) / 1e12
+        tf_sp = 18 * m / (per_launch / 1e3) / 1e12      # 7 products, beta and s per row
         matrix_free = {
             "operator": "7-point stencil %d^3, coefficients of the CSR matrix (no matrix in "
                         "HBM)" % args.N,
@@ -969,7 +988,7 @@ def main():
                                "hbm_gbs": gbs_sp, "hbm_frac": gbs_sp / hbm_peak,
                                "fp64_tflops": tf_sp, "fp64_frac": tf_sp / FP64_PEAK_TFLOPS,
                                "algorithmic_bytes_per_launch": 16 * m,
-                               "fp64_flop_per_launch": 14 * m},
+                               "fp64_flop_per_launch": 18 * m},
             "csr_spmv_avg_launch_ms": kern["spmv"][0] / max(kern["spmv"][1], 1),
         }
         if not args.no_solvers:

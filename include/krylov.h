@@ -141,7 +141,11 @@ int kc_get_fp64_mode(const kc_ctx* ctx);
  *     take float-float (update) or FP64 (finish), instead of FP32 products on the
  *     launches whose error bound, (k + 3) 2^-24 ||C||_1 <= 2^-53 ||w - Q C||, holds; and
  *     the finish's first projection C1 = Q^T w is summed in FP64 instead of float-float
- *     (its error is removed by the second projection either way).
+ *     (its error is removed by the second projection either way);
+ *  8: fused first steps: in FP64 mode 1 the steps with k <= 4 basis columns form
+ *     v = A w and the fused reduction in one pass (one thread per row, one launch fewer,
+ *     w and v read once; the pass stays bound by its FP64 operations, so it is not the
+ *     default);
  * 0 streams both passes through registers, with the bounded FP32 products. */
 kc_status kc_set_staged(kc_ctx* ctx, int flags);
 /* Kernel of the network's 32 -> 32 convolutions: 0 mma.sync (m16n8k16, registers);
@@ -172,7 +176,8 @@ int64_t kc_launch_count(const kc_ctx* ctx);
  * returns, per kernel kind, the summed elapsed milliseconds and launch counts, then
  * clears the records.  Kinds (index): 0 SpMV, 1 fused reduction, 2 DCGS2 update,
  * 3 projection update (x -= Q c), 4 norm / dot, 5 scaling, 6 MGS axpy, 7 small dense
- * kernels, 8 other.  nkinds must be >= 9. */
+ * kernels, 8 other, 9 the CGS2 finish's reductions, 10 the fused SpMV and reduction of
+ * the first DCGS2 steps.  nkinds must be >= 11. */
 kc_status kc_timing_enable(kc_ctx* ctx, int on);
 kc_status kc_timing_read(kc_ctx* ctx, double* ms, int64_t* count, int nkinds);
 /* Read (and synchronise on) the device status word written by the last reductions:

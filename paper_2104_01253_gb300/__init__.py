@@ -98,7 +98,7 @@ class Context:
         return n.value, g.value
 
     KERNEL_KINDS = ("spmv", "reduce", "dcgs2_update", "gemv_sub", "norm", "scale", "axpy",
-                    "small", "other", "finish_reduce")
+                    "small", "other", "finish_reduce", "spmv_reduce")
 
     def timing_enable(self, on=True):
         self.check(self.lib.kc_timing_enable(self.handle, 1 if on else 0))

@@ -194,7 +194,7 @@ kc_status kc_set_barrier_test(kc_ctx* ctx, int on) {
 }
 
 kc_status kc_set_staged(kc_ctx* ctx, int flags) {
-  if (!ctx || flags < 0 || flags > 7) return KC_ERR_INVALID_ARG;
+  if (!ctx || flags < 0 || flags > 15) return KC_ERR_INVALID_ARG;
   ctx->staged = flags;
   return KC_OK;
 }
@@ -287,11 +287,9 @@ kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
     return fail(ctx, KC_ERR_INVALID_ARG, "basis full: k = %d, ncap = %d", k, st->ncap);
   if (st->finished) return fail(ctx, KC_ERR_INVALID_ARG, "expansion already finished");
   const int vec = vec_of(st);
-  if (vec == KC_F64) KC_TRY(launch_spmv_dots(ctx, A, st->w, st->v, vec));  // v = A w
-  else KC_TRY(launch_spmv(ctx, A, st->w, st->v, vec));
   StepArgs sa = step_args(st, k, vec == KC_F32 ? SF_FALLBACK : 0);
-  KC_TRY(launch_reduce(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec,
-                       EPI_DCGS2, sa));                                  // one reduction
+  KC_TRY(launch_matvec_reduce(ctx, A, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec,
+                              sa));                      // v = A w and the one reduction
   if (vec == KC_F32)   // reduced precision: explicit norm when Pythagoras lost its digits
     KC_TRY(launch_fallback_norm(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, A->m, sa));
   KC_TRY(launch_dcgs2_update(ctx, st->Q, st->ldq, st->q_dtype, k, st->w, st->v, A->m, vec));

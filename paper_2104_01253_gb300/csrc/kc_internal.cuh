@@ -125,7 +125,7 @@ enum StepFlags : int { SF_FLEXIBLE = 1, SF_GIVENS = 2, SF_FALLBACK = 4, SF_QR = 
 namespace kc {
 enum KernelId : int {
   KID_SPMV = 0, KID_REDUCE, KID_UPDATE, KID_GEMV_SUB, KID_NORM, KID_SCALE, KID_AXPY,
-  KID_SMALL, KID_OTHER, KID_FIN_REDUCE, KID_COUNT
+  KID_SMALL, KID_OTHER, KID_FIN_REDUCE, KID_SPMV_REDUCE, KID_COUNT
 };
 struct TimingRec { cudaEvent_t a, b; int kid; };
 }  // namespace kc
@@ -226,6 +226,12 @@ kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int 
 // next launch_reduce of (w, v) with the DCGS2 epilogue in the offload mode takes them
 // instead of computing them (any other launch_reduce drops them)
 kc_status launch_spmv_dots(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int vec_dtype);
+// v = A w and the fused DCGS2 reduction of step k with the scalar step (EPI_DCGS2):
+// launch_spmv_dots (or launch_spmv for FP32) and launch_reduce, or with kc_set_staged flag
+// 8 the first steps (k <= 4, FP64 offload mode) as one fused pass
+kc_status launch_matvec_reduce(kc_ctx* ctx, const kc_csr* A, const void* Q, int64_t ldq,
+                               int q_dtype, int k, const void* w, void* v, int64_t m, int vec,
+                               const StepArgs& sa);
 kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int k,
                         const void* x, const void* y, int64_t m, int vec_dtype, int epilogue,
                         const StepArgs& sa);

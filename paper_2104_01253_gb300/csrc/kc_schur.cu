@@ -698,8 +698,8 @@ extern "C" kc_status krylov_schur_eigs(kc_ctx* ctx, const kc_csr* A, const doubl
     // expand k0 .. n-1 with DCGS2 steps, then the CGS2 finish (column n)
     for (int k = k0; k < n; k++) {
       sa.k = k;
-      if ((s = launch_spmv_dots(ctx, A, w, v, KC_F64)) != KC_OK) return s;
-      if ((s = launch_reduce(ctx, Qa, ldq, KC_F64, k, w, v, m, KC_F64, EPI_DCGS2, sa)) != KC_OK) return s;
+      if ((s = launch_matvec_reduce(ctx, A, Qa, ldq, KC_F64, k, w, v, m, KC_F64, sa)) != KC_OK)
+        return s;
       if ((s = launch_dcgs2_update(ctx, Qa, ldq, KC_F64, k, w, v, m, KC_F64)) != KC_OK) return s;
       mv++;
     }

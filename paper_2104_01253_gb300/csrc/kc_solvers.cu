@@ -157,9 +157,8 @@ static kc_status gmres_cycle(kc_ctx* ctx, const kc_csr* A, const Cycle& c, void*
   kc_status s;
   for (int k = 0; k < c.n; k++) {
     sa.k = k;
-    if ((s = (c.vec == KC_F64 ? launch_spmv_dots : launch_spmv)(ctx, A, c.w, c.v, c.vec)) != KC_OK)
+    if ((s = launch_matvec_reduce(ctx, A, c.Q, c.ldq, c.qdt, k, c.w, c.v, m, c.vec, sa)) != KC_OK)
       return s;
-    if ((s = launch_reduce(ctx, c.Q, c.ldq, c.qdt, k, c.w, c.v, m, c.vec, EPI_DCGS2, sa)) != KC_OK) return s;
     if (c.vec == KC_F32 &&
         (s = launch_fallback_norm(ctx, c.Q, c.ldq, c.qdt, k, c.w, m, sa)) != KC_OK) return s;
     if ((s = launch_dcgs2_update(ctx, c.Q, c.ldq, c.qdt, k, c.w, c.v, m, c.vec)) != KC_OK) return s;

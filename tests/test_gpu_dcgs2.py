@@ -70,7 +70,7 @@ def test_spmv_matches_scipy(kc, ctx, name, make):
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("staged", [0, 2, 3, 4])
+@pytest.mark.parametrize("staged", [0, 2, 3, 4, 8])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("name,make", CASES)
 @pytest.mark.parametrize("n", [1, 2, 17, 50])
@@ -79,7 +79,8 @@ def test_dcgs2_matches_oracle(kc, ctx, name, make, n, mode, staged):
     reduction as exact digit products on the tensor cores (2, which takes precedence over
     the staged reduction); the register-streaming kernels with the bounded FP32 products
     of Q C (staged 0) and without them (4), the tensor-copy staged reduction (2) and that
-    with the bulk-copy staged update (3)."""
+    with the bulk-copy staged update (3); flag 8 fuses v = A w into the reduction's pass
+    for the first steps (k <= 4) in mode 1."""
     Ah = make()
     r0 = gaussian_vector(Ah.m, 1002)
     ctx.set_fp64_mode(mode)
@@ -96,6 +97,39 @@ def test_dcgs2_matches_oracle(kc, ctx, name, make, n, mode, staged):
     assert np.abs(Qg - Qo).max() <= 1e-10
     assert loo(Qg) <= 1e-13
     assert rre(Ah.to_scipy(), Qg, Hg) <= 1e-14
+    assert ctx.read_status() == 0
+
+
+def test_fused_first_steps_agree_with_separate_passes(kc, ctx):
+    """With flag 8 the first steps in FP64 mode 1 form v = A w inside the reduction's pass
+    (one launch); by default the SpMV and the reduction run apart.  The row arithmetic of v
+    is shared, so step 0's v (from the same w = r0) is bitwise equal; later steps and H
+    agree to rounding (the sums run in another order), and both runs match the oracle."""
+    Ah = convdiff_csr(37, 3, [50.0, 25.0, 12.5])                         # m = 50653
+    r0 = gaussian_vector(Ah.m, 1002)
+    A = kc.DeviceCSR(Ah)
+    n = 8
+    runs = []
+    for flags in (0, 8):
+        ctx.set_staged(flags)
+        try:
+            st = kc.ArnoldiState(Ah.m, n + 1, kc.KC_F64)
+            kc.dcgs2_arnoldi_init(ctx, A, st, torch.as_tensor(r0, device="cuda"))
+            kc.dcgs2_arnoldi_step(ctx, A, st)
+            v0 = st.v.clone()
+            for _ in range(n - 1):
+                kc.dcgs2_arnoldi_step(ctx, A, st)
+            kc.dcgs2_arnoldi_finish(ctx, A, st)
+            torch.cuda.synchronize()
+        finally:
+            ctx.set_staged(0)
+        runs.append((v0, st.Q(n + 1).cpu().numpy(), st.H(n + 1, n).cpu().numpy()))
+    assert torch.equal(runs[0][0], runs[1][0])
+    Qo, Ho = orc.dcgs2_arnoldi(Ah.to_scipy(), r0, n)
+    for _, Qg, Hg in runs:
+        assert np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho) <= H_TOL
+        assert np.abs(Qg - Qo).max() <= 1e-10
+    assert np.linalg.norm(runs[0][2] - runs[1][2]) / np.linalg.norm(Ho) <= 1e-14
     assert ctx.read_status() == 0
 
 

@@ -39,9 +39,10 @@ def problem():
     return Ah, r0, Qo, Ho
 
 
-@pytest.mark.parametrize("mode,flags", [(1, 0), (0, 0), (2, 0), (1, 4)])
+@pytest.mark.parametrize("mode,flags", [(1, 0), (0, 0), (2, 0), (1, 4), (1, 8)])
 def test_dcgs2_long_basis_matches_oracle(kc, problem, mode, flags):
-    """flags 4: mode 1 without the bounded FP32 products of Q C (float-float always)."""
+    """flags 4: mode 1 without the bounded FP32 products of Q C (float-float always);
+    flags 8: the fused first steps (SpMV and reduction in one pass for k <= 4)."""
     Ah, r0, Qo, Ho = problem
     ctx = kc.Context(0)
     n = N_STEPS
