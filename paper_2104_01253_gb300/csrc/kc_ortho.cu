@@ -741,7 +741,12 @@ k_gemv_sub(const TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ x, int
   __syncthreads();
   const int64_t ngroups = m / R;
   if (sizeof(TQ) == 8 && sizeof(TV) == 8 && s_fast) {
-    const double scale = s_scale, inv = 1.0 / scale;        // powers of two
+    // powers of two: the inverse by its exponent (a division in every thread is a
+    // sequence of FP64 operations on this pipe-bound GPU)
+    const double scale = s_scale;
+    int ex_s = 0;
+    frexp(scale, &ex_s);
+    const double inv = ldexp(1.0, 1 - ex_s);
     for (int i = threadIdx.x; i < k; i += blockDim.x) sf_[i] = d2f_trunc(src[i] * inv);
     __syncthreads();
     const double* Qd = reinterpret_cast<const double*>(Q);
@@ -1532,7 +1537,14 @@ k_dcgs2_update_f64x(double* __restrict__ Q, int64_t ldq, int k, double* __restri
               fabs(cf) <= 0x1p100) ? 1 : 0;
   }
   __syncthreads();
-  const double inv_scale = 1.0 / s_scale;     // exact: a power of two
+  __shared__ double s_inv_scale;
+  if (threadIdx.x == 0) {                     // exact: a power of two, without a division
+    int ex = 0;
+    frexp(s_scale, &ex);
+    s_inv_scale = ldexp(1.0, 1 - ex);
+  }
+  __syncthreads();
+  const double inv_scale = s_inv_scale;
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
     float h, l;
     if (!split_df(sC[i] * inv_scale, h, l)) { h = 0.0f; l = 0.0f; if (sC[i] != 0.0) s_cok = 0; }
