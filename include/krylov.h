@@ -332,7 +332,9 @@ typedef struct {
   double rtol;            /* relative residual target ||b - A x|| / ||b|| */
   double inner_rtol;      /* IR: inner solve tolerance (relative to its right-hand side) */
   int32_t inner_max_cycles; /* IR: cycles per inner solve */
-  int32_t precond;        /* fgmres_solve only: a kc_precond_kind (gmres_solve ignores it) */
+  int32_t precond;        /* a kc_precond_kind.  gmres_solve: KC_PREC_AUTO = none,
+                             KC_PREC_JACOBI = right Jacobi preconditioning (precision 0;
+                             solved by fgmres_solve, A a CSR matrix); fgmres_solve: below */
   int32_t diag_loo;       /* gmres_solve diagnostics: 1 = after every (inner) cycle form the
                              Gram matrix of the n (or, at an early stop, ncols) columns that
                              formed its correction (kc_basis_gram) and report the largest

@@ -283,12 +283,13 @@ def mgs_arnoldi_step(ctx: Context, A: DeviceCSR, st: ArnoldiState):
 
 def gmres_solve(ctx: Context, A: DeviceCSR, b, x, restart=30, rtol=1e-10, maxit=100000,
                 precision=0, A32: DeviceCSR = None, max_outer=50, inner_rtol=1e-4,
-                inner_max_cycles=3, diag_loo=False):
+                inner_max_cycles=3, diag_loo=False, precond: int = 0):
     """Restarted DCGS2-GMRES (precision 0) or FP32 / BF16-basis inner solves in FP64
     iterative refinement (precision 1 / 2).  x holds x0 and receives the solution.
-    diag_loo: also report the largest loss of orthogonality over the cycles' bases."""
+    diag_loo: also report the largest loss of orthogonality over the cycles' bases.
+    precond: PREC_AUTO (none) or PREC_JACOBI (right Jacobi, precision 0)."""
     opts = kc_gmres_opts(restart, maxit, precision, max_outer, rtol, inner_rtol,
-                         inner_max_cycles, 0, 1 if diag_loo else 0)
+                         inner_max_cycles, precond, 1 if diag_loo else 0)
     info = kc_gmres_info()
     a32 = C.byref(A32.c) if A32 is not None else None
     st = ctx.lib.gmres_solve(ctx.handle, C.byref(A.c), a32, _ptr(b), _ptr(x), C.byref(opts),

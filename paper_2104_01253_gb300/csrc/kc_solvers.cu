@@ -221,6 +221,15 @@ kc_status gmres_solve(kc_ctx* ctx, const kc_csr* A, const kc_csr* A32, const dou
   if (n < 1 || n + 1 > NMAX) return fail(ctx, KC_ERR_INVALID_ARG, "restart must be in [1, %d]", NMAX - 1);
   const int prec = opts->precision;
   if (prec < 0 || prec > 2) return fail(ctx, KC_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
+  if (opts->precond == KC_PREC_JACOBI) {
+    // right Jacobi preconditioning: M = D^{-1} is linear, so flexible GMRES with it is
+    // GMRES on A D^{-1}; the flexible solver stores the preconditioned basis it needs
+    if (prec != 0)
+      return fail(ctx, KC_ERR_INVALID_ARG, "the Jacobi preconditioner needs precision 0");
+    return fgmres_solve(ctx, A, nullptr, 0, 0, b, x, opts, info);
+  }
+  if (opts->precond != KC_PREC_AUTO)
+    return fail(ctx, KC_ERR_INVALID_ARG, "unknown preconditioner kind %d", opts->precond);
   if (prec > 0) {
     if ((s = validate_csr(ctx, A32)) != KC_OK) return s;
     if (A32->val_dtype != KC_F32 || A32->m != A->m)

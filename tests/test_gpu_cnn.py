@@ -361,6 +361,31 @@ def test_fgmres_jacobi_matches_oracle(kc, ctx):
     assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
 
 
+def test_gmres_solve_jacobi_option(kc, ctx):
+    """gmres_solve with precond=PREC_JACOBI is right Jacobi-preconditioned GMRES: the same
+    solve as fgmres_solve with the Jacobi step (same iteration count, same x to rounding),
+    against the oracle's Jacobi-preconditioned GMRES; with an FP32 inner solve it is an
+    invalid argument."""
+    Ah = _varcoef(32, 66)
+    b = gaussian_vector(Ah.m, 73)
+    A = kc.DeviceCSR(Ah)
+    bd = torch.as_tensor(b, device="cuda")
+    x1, x2 = torch.zeros_like(bd), torch.zeros_like(bd)
+    i1 = kc.gmres_solve(ctx, A, bd, x1, restart=40, rtol=1e-10, precond=kc.PREC_JACOBI)
+    i2 = kc.fgmres_solve(ctx, A, None, 32, 32, bd, x2, restart=40, rtol=1e-10,
+                         precond=kc.PREC_JACOBI)
+    assert i1["status"] == 0 and i1["rel_resid_true"] <= 1e-10
+    assert i1["iters"] == i2["iters"]
+    assert torch.equal(x1, x2)
+    dinv = cnn.inverse_diagonal(Ah.to_scipy())
+    xo, io = orc_gmres(Ah.to_scipy(), b, restart=40, rtol=1e-10, precond=lambda w: w * dinv)
+    assert abs(io["iters"] - i1["iters"]) <= 1
+    assert np.linalg.norm(x1.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-8
+    with pytest.raises(kc.KrylovError):
+        kc.gmres_solve(ctx, A, bd, torch.zeros_like(bd), restart=40, precision=1,
+                       A32=kc.DeviceCSR(Ah, dtype=torch.float32), precond=kc.PREC_JACOBI)
+
+
 def test_fgmres_with_network_converges(kc, ctx):
     """A perturbed linear network (net(x) ~ -x / 2) in the Jacobi-scaled preconditioner is
     nonlinear: flexible GMRES must reach 1e-10 with an iteration count close to the
