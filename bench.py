@@ -15,7 +15,11 @@ Measurement suites (one GPU, one JSON line each; not the benchmark line):
                                  [--matrix-free] [--restart n] [--reps 3]
       one restarted GMRES solve to 1e-10, wall time and device time by kernel kind;
   python bench.py --suite cnn    [--N 1024] [--batch 1] [--conv 0|1] [--forward 20] [--train 5]
-      the learned preconditioner's forward pass and training step.
+      the learned preconditioner's forward pass and training step;
+  python bench.py --suite learn  [--N 1024]
+      config 5 as a study: learning curve, held-out operators 64-71, extrapolated baselines;
+  python bench.py --suite part   [--N 252] [--n 50]
+      the row-partitioned expansion with P = 1, 2, 4 ranks emulated on one GPU.
 
 Under torchrun each rank runs an independent replica of the workload on its own GPU
 (weak scaling, no data-path collective); rank 0 prints one JSON line.  The reference arm
@@ -72,7 +76,8 @@ def parse():
                         "default: the library's")
     p.add_argument("--no-check", action="store_true",
                    help="skip the loss-of-orthogonality / Arnoldi-relation check")
-    p.add_argument("--suite", default=None, choices=["steps", "solver", "cnn", "learn"],
+    p.add_argument("--suite", default=None,
+                   choices=["steps", "solver", "cnn", "learn", "part"],
                    help="a measurement suite instead of the benchmark line (module docstring)")
     p.add_argument("--modes", type=int, nargs="+", default=[1], choices=[0, 1, 2])
     p.add_argument("--basis", default="f64", choices=["f64", "f32", "bf16"])
@@ -771,6 +776,82 @@ def suite_learn(args):
     print(json.dumps(out), flush=True)
 
 
+def suite_part(args):
+    """The row-partitioned DCGS2 expansion (Section 4's layout) with P ranks emulated on one
+    GPU: each rank has its own context, rows of A (columns re-based onto its halo-extended
+    range of w), basis rows and state; per step every rank runs dcgs2_part_reduce on its
+    halo-extended w, the partial sums are added on the device (standing in for the
+    all-reduce), and every rank runs dcgs2_part_update.  The ranks' kernels are timed with
+    per-launch CUDA events (the halo assembly and the sum are PyTorch copies outside that
+    time).  Reported per P: each rank's kernel time per expansion and their maximum, which
+    is the P-GPU expansion time without communication, against the unpartitioned step."""
+    import torch
+    import paper_2104_01253_gb300 as kc
+    from paper_2104_01253_gb300 import partitioned as pt
+    import synth
+    Ah = synth.config2_operator(args.N)
+    r0 = synth.gaussian_vector(Ah.m, 1002)
+    n = args.n
+    out = {"suite": "part", "m": Ah.m, "n": n, "points": []}
+    for P in (1, 2, 4):
+        blocks = pt.row_blocks(Ah.m, P)
+        ranks = []
+        for lo, hi in blocks:
+            rp, ci, va, glo, ghi = pt.local_rows(Ah.row_ptr, Ah.col_idx, Ah.val, lo, hi)
+            ctx = kc.Context(0)
+            ranks.append((ctx, kc.DeviceCSR(synth.CSR(hi - lo, rp, ci, va)),
+                          kc.ArnoldiState(hi - lo, n + 1, kc.KC_F64), lo, hi, glo, ghi))
+
+        def expansion():
+            for ctx, A_l, st, lo, hi, _, _ in ranks:
+                kc.dcgs2_arnoldi_init(ctx, A_l, st, torch.as_tensor(r0[lo:hi], device="cuda"))
+            for k in range(n):
+                parts = []
+                for ctx, A_l, st, lo, hi, glo, ghi in ranks:
+                    pieces = [ranks[q][2].w[max(a, glo) - a:min(b, ghi) - a]
+                              for q, (a, b) in enumerate(blocks) if max(a, glo) < min(b, ghi)]
+                    part = torch.empty(2 * k + 2, dtype=torch.float64, device="cuda")
+                    kc.dcgs2_part_reduce(ctx, A_l, st, torch.cat(pieces), part)
+                    parts.append(part)
+                tot = torch.stack(parts).sum(0)
+                for ctx, A_l, st, _, _, _, _ in ranks:
+                    kc.dcgs2_part_update(ctx, A_l, st, tot)
+
+        expansion()
+        torch.cuda.synchronize()
+        for r in ranks:
+            r[0].timing_enable(True)
+        expansion()
+        torch.cuda.synchronize()
+        per_rank = []
+        for r in ranks:
+            t = r[0].timing_read()
+            r[0].timing_enable(False)
+            per_rank.append(sum(v[0] for v in t.values()))
+        status = [r[0].read_status() for r in ranks]
+        out["points"].append({"P": P, "rows_per_rank": [hi - lo for lo, hi in blocks],
+                              "kernel_ms_per_rank": per_rank,
+                              "kernel_ms_max": max(per_rank),
+                              "steps_per_s_without_communication": n / (max(per_rank) / 1e3),
+                              "status": status})
+        del ranks
+        torch.cuda.synchronize()
+    ctx = kc.Context(0)
+    A = kc.DeviceCSR(Ah)
+    st = kc.ArnoldiState(Ah.m, n + 1, kc.KC_F64)
+    rd = torch.as_tensor(r0, device="cuda")
+    for timed in (False, True):
+        ctx.timing_enable(timed)
+        kc.dcgs2_arnoldi_init(ctx, A, st, rd)
+        for _ in range(n):
+            kc.dcgs2_arnoldi_step(ctx, A, st)
+        torch.cuda.synchronize()
+    t = ctx.timing_read()
+    ctx.timing_enable(False)
+    out["unpartitioned_kernel_ms"] = sum(v[0] for v in t.values())
+    print(json.dumps(out), flush=True)
+
+
 def suite_cnn(args):
     """kc_cnn_forward and kc_cnn_train_step (regression loss, no Adam update) on a seeded
     random batch of N x N images with He-initialised weights, after two warm-up calls of
@@ -820,7 +901,7 @@ def main():
         if args.suite == "cnn" and args.N == 252:
             args.N = 1024
         return {"steps": suite_steps, "solver": suite_solver, "cnn": suite_cnn,
-                "learn": suite_learn}[args.suite](args)
+                "learn": suite_learn, "part": suite_part}[args.suite](args)
     if args.impl == "reference":
         return run_reference(args, ws, rank)
 
