@@ -777,7 +777,7 @@ def suite_learn(args):
 
 
 def suite_part(args):
-    """The row-partitioned DCGS2 expansion (Section 4's layout) with P ranks emulated on one
+    """The row-partitioned DCGS2 expansion (Section 5's layout) with P ranks emulated on one
     GPU: each rank has its own context, rows of A (columns re-based onto its halo-extended
     range of w), basis rows and state; per step every rank runs dcgs2_part_reduce on its
     halo-extended w, the partial sums are added on the device (standing in for the

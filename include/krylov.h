@@ -59,7 +59,7 @@ typedef struct kc_ctx kc_ctx;
  *              + c5 x_{i-nx ny} + c6 x_{i+nx ny},   stencil = {c0, ..., c6},
  *    each neighbour term present only when that neighbour lies in the grid.  This is the
  *    constant-coefficient form of the h^2-scaled upwind convection-diffusion operators
- *    (2D with nz = 1) and of the Manteuffel matrix of Section 5.1; with it the basis
+ *    (2D with nz = 1) and of the Manteuffel matrix of Section 6.1; with it the basis
  *    generation v = A w of Algorithm 4 reads w once and writes v once instead of streaming
  *    the matrix.  val_dtype KC_F64: FP64 vectors, seven FP64 FMAs per row in both FP64
  *    modes (an error in v, unlike one in S or Q C, is not removed by the next
@@ -215,7 +215,7 @@ kc_status dcgs2_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 
 /* Gram matrix of a basis, G = Q^T Q, for the loss of orthogonality ||I - Q^T Q||_F
- * (Section 5.1).  Q: device, column-major with leading dimension ldq >= m, ncols columns
+ * (Section 6.1).  Q: device, column-major with leading dimension ldq >= m, ncols columns
  * (1 <= ncols <= 128) of type q_dtype (KC_F64, KC_F32 or KC_BF16); G: device FP64,
  * ncols x ncols column-major, overwritten, exactly symmetric.  Products and sums in FP64;
  * the per-block sums are combined with atomics, so the last bits of G may vary from call
@@ -224,10 +224,10 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st);
 kc_status kc_basis_gram(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, int64_t m,
                         int ncols, double* G);
 
-/* ---- row-partitioned DCGS2 (Section 4; Tables 1-2: rows split across processes) ---------
+/* ---- row-partitioned DCGS2 (Section 5; Tables 1-2: rows split across processes) ---------
  * The distributed layout of the paper: rank p owns a contiguous block of m_p rows of A, Q,
  * w and v, and every step makes ONE global sum of its 2k + 2 partial dot products (the
- * MPI_Allreduce of Section 4); the small scalar step is replicated.  These calls are the
+ * MPI_Allreduce of Section 5); the small scalar step is replicated.  These calls are the
  * per-rank work of one GPU; the caller sums the partials over the ranks (NCCL or any other
  * collective: the library makes none) and supplies the halo of w for the matvec.
  *   A_local: the rank's m_p rows in CSR form (FP64 values), its column indices pointing
@@ -300,7 +300,7 @@ kc_status dcgs2_noalloc_read_status(int* status, void* cuda_stream);
 kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, double* Q,
                    int64_t ldq, double* R, int ldr);
 
-/* ICWY-MGS (Section 6): MGS with its rank-1 projections batched into the inverse compact
+/* ICWY-MGS (Section 5): MGS with its rank-1 projections batched into the inverse compact
  * WY projector I - Q T Q^T, T = (I + L)^{-1} with L the strictly lower triangular part of
  * Q^T Q, one reduction per iteration (the fused reduction [Q_k, w]^T [w, A w] of the DCGS2
  * step: its C gives row k of L, beta the norm of the pending w, S and s the projections),
@@ -356,7 +356,7 @@ typedef struct {
   double rel_resid_est;   /* last Givens estimate |g_k| / ||b|| */
   double rel_resid_true;  /* FP64 ||b - A x|| / ||b|| recomputed on the device */
   double max_loo;         /* largest ||I - Q^T Q||_F over the cycles' bases when
-                             kc_gmres_opts.diag_loo is set, else -1 (Section 5.1 metric) */
+                             kc_gmres_opts.diag_loo is set, else -1 (Section 6.1 metric) */
 } kc_gmres_info;
 
 /* Restarted DCGS2-GMRES(n) (FP64), or FP32/BF16-basis DCGS2-GMRES inside FP64 iterative
@@ -420,7 +420,7 @@ kc_status kc_cnn_train_step_residual(kc_ctx* ctx, float* w32, float* adam_m, flo
                                      double* loss);
 
 /* One training sample of the residual loss from the current iterate of a solve (the
- * (residual, correction) pairs of Section 7, the correction left implicit):
+ * (residual, correction) pairs, the correction left implicit):
  *   r = b - A x,  u = D^{-1} r,  s = rms(u) = sqrt(u^T u / m),
  *   xin = u / s,  res = r / s   (FP32, m each, device),
  * D = diag(A) as in fgmres_solve.  A: FP64 CSR (device); b, x: FP64 device vectors of

@@ -8,7 +8,7 @@ generators in ``synth`` serve both).
 Modules
   arnoldi       DCGS2-Arnoldi (Algorithm 4), CGS2-Arnoldi (Algorithm 3), MGS-Arnoldi,
                 DCGS2-QR (Algorithm 2), CGS2-QR (Algorithm 1)
-  metrics       loss of orthogonality and Arnoldi representation error (Section 5.1)
+  metrics       loss of orthogonality and Arnoldi representation error (Section 6.1)
   gmres         restarted GMRES / FGMRES on DCGS2-Arnoldi, FP32 / BF16-basis inner solves
                 inside FP64 iterative refinement
   krylov_schur  Krylov-Schur eigenvalues (Stewart) on DCGS2-Arnoldi, Arnoldi residual test

@@ -12,7 +12,7 @@ diagonal-matrix Lanczos case, and the Manteuffel spectrum through Krylov-Schur.
 The QR variants (tests/test_oracle_stability.py): the loss-of-orthogonality classes of
 Table 3 over graded condition numbers (CGS eps kappa^2, MGS eps kappa, CGS2 and DCGS2 at
 O(eps)), the representation error at O(eps), agreement with Householder QR.  ICWY-MGS
-(Section 6): the MGS class eps kappa of Table 3's level-2 MGS row, equality with MGS level 1
+(Section 5): the MGS class eps kappa of Table 3's level-2 MGS row, equality with MGS level 1
 in exact arithmetic (agreement on well-conditioned inputs), an exact Arnoldi relation, and
 planted mistakes (no L correction, L transposed) that leave its class.
 """
@@ -260,7 +260,7 @@ def _forward_solve_unit_lower(L, r):
 
 
 def icwy_qr(B):
-    """ICWY-MGS QR of B (Section 6): the inverse compact WY projector
+    """ICWY-MGS QR of B (Section 5): the inverse compact WY projector
     P a = (I - Q T Q^T) a with T = (I + L)^{-1}, L strictly lower triangular whose row i
     holds the inner products q_i^T q_{0:i-1} (the strictly lower part of Q^T Q).  One
     reduction per column: at iteration j (j >= 1) the single reduction
@@ -294,7 +294,7 @@ def icwy_qr(B):
 
 
 def icwy_arnoldi(A, r0, n: int):
-    """ICWY-MGS Arnoldi (Section 6's projector in the Arnoldi expansion, one reduction per
+    """ICWY-MGS Arnoldi (Section 5's projector in the Arnoldi expansion, one reduction per
     step).  The pending vector w is the projected, unnormalised A q_{k-1} (w = r0 at the
     start); step k applies A to w (v = A w, so A q_k = v / alpha), and its one reduction
     [Q_k, w]^T [w, v] gives C = Q_k^T w, S = Q_k^T v, beta = w^T w and s = w^T v.  Then

@@ -1,7 +1,7 @@
 """Krylov-Schur eigenvalues on DCGS2-Arnoldi (test infrastructure only).
 
 Stewart's Krylov-Schur restart (cited in Section 1; used for the Manteuffel experiments of
-Section 5.1): expand a Krylov decomposition A Q_n = Q_n B + q_n b^T to n = ncv columns with
+Section 6.1): expand a Krylov decomposition A Q_n = Q_n B + q_n b^T to n = ncv columns with
 DCGS2 steps, take the real Schur form B = Z T Z^T ordered so that the wanted Ritz values
 (largest real part) lead, test each wanted Ritz pair by its Arnoldi residual
 ||(A - lambda I) Q Z y|| = |b^T Z y| (eq. "ArnoldiRes"), keep p columns

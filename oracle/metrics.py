@@ -1,4 +1,4 @@
-"""Stability metrics of Section 5.1 (test infrastructure only).
+"""Stability metrics of Section 6.1 (test infrastructure only).
 
 loo: loss of orthogonality ||I - Q^T Q||_F.
 rre: relative representation error ||A Q_{:,0:n} - Q H||_F / ||A||_F (Arnoldi relation).

@@ -1,5 +1,5 @@
 """Row-partitioned DCGS2 Arnoldi (Algorithm 4) over P ranks, the paper's distributed
-layout (Section 4: Q, w, v and the rows of A split by rows across processes, one global
+layout (Section 5: Q, w, v and the rows of A split by rows across processes, one global
 reduction per step), written as an oracle so that the partition can be checked on CPU
 ranks (torch.distributed with the gloo backend) against the sequential oracle.
 

@@ -18,7 +18,7 @@ same definition, built independently so that one checks the other:
 Pins (tests/test_oracle_stencil.py): the two statements agree; a loop over every row of a
 tiny grid (the definition read literally) agrees with both; the stencil generators in
 ``synth`` reproduce ``synth.convdiff_csr`` and ``synth.manteuffel_csr`` entry for entry;
-the Manteuffel stencil has the closed-form spectrum of Section 5.1.
+the Manteuffel stencil has the closed-form spectrum of Section 6.1.
 """
 from __future__ import annotations
 

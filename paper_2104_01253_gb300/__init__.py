@@ -220,7 +220,7 @@ def dcgs2_qr(ctx: Context, A, Q, R):
 
 
 def icwy_qr(ctx: Context, A, Q, R):
-    """ICWY-MGS QR (Section 6) in the layout of dcgs2_qr."""
+    """ICWY-MGS QR (Section 5) in the layout of dcgs2_qr."""
     n, m = A.shape
     ctx.check(ctx.lib.icwy_qr(ctx.handle, _ptr(A), A.stride(0), m, n, _ptr(Q), Q.stride(0),
                               _ptr(R), R.stride(0)))

@@ -322,7 +322,7 @@ kc_status dcgs2_arnoldi_finish(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {
   return KC_OK;
 }
 
-// ---- row-partitioned DCGS2 (Section 4: rows of Q, w, v and A split across ranks) -----
+// ---- row-partitioned DCGS2 (Section 5: rows of Q, w, v and A split across ranks) -----
 
 static kc_status part_checks(kc_ctx* ctx, const kc_csr* A, const kc_arnoldi* st) {
   if (st->q_dtype != KC_F64)
@@ -455,7 +455,7 @@ kc_status dcgs2_qr(kc_ctx* ctx, const double* A, int64_t lda, int64_t m, int n, 
   return KC_OK;
 }
 
-// ---- ICWY-MGS (Section 6): the fused reduction with the ICWY epilogue, then the DCGS2
+// ---- ICWY-MGS (Section 5): the fused reduction with the ICWY epilogue, then the DCGS2
 // update with C = 0 (q_k = w / alpha, w <- v / alpha - Q_{k+1} y) -------------------------
 
 kc_status icwy_arnoldi_step(kc_ctx* ctx, const kc_csr* A, kc_arnoldi* st) {

@@ -1,5 +1,5 @@
 // Gram matrix of a tall-skinny basis, G = Q^T Q in FP64, and the loss of orthogonality
-// ||I - Q^T Q||_F derived from it (the stability metric of Section 5.1).  A diagnostic:
+// ||I - Q^T Q||_F derived from it (the stability metric of Section 6.1).  A diagnostic:
 // gmres_solve uses it to report the worst loss of orthogonality over its (inner) cycles
 // when kc_gmres_opts.diag_loo is set, and kc_basis_gram exposes it to callers.
 //

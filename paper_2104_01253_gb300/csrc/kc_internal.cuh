@@ -85,7 +85,7 @@ enum Epilogue : int {
   EPI_STORE_C2 = 2,     // store Q^T x into C2
   EPI_STORE_S = 3,      // store Q^T x into S (CGS2 first projection)
   EPI_PARTIAL = 4,      // row-partitioned step: store the (k + 1) x NRHS sums to sa.part
-  EPI_ICWY = 5,         // ICWY-MGS step (Section 6): norm, row of L, triangular solve
+  EPI_ICWY = 5,         // ICWY-MGS step (Section 5): norm, row of L, triangular solve
   EPI_STORE_C1 = 6,     // store Q^T x into C as a first projection, whose error a second
                         // projection removes: the offload reduction may sum it in
                         // float-float (CGS2 finish first pass)

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(256) k_stencil7(const T* __restrict__ x, T* __
   if (DOTS) store_dots(ab, as, dots);
 }
 
-// The ICWY-MGS step (Section 6) from the summed [C, S, beta, s] of the fused reduction
+// The ICWY-MGS step (Section 5) from the summed [C, S, beta, s] of the fused reduction
 // (all threads of one CTA): alpha = sqrt(beta) = ||w|| normalises the pending w into q_k
 // (H(k, k-1) = alpha), row k of the strictly lower triangular L is C / alpha (stored in the
 // K workspace, K(k, i)), and the projection coefficients of the next vector are
@@ -2335,7 +2335,7 @@ kc_status launch_axpy_h(kc_ctx* ctx, const void* q, int q_dtype, void* v, int64_
 }  // namespace kc
 
 // ----------------------------------------------------------------------------------------
-// Row-partitioned DCGS2 (Section 4's distributed layout): each rank owns a block of rows of
+// Row-partitioned DCGS2 (Section 5's distributed layout): each rank owns a block of rows of
 // Q, w, v and A; its reduction stores its partial sums (EPI_PARTIAL), the caller sums them
 // over the ranks (the one global reduction of the step), and the kernels below continue
 // from those sums.  The scalar step runs redundantly on every rank on identical sums, so

@@ -1,4 +1,4 @@
-"""Row-partitioned DCGS2 Arnoldi over several ranks (Section 4, Tables 1-2: the rows of A,
+"""Row-partitioned DCGS2 Arnoldi over several ranks (Section 5, Tables 1-2: the rows of A,
 Q, w and v split across processes, one global sum of 2k + 2 numbers per step).
 
 The per-rank GPU work is libkrylov's dcgs2_part_reduce / dcgs2_part_update /

@@ -1,7 +1,7 @@
 """Synthetic sparse operators in CSR form (int32 indices, float64 values).
 
 The paper's own Krylov experiments use the Manteuffel "central differences" matrix
-(Section 5.1, its eigenvalue formula) and SuiteSparse / 3D Laplace problems that are not
+(Section 6.1, its eigenvalue formula) and SuiteSparse / 3D Laplace problems that are not
 available here.  The throughput workloads are therefore convection-diffusion operators
 
     -div(kappa grad u) + b . grad u      on (0,1)^d, homogeneous Dirichlet boundary,
@@ -126,7 +126,7 @@ def convdiff_csr(N: int, dim: int, wind, kappa=None) -> CSR:
 
 
 def manteuffel_csr(k: int, beta: float = 0.5) -> CSR:
-    """Manteuffel's central-difference matrix on a k x k grid with h = 1 (Section 5.1).
+    """Manteuffel's central-difference matrix on a k x k grid with h = 1 (Section 6.1).
 
     A = I (x) T + T (x) I with T = tridiag(-1 - beta/2, 2, -1 + beta/2): the 5-point
     Laplacian M plus (beta/2) times the skew-symmetric centred first difference N.  Its

@@ -7,7 +7,7 @@ FP64 modes there, on the config-2 operator family (3D upwind convection-diffusio
 along (1, 0.5, 0.25), Peclet 50) at N = 162 (m = 4,251,528), start vector N(0,1) seed
 1002.  Tolerances as in the other DCGS2 parity tests: H to 1e-12 relative (Frobenius),
 basis entries to 1e-10 absolute, loss of orthogonality and representation error at
-O(eps) (Section 5.1).  The oracle run (about 20 s of host time) is shared by the modes.
+O(eps) (Section 6.1).  The oracle run (about 20 s of host time) is shared by the modes.
 """
 import numpy as np
 import pytest

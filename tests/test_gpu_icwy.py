@@ -1,4 +1,4 @@
-"""GPU parity of ICWY-MGS (Section 6: the inverse compact WY projector with
+"""GPU parity of ICWY-MGS (Section 5: the inverse compact WY projector with
 T = (I + L)^{-1}, one reduction per iteration) against the FP64 oracle: the Arnoldi
 expansion (H to 1e-12 relative, basis to 1e-10, exact Arnoldi relation) and the QR of
 given columns (elementwise on a well-conditioned matrix; on ill-conditioned ones the loss

@@ -51,7 +51,7 @@ def test_ks_small_copy_matches_dense_and_oracle(kc, ctx):
 
 
 def test_ks_manteuffel_closed_form(kc, ctx):
-    """Distinct largest Manteuffel eigenvalues from the closed form (Section 5.1)."""
+    """Distinct largest Manteuffel eigenvalues from the closed form (Section 6.1)."""
     k, beta = 20, 0.5
     Ah = manteuffel_csr(k, beta)
     v0 = gaussian_vector(Ah.m, 8)

@@ -1,5 +1,5 @@
 """GPU parity of the row-partitioned DCGS2 step (dcgs2_part_reduce / dcgs2_part_update /
-dcgs2_part_finish, Section 4's layout) against the FP64 oracle.
+dcgs2_part_finish, Section 5's layout) against the FP64 oracle.
 
 One GPU is available, so the ranks are emulated: (1) in one process, P ranks with their
 own contexts and row blocks, whose partial sums are added on the device between the

@@ -21,7 +21,7 @@ def mant():
 
 @pytest.mark.parametrize("variant", [orc.dcgs2_arnoldi, orc.cgs2_arnoldi, orc.mgs_arnoldi])
 def test_arnoldi_relation(mant, variant):
-    """A Q_n = Q_{n+1} H_n to O(eps) (eq. "arnoldi"; RRE of Section 5.1)."""
+    """A Q_n = Q_{n+1} H_n to O(eps) (eq. "arnoldi"; RRE of Section 6.1)."""
     r0 = gaussian_vector(mant.shape[0], 1)
     Q, H = variant(mant, r0, 40)
     assert rre(mant, Q, H) < 1e-15
@@ -39,7 +39,7 @@ def test_loss_of_orthogonality_eps(mant, variant, bound):
 
 
 def test_mgs_loses_more_orthogonality_than_dcgs2():
-    """MGS loses orthogonality like eps*kappa, DCGS2 stays at eps (Table 3, Section 5.1)."""
+    """MGS loses orthogonality like eps*kappa, DCGS2 stays at eps (Table 3, Section 6.1)."""
     A = manteuffel_csr(30).to_scipy()
     r0 = gaussian_vector(A.shape[0], 3)
     Qm, _ = orc.mgs_arnoldi(A, r0, 80)

@@ -1,4 +1,4 @@
-"""Pins of the ICWY-MGS oracle (Section 6: the inverse compact WY projector
+"""Pins of the ICWY-MGS oracle (Section 5: the inverse compact WY projector
 I - Q (I + L)^{-1} Q^T, one reduction per iteration).  In exact arithmetic the projector
 is the product of MGS's rank-1 projections, so ICWY-MGS is MGS (agreement on
 well-conditioned inputs, against MGS level 1 and Householder QR); in floating point it

@@ -18,7 +18,7 @@ def test_ks_matches_dense_eigenvalues_on_small_copy():
 
 
 def test_ks_manteuffel_closed_form():
-    """Largest distinct Manteuffel eigenvalues from the closed form (Section 5.1)."""
+    """Largest distinct Manteuffel eigenvalues from the closed form (Section 6.1)."""
     k, beta = 20, 0.5
     A = manteuffel_csr(k, beta).to_scipy()
     res = krylov_schur(A, gaussian_vector(A.shape[0], 8), nev=4, ncv=30, nkeep=15, tol=1e-10)

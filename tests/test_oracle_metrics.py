@@ -1,4 +1,4 @@
-"""Pins of the stability metrics of Section 5.1 (CPU only).
+"""Pins of the stability metrics of Section 6.1 (CPU only).
 
 loo(Q) = ||I - Q^T Q||_F and rre(A, Q, H) = ||A Q_{:,0:n} - Q H||_F / ||A||_F are checked
 on inputs whose values are known in closed form, so that a wrong normaliser (2-norm

@@ -1,6 +1,6 @@
 """Pins of the stencil oracle (CPU): the two statements of the definition against each
 other and against a literal loop, the generators in synth against the CSR generators, and
-the Manteuffel stencil against its closed-form spectrum (Section 5.1)."""
+the Manteuffel stencil against its closed-form spectrum (Section 6.1)."""
 import numpy as np
 import pytest
 
@@ -86,7 +86,7 @@ def test_manteuffel_stencil_matrix_and_spectrum():
     B = stencil7_matrix(st.grid, st.c)
     B.eliminate_zeros()
     assert (synth.manteuffel_csr(k, beta).to_scipy() != B).nnz == 0
-    # Section 5.1: 2 [2 - sqrt(1 - (beta/2)^2) (cos(l pi/(k+1)) + cos(j pi/(k+1)))]
+    # Section 6.1: 2 [2 - sqrt(1 - (beta/2)^2) (cos(l pi/(k+1)) + cos(j pi/(k+1)))]
     t = np.cos(np.arange(1, k + 1) * np.pi / (k + 1))
     exact = np.sort((2 * (2 - np.sqrt(1 - (beta / 2) ** 2) * (t[:, None] + t[None, :]))).ravel())
     ev = np.linalg.eigvals(B.toarray())

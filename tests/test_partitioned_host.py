@@ -1,6 +1,6 @@
 """Host side of the row-partitioned DCGS2 (paper_2104_01253_gb300.partitioned) on CPU gloo
 ranks: each rank's local CSR rows with re-based columns and its halo of w, assembled by
-point-to-point messages, give exactly its rows of A w (Section 4's layout: rows of A and
+point-to-point messages, give exactly its rows of A w (Section 5's layout: rows of A and
 of the vectors split across processes).  Includes a partition whose halo reaches past the
 neighbouring rank."""
 import os

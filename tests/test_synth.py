@@ -21,7 +21,7 @@ def _golden():
 
 
 def test_manteuffel_matches_printed_table():
-    """Table "stab_manteuffel" (Section 5.1): ||A||_2, cond(A) and non-normality, k = 50."""
+    """Table "stab_manteuffel" (Section 6.1): ||A||_2, cond(A) and non-normality, k = 50."""
     g = _golden()
     A = manteuffel_csr(50).to_scipy().toarray()
     s = np.linalg.svd(A, compute_uv=False)
@@ -32,7 +32,7 @@ def test_manteuffel_matches_printed_table():
 
 
 def test_manteuffel_closed_form_spectrum():
-    """Eigenvalues 2[2 - sqrt(1-(beta/2)^2)(cos(l pi/L) + cos(j pi/L))], L = k+1 (Section 5.1)."""
+    """Eigenvalues 2[2 - sqrt(1-(beta/2)^2)(cos(l pi/L) + cos(j pi/L))], L = k+1 (Section 6.1)."""
     k, beta = 9, 0.5
     A = manteuffel_csr(k, beta).to_scipy().toarray()
     L = k + 1
