@@ -18,6 +18,7 @@ namespace kc {
 constexpr int NMAX = 128;            // largest basis (ncap) any kernel supports
 constexpr int RED_THREADS = 512;     // threads of a reduction CTA (16 warps)
 constexpr int RED_WARPS = RED_THREADS / 32;
+constexpr int RED_RSUB_TASKS = 8;    // FP32 / BF16 reductions of at most this many tasks: row sub-blocks
 constexpr int PARTIAL_CTAS_PER_SM = 16;  // reduction CTAs per SM the partials buffer holds
                                           // (16 two-warp CTAs stream w and v at k = 0: 90 us
                                           // instead of 121 with 8, at m = 16 M)

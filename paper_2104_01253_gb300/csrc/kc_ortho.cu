@@ -507,6 +507,9 @@ __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int 
 // Warp w owns tasks w, w+16, w+32, ... (TPW of them) and keeps their partial sums in
 // registers over all of the CTA's rows; the 16 warps of a CTA walk the same rows, so
 // x and y are read from HBM once and served from L1 to the other warps.
+// With rsub > 1 (a few tasks: one slot, nw = ntask task warps) the CTA's warps form rsub
+// row sub-blocks: each walks its share of the CTA's rows with the whole task set, and the
+// sub-block sums are added in shared memory in sub-block order.
 // The last CTA to finish sums the partials in CTA order (deterministic) and runs the
 // epilogue: the scalar step of Algorithm 4 or a plain store.
 // ----------------------------------------------------------------------------------------
@@ -515,14 +518,16 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
          const TV* __restrict__ y, int64_t m, double* __restrict__ partials,
          unsigned int* __restrict__ counter, Scalars* __restrict__ sc, int epilogue,
-         StepArgs sa) {
+         StepArgs sa, int rsub) {
   using TA = typename Acc<TV>::T;
   constexpr int R = Grp<TV>::R;
+  pdl_wait();
   if (sc->stop) return;
   // (one- to three-slot launches size their CTAs to the task count; a compile-time warp
   // count keeps the four- and eight-slot variants within 64 registers)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nw = TPW <= 3 ? (int)(blockDim.x >> 5) : RED_WARPS;
+  const int nw = TPW <= 3 ? (int)(blockDim.x >> 5) / rsub : RED_WARPS;
+  const int wt = warp % nw, rs = warp / nw;        // task warp, row sub-block
   const int ntask = k + 1;
   TA acc[TPW][NRHS];
 #pragma unroll
@@ -531,8 +536,9 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
     for (int r = 0; r < NRHS; r++) acc[i][r] = 0;
 
   const int64_t ngroups = m / R;
-  const int64_t g0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
-  const int64_t g1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * ngroups / gridDim.x;
+  const int64_t b1 = (int64_t)(blockIdx.x + 1) * ngroups / gridDim.x;
+  const int64_t g0 = b0 + (b1 - b0) * rs / rsub, g1 = b0 + (b1 - b0) * (rs + 1) / rsub;
   int64_t g = g0 + lane;
   // FP32 / BF16 vectors (HBM-bound): two row groups per iteration, every load issued
   // before the arithmetic, so twice the bytes are in flight per warp
@@ -545,7 +551,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
       TA qa[TPW][R], qb[TPW][R];
 #pragma unroll
       for (int i = 0; i < TPW; i++) {
-        const int t = warp + nw * i;
+        const int t = wt + nw * i;
         if (t < k) {
           load_q(Q + (int64_t)t * ldq, g, qa[i]);
           load_q(Q + (int64_t)t * ldq, g + 32, qb[i]);
@@ -556,7 +562,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
       }
 #pragma unroll
       for (int i = 0; i < TPW; i++) {
-        if (warp + nw * i >= ntask) continue;
+        if (wt + nw * i >= ntask) continue;
 #pragma unroll
         for (int r = 0; r < R; r++) {
           acc[i][0] += qa[i][r] * (TA)xa[r];
@@ -575,7 +581,7 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
     if (NRHS == 2) ldv(y, g, yv);
 #pragma unroll
     for (int i = 0; i < TPW; i++) {
-      const int t = warp + nw * i;
+      const int t = wt + nw * i;
       if (t < ntask) {
         TA qv[R];
         if (t < k) {
@@ -592,14 +598,14 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
       }
     }
   }
-  // ragged tail: rows ngroups*R .. m-1, taken by the last CTA's warps
-  if (blockIdx.x == gridDim.x - 1) {
+  // ragged tail: rows ngroups*R .. m-1, taken by the last CTA's first row sub-block
+  if (blockIdx.x == gridDim.x - 1 && rs == 0) {
     for (int64_t row = ngroups * R + lane; row < m; row += 32) {
       TA xs = (TA)__ldcg(x + row);
       TA ys = NRHS == 2 ? (TA)__ldcg(y + row) : (TA)0;
 #pragma unroll
       for (int i = 0; i < TPW; i++) {
-        const int t = warp + nw * i;
+        const int t = wt + nw * i;
         if (t < ntask) {
           TA q = t < k ? (TA)ld1(Q + (int64_t)t * ldq, row) : xs;
           acc[i][0] += q * xs;
@@ -608,15 +614,39 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
       }
     }
   }
+  double sum[TPW][NRHS];
 #pragma unroll
-  for (int i = 0; i < TPW; i++) {
-    const int t = warp + nw * i;
+  for (int i = 0; i < TPW; i++)
 #pragma unroll
-    for (int r = 0; r < NRHS; r++) {
-      double v = (double)warp_sum(acc[i][r]);
-      if (lane == 0 && t < ntask) partials[(int64_t)blockIdx.x * PSTRIDE + t * NRHS + r] = v;
-    }
+    for (int r = 0; r < NRHS; r++) sum[i][r] = (double)warp_sum(acc[i][r]);
+  __shared__ double red[RED_WARPS][TPW][NRHS];     // sub-block sums (rsub > 1)
+  if (rsub > 1) {
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < TPW; i++)
+#pragma unroll
+        for (int r = 0; r < NRHS; r++) red[warp][i][r] = sum[i][r];
+    __syncthreads();
+    if (rs == 0)
+#pragma unroll
+      for (int i = 0; i < TPW; i++)
+#pragma unroll
+        for (int r = 0; r < NRHS; r++) {
+          double t = red[wt][i][r];
+          for (int q = 1; q < rsub; q++) t += red[q * nw + wt][i][r];
+          sum[i][r] = t;
+        }
   }
+  if (rs == 0 && lane == 0)
+#pragma unroll
+    for (int i = 0; i < TPW; i++) {
+      const int t = wt + nw * i;
+      if (t < ntask)
+#pragma unroll
+        for (int r = 0; r < NRHS; r++)
+          partials[(int64_t)blockIdx.x * PSTRIDE + t * NRHS + r] = sum[i][r];
+    }
+  pdl_trigger();
   if (!last_cta(counter)) return;
   reduce_epilogue(partials, k, NRHS, sc, epilogue, sa);
 }
@@ -632,6 +662,7 @@ k_dcgs2_update(TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ w,
                const TV* __restrict__ v, int64_t m, const Scalars* __restrict__ sc) {
   using TA = typename Acc<TV>::T;
   constexpr int R = Grp<TV>::R;
+  pdl_wait();
   if (sc->stop) return;
   __shared__ TA sC[NMAX], sT[NMAX + 1];
   for (int i = threadIdx.x; i <= k; i += blockDim.x) {
@@ -681,6 +712,7 @@ k_dcgs2_update(TQ* __restrict__ Q, int64_t ldq, int k, TV* __restrict__ w,
     for (int r = 0; r < R; r++) wo[r] = (TV)(wn[r] - qn[r] * sT[k]);
     stv(w, g, wo);
   }
+  pdl_trigger();
   // ragged tail
   if (blockIdx.x == 0) {
     for (int64_t row = ngroups * R + threadIdx.x; row < m; row += blockDim.x) {
@@ -1899,20 +1931,24 @@ kc_status launch_spmv(kc_ctx* ctx, const kc_csr* A, const void* x, void* y, int 
     if (vec_dtype == KC_F64) {
       Stencil7<double> c;
       for (int i = 0; i < 7; i++) c.c[i] = A->stencil[i];
-      k_stencil7<double><<<grid, 256, 0, ctx->stream>>>((const double*)x, (double*)y, nx, ny,
-                                                        nz, c, ctx->scal);
+      KC_CUDA(ctx, launch_pdl(ctx->stream, k_stencil7<double>, grid, 256, 0, (const double*)x,
+                              (double*)y, nx, ny, nz, c, (const Scalars*)ctx->scal,
+                              (double*)nullptr));
     } else {
       Stencil7<float> c;
       for (int i = 0; i < 7; i++) c.c[i] = (float)A->stencil[i];
-      k_stencil7<float><<<grid, 256, 0, ctx->stream>>>((const float*)x, (float*)y, nx, ny, nz,
-                                                       c, ctx->scal);
+      KC_CUDA(ctx, launch_pdl(ctx->stream, k_stencil7<float>, grid, 256, 0, (const float*)x,
+                              (float*)y, nx, ny, nz, c, (const Scalars*)ctx->scal,
+                              (double*)nullptr));
     }
   } else if (A->val_dtype == KC_F64 && vec_dtype == KC_F64)
-    k_spmv<double, double><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
-        (const double*)A->val, (const double*)x, (double*)y, A->m, ctx->scal);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_spmv<double, double>, grid, 256, 0, A->row_ptr,
+                            A->col_idx, (const double*)A->val, (const double*)x, (double*)y,
+                            A->m, (const Scalars*)ctx->scal, (double*)nullptr));
   else if (A->val_dtype == KC_F32 && vec_dtype == KC_F32)
-    k_spmv<float, float><<<grid, 256, 0, ctx->stream>>>(A->row_ptr, A->col_idx,
-        (const float*)A->val, (const float*)x, (float*)y, A->m, ctx->scal);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_spmv<float, float>, grid, 256, 0, A->row_ptr,
+                            A->col_idx, (const float*)A->val, (const float*)x, (float*)y, A->m,
+                            (const Scalars*)ctx->scal, (double*)nullptr));
   KC_LAUNCHED(ctx);
   return KC_OK;
 }
@@ -1943,8 +1979,9 @@ kc_status launch_spmv_dots(kc_ctx* ctx, const kc_csr* A, const void* x, void* y,
 }
 
 template <typename TQ, typename TV, int NRHS>
-static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int k,
-                            const TV* x, const TV* y, int64_t m, int epi, const StepArgs& sa) {
+static kc_status reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int k,
+                                 const TV* x, const TV* y, int64_t m, int epi,
+                                 const StepArgs& sa) {
   const int ntask = k + 1;
   // Few tasks: one warp per task and as many CTAs per SM as fit, so that every SM streams
   // many row ranges at once (16 warps sharing one row range left most of them idle with one
@@ -1952,38 +1989,46 @@ static void reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq, int
   // this way); measured faster up to 10 tasks, while from 13 to 16 the 2 x 16-warp layout
   // is ahead.  17-32 and 33-48 tasks: two or three slots per warp in ceil(ntask / slots)
   // warps, so that no warp carries more columns than the others (17 tasks on 16 warps ran
-  // at half pace).
-  int nw = RED_WARPS;
-  const int slots = ntask <= 10 ? 1 : (ntask <= RED_WARPS ? 0 : (ntask <= 2 * RED_WARPS ? 2 : (ntask <= 3 * RED_WARPS ? 3 : 0)));
+  // at half pace).  FP32 / BF16 vectors with at most RED_RSUB_TASKS tasks: CTAs of
+  // RED_WARPS / ntask row sub-blocks of ntask warps, so that each SM holds as many warps
+  // with loads in flight while the partials (and the last CTA's sums over them) stay few.
+  int nw = RED_WARPS, rsub = 1;
+  const bool split = sizeof(TV) == 4 && ntask <= RED_RSUB_TASKS;
+  const int slots = split ? 1 : (ntask <= 10 ? 1 : (ntask <= RED_WARPS ? 0 : (ntask <= 2 * RED_WARPS ? 2 : (ntask <= 3 * RED_WARPS ? 3 : 0))));
   if (slots) {
     nw = (ntask + slots - 1) / slots;
+    if (split) rsub = RED_WARPS / ntask;
+    const int nwc = nw * rsub;                    // warps per CTA
     static int occ[4][RED_WARPS + 1];             // resident CTAs per SM, by slots and warps
-    int& o = occ[slots][nw];
+    int& o = occ[slots][nwc];
     if (o == 0) {
       int n = 0;
       const cudaError_t e =
-          slots == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 1, NRHS>, 32 * nw, 0)
-          : slots == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 2, NRHS>, 32 * nw, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 3, NRHS>, 32 * nw, 0);
+          slots == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 1, NRHS>, 32 * nwc, 0)
+          : slots == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 2, NRHS>, 32 * nwc, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_reduce<TQ, TV, 3, NRHS>, 32 * nwc, 0);
       if (e != cudaSuccess || n < 1) n = 1;
       o = n;
     }
     const int cps = o < PARTIAL_CTAS_PER_SM ? o : PARTIAL_CTAS_PER_SM;
     const int64_t ngroups = m / Grp<TV>::R;
-    int64_t b = (ngroups + 32 * 4 - 1) / (32 * 4);
+    int64_t b = (ngroups + 32 * 4 * rsub - 1) / (32 * 4 * rsub);   // >= 4 groups per lane
     const int64_t cap = (int64_t)ctx->num_sms * cps;
     if (b > cap) b = cap;
     grid = (int)(b < 1 ? 1 : b);
   }
+  cudaError_t le = cudaSuccess;
   auto args = [&](auto kern) {
-    kern<<<grid, 32 * nw, 0, ctx->stream>>>(Q, ldq, k, x, y, m, ctx->partials,
-                                            ctx->counters, ctx->scal, epi, sa);
+    le = launch_pdl(ctx->stream, kern, grid, 32 * nw * rsub, 0, Q, ldq, k, x, y, m,
+                    ctx->partials, ctx->counters, ctx->scal, epi, sa, rsub);
   };
   if (ntask <= RED_WARPS) args(k_reduce<TQ, TV, 1, NRHS>);
   else if (ntask <= 2 * RED_WARPS) args(k_reduce<TQ, TV, 2, NRHS>);
   else if (ntask <= 3 * RED_WARPS) args(k_reduce<TQ, TV, 3, NRHS>);
   else if (ntask <= 4 * RED_WARPS) args(k_reduce<TQ, TV, 4, NRHS>);
   else args(k_reduce<TQ, TV, 8, NRHS>);
+  KC_CUDA(ctx, le);
+  return KC_OK;
 }
 
 // Task layout of the offload reduction for ntask equal tasks (the DCGS2 step: k + 2; the
@@ -2195,14 +2240,14 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
       else go(k_reduce1_f64<3, 2, false>);
     }
   } else if (q_dtype == KC_F64 && vec_dtype == KC_F64) {
-    if (two) reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa);
-    else reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa);
+    if (two) KC_TRY((reduce_dispatch<double, double, 2>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, (const double*)y, m, epilogue, sa)));
+    else KC_TRY((reduce_dispatch<double, double, 1>(ctx, grid, (const double*)Q, ldq, k, (const double*)x, nullptr, m, epilogue, sa)));
   } else if (q_dtype == KC_F32 && vec_dtype == KC_F32) {
-    if (two) reduce_dispatch<float, float, 2>(ctx, grid, (const float*)Q, ldq, k, (const float*)x, (const float*)y, m, epilogue, sa);
-    else reduce_dispatch<float, float, 1>(ctx, grid, (const float*)Q, ldq, k, (const float*)x, nullptr, m, epilogue, sa);
+    if (two) KC_TRY((reduce_dispatch<float, float, 2>(ctx, grid, (const float*)Q, ldq, k, (const float*)x, (const float*)y, m, epilogue, sa)));
+    else KC_TRY((reduce_dispatch<float, float, 1>(ctx, grid, (const float*)Q, ldq, k, (const float*)x, nullptr, m, epilogue, sa)));
   } else {
-    if (two) reduce_dispatch<__nv_bfloat16, float, 2>(ctx, grid, (const __nv_bfloat16*)Q, ldq, k, (const float*)x, (const float*)y, m, epilogue, sa);
-    else reduce_dispatch<__nv_bfloat16, float, 1>(ctx, grid, (const __nv_bfloat16*)Q, ldq, k, (const float*)x, nullptr, m, epilogue, sa);
+    if (two) KC_TRY((reduce_dispatch<__nv_bfloat16, float, 2>(ctx, grid, (const __nv_bfloat16*)Q, ldq, k, (const float*)x, (const float*)y, m, epilogue, sa)));
+    else KC_TRY((reduce_dispatch<__nv_bfloat16, float, 1>(ctx, grid, (const __nv_bfloat16*)Q, ldq, k, (const float*)x, nullptr, m, epilogue, sa)));
   }
   KC_LAUNCHED(ctx);
   return KC_OK;
@@ -2221,11 +2266,17 @@ kc_status launch_dcgs2_update(kc_ctx* ctx, void* Q, int64_t ldq, int q_dtype, in
                             ldq, k, (double*)w, (const double*)v, m,
                             (const Scalars*)ctx->scal, !(ctx->staged & 4)));
   else if (q_dtype == KC_F64)
-    k_dcgs2_update<double, double><<<grid, UPD_THREADS, 0, ctx->stream>>>((double*)Q, ldq, k, (double*)w, (const double*)v, m, ctx->scal);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_dcgs2_update<double, double>, grid, UPD_THREADS, 0,
+                            (double*)Q, ldq, k, (double*)w, (const double*)v, m,
+                            (const Scalars*)ctx->scal));
   else if (q_dtype == KC_F32)
-    k_dcgs2_update<float, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((float*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_dcgs2_update<float, float>, grid, UPD_THREADS, 0,
+                            (float*)Q, ldq, k, (float*)w, (const float*)v, m,
+                            (const Scalars*)ctx->scal));
   else
-    k_dcgs2_update<__nv_bfloat16, float><<<grid, UPD_THREADS, 0, ctx->stream>>>((__nv_bfloat16*)Q, ldq, k, (float*)w, (const float*)v, m, ctx->scal);
+    KC_CUDA(ctx, launch_pdl(ctx->stream, k_dcgs2_update<__nv_bfloat16, float>, grid,
+                            UPD_THREADS, 0, (__nv_bfloat16*)Q, ldq, k, (float*)w,
+                            (const float*)v, m, (const Scalars*)ctx->scal));
   KC_LAUNCHED(ctx);
   return KC_OK;
 }
@@ -2478,7 +2529,7 @@ extern "C" kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st,
   const int ntask = k + 1;
   auto go = [&](auto kern) {
     kern<<<grid, RED_THREADS, 0, stream>>>(Q, st->ldq, k, w, v, m, scr->partials, scr->counter,
-                                           &scr->sc, (int)EPI_DCGS2, sa);
+                                           &scr->sc, (int)EPI_DCGS2, sa, 1);
   };
   if (ntask <= RED_WARPS) go(k_reduce<double, double, 1, 2>);
   else if (ntask <= 2 * RED_WARPS) go(k_reduce<double, double, 2, 2>);
