@@ -129,15 +129,17 @@ kc_status kc_create(kc_ctx** out, int device, void* cuda_stream) {
   ctx->reduce_grid = 2 * p.multiProcessorCount;
   const size_t plen =
       (size_t)PARTIAL_CTAS_PER_SM * p.multiProcessorCount * (2 * NMAX + 4) * sizeof(double);
+  // 16 ticket counters, then one per group of RED_GROUP partials rows (group_counters)
+  const size_t ncount = 16 + ((size_t)PARTIAL_CTAS_PER_SM * p.multiProcessorCount + RED_GROUP - 1) / RED_GROUP;
   bool ok = cudaMalloc(&ctx->partials, plen) == cudaSuccess &&
             cudaMalloc(&ctx->dots, (size_t)16 * p.multiProcessorCount * sizeof(double)) ==
                 cudaSuccess &&
-            cudaMalloc(&ctx->counters, 16 * sizeof(unsigned int)) == cudaSuccess &&
+            cudaMalloc(&ctx->counters, ncount * sizeof(unsigned int)) == cudaSuccess &&
             cudaMalloc(&ctx->scal, sizeof(Scalars)) == cudaSuccess &&
             cudaMallocHost(&ctx->scal_host, sizeof(Scalars)) == cudaSuccess;
   ctx->dwork_len = 1 << 20;
   ok = ok && cudaMalloc(&ctx->dwork, ctx->dwork_len * sizeof(double)) == cudaSuccess;
-  if (ok) ok = cudaMemset(ctx->counters, 0, 16 * sizeof(unsigned int)) == cudaSuccess &&
+  if (ok) ok = cudaMemset(ctx->counters, 0, ncount * sizeof(unsigned int)) == cudaSuccess &&
                cudaMemset(ctx->scal, 0, sizeof(Scalars)) == cudaSuccess &&
                cudaDeviceSynchronize() == cudaSuccess;
   if (!ok) {

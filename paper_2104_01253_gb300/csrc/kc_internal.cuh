@@ -19,6 +19,7 @@ constexpr int NMAX = 128;            // largest basis (ncap) any kernel supports
 constexpr int RED_THREADS = 512;     // threads of a reduction CTA (16 warps)
 constexpr int RED_WARPS = RED_THREADS / 32;
 constexpr int RED_RSUB_TASKS = 8;    // FP32 / BF16 reductions of at most this many tasks: row sub-blocks
+constexpr int RED_GROUP = 16;        // partials rows per group of a two-level reduction completion
 constexpr int PARTIAL_CTAS_PER_SM = 16;  // reduction CTAs per SM the partials buffer holds
                                           // (16 two-warp CTAs stream w and v at k = 0: 90 us
                                           // instead of 121 with 8, at m = 16 M)
@@ -145,7 +146,8 @@ struct kc_ctx {
   int dots_pending;        // CTAs whose pairs the next reduction of (dots_x, dots_y) takes
   const void* dots_x;
   const void* dots_y;
-  unsigned int* counters;  // ticket counters for last-CTA reductions
+  unsigned int* counters;  // ticket counters for last-CTA reductions (16), then the
+                           // group counters of two-level completions (group_counters)
   kc::Scalars* scal;       // device scalars
   kc::Scalars* scal_host;  // pinned host mirror for reads
   double* dwork;           // general FP64 device workspace (small dense solves)
@@ -288,6 +290,8 @@ kc_status cnn_adam(kc_ctx* ctx, float* w, const float* g, float* m, float* v, in
 int64_t cnn_nparam();
 // the operator is the matrix-free 7-point stencil rather than a CSR matrix
 inline bool is_stencil(const kc_csr* A) { return A->grid[0] > 0; }
+// the group counters of the two-level reduction completion (tree_arrive)
+inline unsigned int* group_counters(kc_ctx* ctx) { return ctx->counters + 16; }
 
 // Programmatic dependent launch (griddepcontrol) for the kernels of the DCGS2 step, which
 // follow one another on the stream without a host synchronisation.  A kernel launched with

@@ -175,6 +175,62 @@ __device__ __forceinline__ bool last_cta(unsigned int* counter) {
   return true;
 }
 
+// Column sums of a short nrows x nval table (row c at base + c * stride) into tot[0:nval]
+// in a fixed order, by every thread of the CTA (no barrier inside): P threads per value
+// (aligned lane groups, P = 8, 4, 2 or 1 as the CTA allows), each adding every P-th row in
+// row order, their sums combined by a fixed xor tree.  Against sum_rows this issues about
+// one FP64 add per table entry instead of the warp tree's five per lane and value, which
+// matters on the one SM that runs a reduction's last steps (two FP64 adds per clock).
+__device__ void sum_cols(const double* __restrict__ base, int nrows, int64_t stride, int nval,
+                         double* tot) {
+  const int nt = (int)blockDim.x;
+  const int P = nval * 8 <= nt ? 8 : (nval * 4 <= nt ? 4 : (nval * 2 <= nt ? 2 : 1));
+  for (int b = 0; b < nval; b += nt / P) {                   // uniform over the CTA
+    const int v = b + (int)threadIdx.x / P, sub = (int)threadIdx.x % P;
+    double acc = 0.0;
+    if (v < nval) {
+#pragma unroll 4
+      for (int c = sub; c < nrows; c += P) acc += __ldcg(base + (int64_t)c * stride + v);
+    }
+    for (int o = P / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (v < nval && sub == 0) tot[v] = acc;
+  }
+}
+
+// Two-level completion of a reduction whose CTAs wrote rows 0..nr-1 of the partials
+// (cpr CTAs per row, each writing its own entries of the row; CTA b belongs to row
+// b / cpr).  Rows form groups of RED_GROUP; the last CTA of a group to arrive (counted in
+// gcount[group]) sums the group's rows in row order into the group's first row, and the
+// last group to finish (counted in *counter) returns true in every thread of its CTA.
+// The final sums then take ceil(nr / RED_GROUP) rows (stride RED_GROUP rows) instead of
+// nr, and the groups' sums run on many SMs while the other CTAs still stream.
+__device__ __noinline__ bool tree_arrive(double* __restrict__ partials, int nr, int cpr, int nval,
+                            unsigned int* counter, unsigned int* gcount) {
+  __shared__ unsigned int ticket;
+  const int r = (int)blockIdx.x / cpr, g = r / RED_GROUP;
+  const int r0 = g * RED_GROUP, r1 = r0 + RED_GROUP < nr ? r0 + RED_GROUP : nr;
+  const int ng = (nr + RED_GROUP - 1) / RED_GROUP;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(gcount + g, 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)((r1 - r0) * cpr - 1)) return false;
+  __threadfence();
+  if (r1 - r0 > 1) {
+    double* row0 = partials + (int64_t)r0 * PSTRIDE;
+    sum_cols(row0, r1 - r0, PSTRIDE, nval, row0);             // in place (per value)
+  }
+  if (threadIdx.x == 0) gcount[g] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned int)(ng - 1)) return false;
+  __threadfence();
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
 __device__ __forceinline__ void set_status(Scalars* sc, int st) {
   if (sc->status == KC_OK) sc->status = st;
 }
@@ -502,6 +558,17 @@ __device__ void reduce_epilogue(const double* __restrict__ partials, int k, int 
   epilogue_from_tot(tot, k, NRHS, sc, epilogue, sa);
 }
 
+// Last CTA of a two-level reduction (tree_arrive over nr partials rows): the fixed-order
+// sums of the group rows, then the epilogue.
+__device__ void tree_epilogue(const double* __restrict__ partials, int nr, int k, int NRHS,
+                              Scalars* __restrict__ sc, int epilogue, const StepArgs& sa) {
+  __shared__ double tot[PSTRIDE];
+  sum_cols(partials, (nr + RED_GROUP - 1) / RED_GROUP, (int64_t)RED_GROUP * PSTRIDE,
+           (k + 1) * NRHS, tot);
+  __syncthreads();
+  epilogue_from_tot(tot, k, NRHS, sc, epilogue, sa);
+}
+
 // ----------------------------------------------------------------------------------------
 // K1': fused reduction.  Tasks t = 0..k-1 are Q(:,t)^T [x, y]; task k is x^T [x, y].
 // Warp w owns tasks w, w+16, w+32, ... (TPW of them) and keeps their partial sums in
@@ -518,7 +585,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
          const TV* __restrict__ y, int64_t m, double* __restrict__ partials,
          unsigned int* __restrict__ counter, Scalars* __restrict__ sc, int epilogue,
-         StepArgs sa, int rsub) {
+         StepArgs sa, int rsub, unsigned int* __restrict__ gcount) {
   using TA = typename Acc<TV>::T;
   constexpr int R = Grp<TV>::R;
   pdl_wait();
@@ -647,6 +714,11 @@ k_reduce(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restrict__ x,
           partials[(int64_t)blockIdx.x * PSTRIDE + t * NRHS + r] = sum[i][r];
     }
   pdl_trigger();
+  if (gcount) {                                   // two-level completion
+    if (!tree_arrive(partials, (int)gridDim.x, 1, ntask * NRHS, counter, gcount)) return;
+    tree_epilogue(partials, (int)gridDim.x, k, NRHS, sc, epilogue, sa);
+    return;
+  }
   if (!last_cta(counter)) return;
   reduce_epilogue(partials, k, NRHS, sc, epilogue, sa);
 }
@@ -933,6 +1005,23 @@ __device__ __forceinline__ void f64x_load(const double* const (&ap)[TPW], int64_
     if (ap[i]) load_q(ap[i], g, av[i]);
 }
 
+// beta and s from the SpMV (one warp): row block r of nr adds its share of the SpMV CTAs'
+// sums (in CTA order) into dst[0] and dst[1] of its partials row, so that the final sums
+// take them with the columns
+__device__ __noinline__ void add_dots(double* __restrict__ dst, const double* __restrict__ dots,
+                                      int r, int nr, int ndots) {
+  const int lane = threadIdx.x & 31;
+  const int c0 = (int)((int64_t)r * ndots / nr), c1 = (int)((int64_t)(r + 1) * ndots / nr);
+  double ab = 0.0, as = 0.0;
+  for (int c = c0 + lane; c < c1; c += 32) {
+    ab += __ldcg(dots + 2 * c);
+    as += __ldcg(dots + 2 * c + 1);
+  }
+  ab = warp_sum(ab);
+  as = warp_sum(as);
+  if (lane == 0) { dst[0] = ab; dst[1] = as; }
+}
+
 // most warps of a row-split offload reduction CTA (rsub > 1); the task counts that take
 // the row split on long vectors, and the warps per CTA it aims at
 constexpr int F64X_RSUB_MAXW = 16;
@@ -956,7 +1045,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
               const double* __restrict__ y, int64_t m, double* __restrict__ partials,
               unsigned int* __restrict__ counter, Scalars* __restrict__ sc, StepArgs sa,
               int nsplit, int nt, int epi, const double* __restrict__ dots, int ndots,
-              int rsub) {
+              int rsub, unsigned int* __restrict__ gcount) {
   pdl_wait();
   if (sc->stop) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1046,7 +1135,7 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
       }
   }
   if (rs == 0 && lane == 0) {
-    double* pp = partials + (int64_t)r * PSTRIDE;    // row block r: one writer per task
+    double* pp = partials + (int64_t)r * PSTRIDE;    // row block r: one writer per entry
 #pragma unroll
     for (int i = 0; i < TPW; i++) {
       const int t = tk[i];
@@ -1055,9 +1144,10 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
       else pp[2 * k + (t - k)] = cv[i];       // beta -> [2k], s -> [2k + 1]
     }
   }
+  if (ndots && h == 0 && warp == 0) add_dots(partials + (int64_t)r * PSTRIDE + 2 * k, dots, r, nr, ndots);
   pdl_trigger();
-  if (!last_cta(counter)) return;
-  reduce_epilogue(partials, k, 2, sc, epi, sa, nr, dots, ndots);
+  if (!tree_arrive(partials, nr, nsplit, 2 * k + 2, counter, gcount)) return;
+  tree_epilogue(partials, nr, k, 2, sc, epi, sa);
 }
 
 // The first DCGS2 steps in one pass (k <= FUSE_KMAX basis columns, FP64 offload mode): one
@@ -2020,7 +2110,8 @@ static kc_status reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq
   cudaError_t le = cudaSuccess;
   auto args = [&](auto kern) {
     le = launch_pdl(ctx->stream, kern, grid, 32 * nw * rsub, 0, Q, ldq, k, x, y, m,
-                    ctx->partials, ctx->counters, ctx->scal, epi, sa, rsub);
+                    ctx->partials, ctx->counters, ctx->scal, epi, sa, rsub,
+                    group_counters(ctx));
   };
   if (ntask <= RED_WARPS) args(k_reduce<TQ, TV, 1, NRHS>);
   else if (ntask <= 2 * RED_WARPS) args(k_reduce<TQ, TV, 2, NRHS>);
@@ -2206,7 +2297,8 @@ kc_status launch_reduce(kc_ctx* ctx, const void* Q, int64_t ldq, int q_dtype, in
       le = launch_pdl(ctx->stream, kern, g, 32 * nw, 0, (const double*)Q, ldq, k,
                       (const double*)x, (const double*)y, m, ctx->partials, ctx->counters,
                       ctx->scal, sa, nsplit, nt, epilogue,
-                      (const double*)(ndots ? ctx->dots : nullptr), ndots, rsub);
+                      (const double*)(ndots ? ctx->dots : nullptr), ndots, rsub,
+                      group_counters(ctx));
     };
     if (tpw == 1) go(k_reduce_f64x<1, 2>);
     else if (tpw == 2) go(k_reduce_f64x<2, 2>);
@@ -2529,7 +2621,8 @@ extern "C" kc_status dcgs2_arnoldi_step_noalloc(const kc_csr* A, kc_arnoldi* st,
   const int ntask = k + 1;
   auto go = [&](auto kern) {
     kern<<<grid, RED_THREADS, 0, stream>>>(Q, st->ldq, k, w, v, m, scr->partials, scr->counter,
-                                           &scr->sc, (int)EPI_DCGS2, sa, 1);
+                                           &scr->sc, (int)EPI_DCGS2, sa, 1,
+                                           (unsigned int*)nullptr);
   };
   if (ntask <= RED_WARPS) go(k_reduce<double, double, 1, 2>);
   else if (ntask <= 2 * RED_WARPS) go(k_reduce<double, double, 2, 2>);
