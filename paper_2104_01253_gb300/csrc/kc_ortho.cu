@@ -109,6 +109,30 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Sums of V values (V a power of two, at most 32) over the 32 lanes of a warp in one
+// butterfly.  At each of the first log2 V levels a lane keeps half of its values and adds
+// its partner's copies of them (V - 1 adds in all), then the remaining levels add the one
+// value left: V - 1 + 5 - log2 V adds per lane against 5 V for V separate trees, which counts
+// where FP64 adds issue at two per clock per SM.  Lane l ends with the total of value
+// l & (V - 1) in x[0], in a fixed order (bitwise the same in every lane that holds it).
+template <int V>
+__device__ __forceinline__ double warp_sum_multi(double (&x)[V]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = V / 2; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;               // this lane keeps the upper half
+#pragma unroll
+    for (int i = 0; i < h; i++) {
+      const double send = up ? x[i] : x[i + h];
+      const double keep = up ? x[i + h] : x[i];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+#pragma unroll
+  for (int o = V; o < 32; o <<= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+  return x[0];
+}
+
 // Column sums of an nrows x nval table (row c at base + c * stride) in a fixed order
 // (deterministic) into tot[0:nval], by every thread of the CTA (it synchronises; tot may
 // be read after a further __syncthreads).  The last CTA of a reduction runs this while
@@ -311,16 +335,15 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
 // CTA sums of x^T x and x^T y (FP64, fixed order) into dots[2 b], dots[2 b + 1]
 __device__ __forceinline__ void store_dots(double ab, double as, double* dots) {
   __shared__ double red[2][8];
-  ab = warp_sum(ab);
-  as = warp_sum(as);
+  double x[2] = {ab, as};
+  const double v = warp_sum_multi<2>(x);          // lane 0: x^T x, lane 1: x^T y
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { red[0][warp] = ab; red[1][warp] = as; }
+  if (lane < 2) red[lane][warp] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = 0.0, t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) { b += red[0][i]; t += red[1][i]; }
-    dots[2 * blockIdx.x] = b;
-    dots[2 * blockIdx.x + 1] = t;
+  if (threadIdx.x < 2) {
+    double b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) b += red[threadIdx.x][i];
+    dots[2 * blockIdx.x + threadIdx.x] = b;
   }
 }
 
@@ -1113,36 +1136,31 @@ k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __
       }
     }
   }
-  __shared__ double red[F64X_RSUB_MAXW][TPW][2];  // sub-block sums (rsub > 1)
-  double cv[TPW], svv[TPW];
+  // the warp's 2 TPW sums in one butterfly: value 2 i is C (or beta, s) of slot i, 2 i + 1
+  // its S; lane l < 2 TPW ends with value l
+  constexpr int V = TPW == 1 ? 2 : (TPW == 2 ? 4 : 8);
+  double xs[V];
 #pragma unroll
-  for (int i = 0; i < TPW; i++) {
-    cv[i] = warp_sum(ac[i]);
-    svv[i] = warp_sum(as64[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])));
+  for (int i = 0; i < V / 2; i++) {
+    xs[2 * i] = i < TPW ? ac[i] : 0.0;
+    xs[2 * i + 1] = i < TPW ? as64[i] + (f2d_bits(sh[i]) + f2d_bits(sl[i])) : 0.0;
   }
+  double mine = warp_sum_multi<V>(xs);
+  __shared__ double red[F64X_RSUB_MAXW][2 * TPW];   // sub-block sums (rsub > 1)
   if (rsub > 1) {
-    if (lane == 0)
-#pragma unroll
-      for (int i = 0; i < TPW; i++) { red[warp][i][0] = cv[i]; red[warp][i][1] = svv[i]; }
+    if (lane < 2 * TPW) red[warp][lane] = mine;
     __syncthreads();
-    if (rs == 0)
-#pragma unroll
-      for (int i = 0; i < TPW; i++) {
-        double c = red[wt][i][0], sv = red[wt][i][1];
-        for (int q = 1; q < rsub; q++) { c += red[q * nw + wt][i][0]; sv += red[q * nw + wt][i][1]; }
-        cv[i] = c;
-        svv[i] = sv;
-      }
+    if (rs == 0 && lane < 2 * TPW)
+      for (int q = 1; q < rsub; q++) mine += red[q * nw + wt][lane];
   }
-  if (rs == 0 && lane == 0) {
-    double* pp = partials + (int64_t)r * PSTRIDE;    // row block r: one writer per entry
+  if (rs == 0 && lane < 2 * TPW) {
+    int t = k + 2;                                   // the task of slot lane / 2
 #pragma unroll
-    for (int i = 0; i < TPW; i++) {
-      const int t = tk[i];
-      if (t > k + 1) continue;
-      if (t < k) { pp[2 * t] = cv[i]; pp[2 * t + 1] = svv[i]; }
-      else pp[2 * k + (t - k)] = cv[i];       // beta -> [2k], s -> [2k + 1]
-    }
+    for (int i = 0; i < TPW; i++)
+      if ((lane >> 1) == i) t = tk[i];
+    double* pp = partials + (int64_t)r * PSTRIDE;    // row block r: one writer per entry
+    if (t < k) pp[2 * t + (lane & 1)] = mine;
+    else if (t <= k + 1 && (lane & 1) == 0) pp[2 * k + (t - k)] = mine;   // beta, s
   }
   if (ndots && h == 0 && warp == 0) add_dots(partials + (int64_t)r * PSTRIDE + 2 * k, dots, r, nr, ndots);
   pdl_trigger();
