@@ -259,33 +259,42 @@ __device__ __forceinline__ void set_status(Scalars* sc, int st) {
   if (sc->status == KC_OK) sc->status = st;
 }
 
-// The scalar step of Algorithm 4 after alpha is known (all threads of one CTA).
-// Inputs in sc: C (C_{0:k-1}), S (raw S_{0:k-1} = Q_k^T v), s (= w^T v), cs (= C^T S).
+// The scalar step of Algorithm 4 after alpha is known (all threads of one CTA), with
+// inva = 1 / alpha.  Inputs: C (C_{0:k-1}) and S (raw S_{0:k-1} = Q_k^T v) from tot
+// (tot[2i], tot[2i+1], shared memory) or, without tot, from sc; s (= w^T v), cs (= C^T S)
+// from sc.
 //   T_{0:k-1} = S/alpha, T_k = (s - C^T S)/alpha^2 (eq. 30);
 //   H(0:k, k-1) = K(0:k, k-1) + C, H(k, k-1) = alpha;
 //   K(0:k, k) = T - H(0:k, 0:k-1) C / alpha (the flexible variant keeps K = T);
 //   GMRES: Givens rotation of the finalised column k-1.
-__device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha) {
+__device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha,
+                            double inva, const double* tot = nullptr) {
   // The last CTA runs this once per step, so its dependent FP64 chains (about 70 cycles a
-  // link) are on the step's critical path: C, the finalised H column and the Givens state
-  // are staged in shared memory first, the column norm is a warp sum, and the K-column
-  // products unroll their loads.
-  __shared__ double s_c[NMAX], s_h[NMAX + 2], s_gc[NMAX], s_gs[NMAX];
+  // link) are on the step's critical path: C, T, the finalised H column and the Givens
+  // state are staged in shared memory, the divisions by alpha are products with its
+  // reciprocal (computed beside the square root), the breakdown test compares squares, and
+  // the K-column products unroll their loads.
+  __shared__ double s_c[NMAX], s_h[NMAX + 2], s_gc[NMAX], s_gs[NMAX], s_t[NMAX + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool qr = (sa.flags & SF_QR) != 0;
   if (threadIdx.x == 0) {
     sc->alpha = alpha;
-    sc->inv_alpha = 1.0 / alpha;
-    const bool qr = (sa.flags & SF_QR) != 0;
-    sc->vscale = qr ? 1.0 : 1.0 / alpha;
-    sc->T[k] = qr ? (sc->s - sc->cs) / alpha : (sc->s - sc->cs) / (alpha * alpha);
+    sc->inv_alpha = inva;
+    sc->vscale = qr ? 1.0 : inva;
+    const double tk = qr ? (sc->s - sc->cs) * inva : (sc->s - sc->cs) * inva * inva;
+    sc->T[k] = tk;
+    s_t[k] = tk;
     if ((sa.flags & SF_GIVENS) && k == 0) { sc->g[0] = alpha; sc->ncols = 0; }
-    if (sa.flags & SF_FLEXIBLE) sc->zscale[k] = 1.0 / alpha;
+    if (sa.flags & SF_FLEXIBLE) sc->zscale[k] = inva;
     if (k >= 1 || qr) sa.H[k + (int64_t)(k - 1) * sa.ldh] = alpha;
     s_h[k] = alpha;
   }
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double c = sc->C[i];
-    sc->T[i] = (sa.flags & SF_QR) ? sc->S[i] : sc->S[i] / alpha;
+    const double c = tot ? tot[2 * i] : sc->C[i];
+    const double si = tot ? tot[2 * i + 1] : sc->S[i];
+    const double t = qr ? si : si * inva;
+    sc->T[i] = t;
+    s_t[i] = t;
     const double h = sa.K[i + (int64_t)(k - 1) * sa.ldk] + c;
     sa.H[i + (int64_t)(k - 1) * sa.ldh] = h;
     s_c[i] = c;
@@ -297,7 +306,7 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
     double cn = 0.0;
     for (int i = lane; i <= k; i += 32) cn += s_h[i] * s_h[i];
     cn = warp_sum(cn);
-    if (lane == 0 && alpha <= 1e-13 * sqrt(cn)) set_status(sc, KC_ERR_BREAKDOWN);
+    if (lane == 0 && alpha * alpha <= 1e-26 * cn) set_status(sc, KC_ERR_BREAKDOWN);
   }
   // K(i, k) = T_i - H(i, 0:k-1) C / alpha for i <= k: P lanes per row (aligned groups of a
   // warp), each over every P-th column, added by a fixed xor tree, so that each thread has
@@ -314,7 +323,7 @@ __device__ void scalar_step(Scalars* sc, const StepArgs& sa, int k, double alpha
         for (int j = sub; j < k; j += P) hc += sa.H[i + (int64_t)j * sa.ldh] * s_c[j];
       }
       for (int o = P / 2; o > 0; o >>= 1) hc += __shfl_xor_sync(0xffffffffu, hc, o);
-      if (i <= k && sub == 0) sa.K[i + (int64_t)k * sa.ldk] = sc->T[i] - hc / alpha;
+      if (i <= k && sub == 0) sa.K[i + (int64_t)k * sa.ldk] = s_t[i] - hc * inva;
     }
   }
   if (threadIdx.x == 0 && (sa.flags & SF_GIVENS) && k >= 1) {
@@ -500,7 +509,7 @@ __device__ void icwy_step(const double* tot, int k, Scalars* __restrict__ sc,
 // ICWY-MGS step, or the scalar step of Algorithm 4.
 __device__ void epilogue_from_tot(const double* tot, int k, int NRHS, Scalars* __restrict__ sc,
                                   int epilogue, const StepArgs& sa) {
-  __shared__ double s_alpha;
+  __shared__ double s_alpha, s_inva;
   const int nval = (k + 1) * NRHS;
   if (epilogue == EPI_PARTIAL) {
     for (int i = threadIdx.x; i < nval; i += blockDim.x) sa.part[i] = tot[i];
@@ -556,10 +565,11 @@ __device__ void epilogue_from_tot(const double* tot, int k, int NRHS, Scalars* _
         }
       }
       s_alpha = sqrt(a2);
+      s_inva = 1.0 / s_alpha;
     }
   }
   __syncthreads();
-  if (s_ok) scalar_step(sc, sa, k, s_alpha);
+  if (s_ok) scalar_step(sc, sa, k, s_alpha, s_inva, tot);
 }
 
 // Last CTA of a reduction: deterministic sum of the per-CTA partials, then the epilogue.
@@ -1854,17 +1864,18 @@ k_fallback_norm(const TQ* __restrict__ Q, int64_t ldq, int k, const TV* __restri
   }
   if (!last_cta(counter)) return;
   __shared__ double tot[1];
-  __shared__ double s_alpha;
+  __shared__ double s_alpha, s_inva;
   sum_partials(partials, gridDim.x, 1, tot);
   __syncthreads();
   if (threadIdx.x == 0) {
     s_alpha = sqrt(tot[0]);
+    s_inva = 1.0 / s_alpha;
     sc->fallback = 0;
     sc->pyth_fallbacks++;
     if (!(s_alpha > 0.0)) set_status(sc, KC_ERR_BREAKDOWN);
   }
   __syncthreads();
-  scalar_step(sc, sa, k, s_alpha);
+  scalar_step(sc, sa, k, s_alpha, s_inva);
 }
 
 // The epilogue of a norm / dot reduction from xx = x^T x and xy = x^T y (one thread).
