@@ -2112,8 +2112,13 @@ static kc_status reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq
   // RED_WARPS / ntask row sub-blocks of ntask warps, so that each SM holds as many warps
   // with loads in flight while the partials (and the last CTA's sums over them) stay few.
   int nw = RED_WARPS, rsub = 1;
+  // FP32 / BF16 vectors from RED_RSUB_TASKS + 1 to 48 tasks: three slots per warp in CTAs
+  // of ceil(ntask / 3) warps, as many per SM as fit.  Every layout holds about 32 warps per
+  // SM (64 registers), so three slots keep the most basis loads in flight (one slot per
+  // warp left the FP32 reduction at 0.62-0.72 of HBM at k = 10-25, m = 16 M).
   const bool split = sizeof(TV) == 4 && ntask <= RED_RSUB_TASKS;
-  const int slots = split ? 1 : (ntask <= 10 ? 1 : (ntask <= RED_WARPS ? 0 : (ntask <= 2 * RED_WARPS ? 2 : (ntask <= 3 * RED_WARPS ? 3 : 0))));
+  const bool three = sizeof(TV) == 4 && !split && ntask <= 3 * RED_WARPS;
+  const int slots = split ? 1 : (three ? 3 : (ntask <= 10 ? 1 : (ntask <= RED_WARPS ? 0 : (ntask <= 2 * RED_WARPS ? 2 : (ntask <= 3 * RED_WARPS ? 3 : 0)))));
   if (slots) {
     nw = (ntask + slots - 1) / slots;
     if (split) rsub = RED_WARPS / ntask;
@@ -2142,7 +2147,8 @@ static kc_status reduce_dispatch(kc_ctx* ctx, int grid, const TQ* Q, int64_t ldq
                     ctx->partials, ctx->counters, ctx->scal, epi, sa, rsub,
                     group_counters(ctx));
   };
-  if (ntask <= RED_WARPS) args(k_reduce<TQ, TV, 1, NRHS>);
+  if (three) args(k_reduce<TQ, TV, 3, NRHS>);
+  else if (ntask <= RED_WARPS) args(k_reduce<TQ, TV, 1, NRHS>);
   else if (ntask <= 2 * RED_WARPS) args(k_reduce<TQ, TV, 2, NRHS>);
   else if (ntask <= 3 * RED_WARPS) args(k_reduce<TQ, TV, 3, NRHS>);
   else if (ntask <= 4 * RED_WARPS) args(k_reduce<TQ, TV, 4, NRHS>);
