@@ -52,7 +52,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) over algorithmic bytes of the offload-mode register-streaming
 # kernels, from the ncu capture summarised in profiles/launches_dcgs2_m16003008_n50.md
 # (steps k = 25 and 26 at m = 4,096,000).  Valid only for those kernels as captured.
-TRAFFIC_RATIO = {"reduce": 1.005, "dcgs2_update": 0.950}
+TRAFFIC_RATIO = {"reduce": 1.007, "dcgs2_update": 0.950}
 
 
 def parse():
