@@ -610,8 +610,10 @@ __device__ void tree_epilogue(const double* __restrict__ partials, int nr, int k
 // With rsub > 1 (a few tasks: one slot, nw = ntask task warps) the CTA's warps form rsub
 // row sub-blocks: each walks its share of the CTA's rows with the whole task set, and the
 // sub-block sums are added in shared memory in sub-block order.
-// The last CTA to finish sums the partials in CTA order (deterministic) and runs the
-// epilogue: the scalar step of Algorithm 4 or a plain store.
+// The partials are summed in a fixed order (deterministic): with gcount, in two levels
+// (tree_arrive: groups of RED_GROUP rows, then the group rows), else by the last CTA to
+// finish in CTA order (the allocation-free step).  The CTA that completes the sums runs
+// the epilogue: the scalar step of Algorithm 4 or a plain store.
 // ----------------------------------------------------------------------------------------
 template <typename TQ, typename TV, int TPW, int NRHS>
 __global__ void __launch_bounds__(RED_THREADS)
@@ -1072,6 +1074,11 @@ constexpr int F64X_RSUB_WARPS = 8;
 // nw / rsub task warps each: every sub-block walks its share of the CTA's rows with the
 // whole task set, so that more warps per SM have loads in flight, and the sub-blocks'
 // sums are added in shared memory in sub-block order before the CTA writes its partials.
+//
+// A warp's sums of its slots come from one butterfly (warp_sum_multi).  With beta and s
+// from the SpMV (ndots > 0), the first warp of each row block's subset-0 CTA adds its share
+// of the SpMV CTAs' sums into the row (add_dots).  The rows are then summed in two levels
+// (tree_arrive, tree_epilogue) and the completing CTA runs the scalar step.
 template <int TPW, int GR>
 __global__ void __launch_bounds__(1024)
 k_reduce_f64x(const double* __restrict__ Q, int64_t ldq, int k, const double* __restrict__ x,
